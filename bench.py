@@ -1,0 +1,412 @@
+"""Benchmark: latent MPM steps/s on one GB300 (and the full-order step beside it).
+
+One "step" is one pass of the whole latent hot path: field inference on the
+integration particles, binning, P2G, grid update, G2P on the sample particles
+and the Gauss-Newton inversion (5 iterations).  Workload: the 200,000-particle
+slab scene with 10,000 integration and 700 sample particles, r = 6, fields of
+5 hidden layers x 128 (BF16 on the tensor cores), 128^3 grid.  Each step is one
+replay of a CUDA graph of one nsf_latent_step call; L2 is flushed (a 512 MB
+write) between timed steps and the flush is outside the timed events.
+
+The full-order MLS-MPM step on the same 200,000-particle slab (neo-Hookean,
+sticky blade) is timed the same way and reported as "full_order".
+
+--impl reference times the FP64 CPU oracle instead (the reference arm of this
+benchmark): the same workload and metric on the host cores.
+
+Multi-GPU (torchrun): replicas only, one independent scene per rank, no
+collective on the data path; value = all ranks' steps / max-over-ranks time.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "latent steps/s vs full-order MPM steps/s on 1 GB300; % tensor/HBM roofline"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def mlp_macs(r, width, depth, out_dim):
+    return (3 + r) * width + (depth - 1) * width * width + width * out_dim
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value, world, device=None):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ GPU ---
+def run_gpu(args, rank, world, local):
+    import torch
+    import paper_2310_17790_gb300 as nsf
+    from paper_2310_17790_gb300 import _native as N
+    from scenes.synthetic import full_config2, latent_config3
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sc = latent_config3(precision=args.precision, steps=args.steps)
+    fs = sc.fields
+    F = nsf.Fields.from_spec(fs)
+    X = torch.from_numpy(np.ascontiguousarray(sc.X.T)).to(dev)
+    gd = nsf.grid_desc(sc.grid.n, sc.grid.dx, sc.grid.gravity, sc.grid.wall_cells)
+    stp = nsf.LatentStepper(F, X, sc.n_S, sc.mass, sc.vol0, gd)
+    z = torch.tensor(sc.z0, dtype=torch.float64, device=dev)
+    zp = z.clone()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # stage events (recorded by the library inside the captured step)
+    nst = N.NSF_LATENT_STAGES
+    taps = N.nsf_latent_taps()
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+    with torch.cuda.stream(stream):
+        for e in ev_b + ev_e:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for i in range(nst):
+        taps.ev_begin[i] = ev_b[i].cuda_event
+        taps.ev_end[i] = ev_e[i].cuda_event
+
+    # first step fills the g(X, z_prev) cache; later steps reuse it
+    with torch.cuda.stream(stream):
+        stp.step(z, zp, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        stp.step(z, zp, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping, taps=taps,
+                 stream=stream, reuse_prev=True)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert stp.read_status() == 0, nsf.status_string(stp.read_status())
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    stage_ms = np.zeros((K, nst))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+                graph.replay()
+                ends[k].record(stream)
+                if k % 16 == 15 or k == K - 1:
+                    # read stage events of completed steps without draining the queue
+                    pass
+            torch.cuda.synchronize()
+    # stage times are those of the last replay (events are reused each replay);
+    # the total is summed per step
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    status = stp.read_status()
+    total_ms = reduce_max(total_ms, world, dev if world > 1 else None)
+
+    # per-stage durations averaged over a separate pass of graph replays
+    stage_runs = min(K, 50)
+    st_acc = np.zeros(nst)
+    with torch.cuda.stream(stream):
+        for k in range(stage_runs):
+            flush.fill_(float(k))
+            graph.replay()
+            torch.cuda.synchronize()
+            st_acc += [ev_b[i].elapsed_time(ev_e[i]) for i in range(nst)]
+    st_ms = st_acc / stage_runs
+
+    steps_per_s = world * K / (total_ms / 1e3)
+    ms_per_step = total_ms / K
+
+    # roofline of the dominant stage
+    peaks, peak_src = load_peaks()
+    r = fs.r
+    macs = [mlp_macs(r, fs.width[i], fs.depth[i], od) for i, od in enumerate((3, 6, 9))]
+    n_N, n_S = sc.X.shape[0], sc.n_S
+    flops = {
+        "inference": 2.0 * n_N * sum(macs),
+        "gauss_newton": 2.0 * sc.gn_iters * n_S * (1 + r) * macs[0],
+    }
+    names = N.NSF_STAGE_NAMES
+    dom = int(np.argmax(st_ms))
+    dom_name = names[dom]
+    if dom_name in flops:
+        peak = peaks["bf16_tflops"] if args.precision == "bf16" else peaks.get("fp32_tflops", 0) or None
+        achieved = flops[dom_name] / (st_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": dom_name, "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None,
+                "peak_source": f"bf16 dense burst, {peak_src}", "traffic": None}
+    else:
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": None,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None}
+
+    # e2e: through the public API with host buffers, copies inside the timed region
+    e2e = run_e2e(args, nsf, sc, F, gd, dev)
+
+    full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
+
+    launches_per_step = 1 + 3 + 1 + 1 + 1 + sc.gn_iters
+    out = {
+        "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": sc.name, "n_integration": n_N, "n_sample": n_S, "r": r,
+                   "width": fs.width[0], "depth": fs.depth[0], "grid": list(sc.grid.n),
+                   "gn_iters": sc.gn_iters, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas{world}", "graph": "one CUDA graph per step"},
+        "stages_ms": {names[i]: float(st_ms[i]) for i in range(nst)},
+        "roofline": roof,
+        "e2e": e2e,
+        "full_order": full,
+        "gpu_launches": launches_per_step * K,
+        "status": status,
+    }
+    return out, clocks
+
+
+def run_e2e(args, nsf, sc, F, gd, dev):
+    """Host-buffer end to end: per step, H2D of X and z (pinned), the step call
+    through the public API, D2H of z."""
+    import torch
+    Kh = min(args.steps, 50)
+    Xh = torch.from_numpy(np.ascontiguousarray(sc.X.T)).pin_memory()
+    zh = torch.tensor(sc.z0, dtype=torch.float64).pin_memory()
+    zph = zh.clone().pin_memory()
+    out = torch.empty_like(zh).pin_memory()
+    Xd = torch.empty_like(Xh, device=dev)
+    zd = torch.empty_like(zh, device=dev)
+    zpd = torch.empty_like(zh, device=dev)
+    stp = nsf.LatentStepper(F, Xd, sc.n_S, sc.mass, sc.vol0, gd)
+    for _ in range(3):
+        Xd.copy_(Xh, non_blocking=True); zd.copy_(zh, non_blocking=True); zpd.copy_(zph, non_blocking=True)
+        stp.step(zd, zpd, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping)
+        out.copy_(zd, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Kh):
+        Xd.copy_(Xh, non_blocking=True)
+        zd.copy_(zh, non_blocking=True)
+        zpd.copy_(zph, non_blocking=True)
+        stp.step(zd, zpd, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping)
+        out.copy_(zd, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt = time.perf_counter() - t0
+    h2d = Xh.numel() * 4 + 2 * zh.numel() * 8
+    return {"value": Kh / dt, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(out.numel() * 8), "steps": Kh,
+            "note": "eager API call per step (no graph), host wall clock"}
+
+
+def run_full(args, nsf, fc, dev, flush):
+    import torch
+    Kf = min(args.steps, 200)
+    x, v = (torch.from_numpy(np.ascontiguousarray(a.T)).to(dev) for a in (fc.x, fc.v))
+    Cm, Fm = (torch.from_numpy(np.ascontiguousarray(a.T)).to(dev) for a in (fc.C, fc.F))
+    gd = nsf.grid_desc(fc.grid.n, fc.grid.dx, fc.grid.gravity, fc.grid.wall_cells, fc.grid.blade)
+    mat = nsf.material(**fc.material)
+    st = nsf.FullStepper(gd, mat, x, v, Cm, Fm, fc.mass, fc.vol0)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        st.step(fc.dt, t0=0.0, nsteps=1, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        st.step(fc.dt, t0=0.0, nsteps=1, stream=stream)
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    torch.cuda.synchronize()
+    s = [torch.cuda.Event(enable_timing=True) for _ in range(Kf)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(Kf)]
+    with torch.cuda.stream(stream):
+        for k in range(Kf):
+            flush.fill_(float(k))
+            s[k].record(stream)
+            graph.replay()
+            e[k].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(s, e))
+    return {"steps_per_s": Kf / (ms / 1e3), "ms_per_step": ms / Kf, "steps": Kf,
+            "workload": fc.name, "status": st.read_status(),
+            "note": "blade time frozen at t=0 inside the replayed graph"}
+
+
+# ---------------------------------------------------------- CPU oracle ---
+def run_oracle(args, budget_s):
+    """The FP64 oracle's latent step on the same workload (bounded sample)."""
+    from oracle import fields as ofields, latent as olatent, mpm as ompm
+    from scenes.synthetic import latent_config3
+
+    sc = latent_config3(precision=args.precision)
+    fs = sc.fields
+    fl = []
+    for i, k in enumerate("ghl"):
+        w = np.asarray(fs.weights[k], np.float64)
+        if fs.precision == "bf16":     # the weight matrices the GPU path uses
+            off = 0
+            for a, b in ofields.layer_dims(fs.r, fs.width[i], fs.depth[i], ofields.OUT_DIM[k]):
+                w[off:off + a * b] = ofields.round_to_bf16(w[off:off + a * b])
+                off += a * b + b
+        fl.append(ofields.Field(w, fs.r, fs.width[i], fs.depth[i], ofields.OUT_DIM[k],
+                                fs.out_scale[k], fs.out_shift[k], residual=(k == "g")))
+    of = olatent.Fields(*fl)
+    g = sc.grid
+    og = ompm.Grid(g.n, g.dx, g.gravity, g.wall_cells, g.blade)
+    X = sc.X.astype(np.float64)
+    z, zp = sc.z0.copy(), sc.z0.copy()
+    steps, t0 = 0, time.perf_counter()
+    max_steps = max(1, args.steps)
+    while steps < max_steps:
+        zn, _ = olatent.latent_step(of, X, sc.n_S, sc.mass, sc.vol0, z, zp, sc.dt, og,
+                                    t=steps * sc.dt, iters=sc.gn_iters, damping=sc.damping)
+        z, zp = zn, z
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": steps / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} consecutive latent steps of {sc.name} (FP64 NumPy oracle)",
+            "seconds": el}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="nsf", choices=["nsf", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        cb = run_oracle(args, budget_s=max(5.0, min(120.0, args.cpu_budget * 3)))
+        out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "steps/s",
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "latent-10000N-700S-r6-w128d5-grid128 (FP64 CPU oracle)"},
+               "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0},
+               "wall_s": time.perf_counter() - t0}
+        print(json.dumps(out))
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out, clocks = run_gpu(args, rank, world, local)
+    out["clocks"] = clocks.summary()
+    if rank == 0:
+        out["cpu_baseline"] = run_oracle(args, budget_s=args.cpu_budget)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

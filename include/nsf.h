@@ -1,0 +1,316 @@
+/*
+ * nsf.h -- C ABI of libnsf, a GB300 (sm_103a) implementation of one latent
+ * time step of "Neural Stress Fields for Reduced-order Elastoplasticity and
+ * Fracture" (Zong et al., SIGGRAPH Asia 2023), plus the full-order MLS-MPM step
+ * it reduces.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All particle arrays are float32, component-major ("SoA"): an array of k
+ *   components for n particles is laid out [k][n], component c of particle p at
+ *   index c * n + p.  3x3 matrices are stored row-major as 9 components
+ *   (C_ab at component 3a + b).  Symmetric stresses use 6 components in the
+ *   order (xx, yy, zz, yz, xz, xy).
+ * - Latent codes z are float64 device arrays of r values.
+ * - The background grid has n[0] x n[1] x n[2] nodes (each a multiple of 4),
+ *   node (i, j, k) at position (i, j, k) * dx.  A particle's quadratic B-spline
+ *   stencil is the 3x3x3 nodes base + {0,1,2} with base = floor(x / dx - 0.5);
+ *   a particle whose stencil leaves the grid is reported as NSF_ERR_OUT_OF_GRID
+ *   and skipped (never clamped).
+ * - Every pointer argument named d_* is device memory owned by the caller.
+ *   Nothing is retained after a call returns except inside an nsf_fields.
+ * - Calls only enqueue work on the caller's CUDA stream (cudaStream_t passed as
+ *   void*; NULL is the legacy default stream) and never synchronise or allocate,
+ *   except nsf_create_fields / nsf_destroy_fields.
+ * - Errors.  The return value reports argument errors (NSF_ERR_INVALID_ARG,
+ *   NSF_ERR_WORKSPACE, NSF_ERR_UNSUPPORTED) and launch failures (NSF_ERR_CUDA).
+ *   Conditions found on the device (out-of-grid particle, non-finite value,
+ *   non-positive Cholesky pivot) are written asynchronously to the caller's
+ *   int *d_status: the first error wins, later ones are dropped, and the
+ *   computation carries on (a singular Gauss-Newton system leaves z unchanged
+ *   for that iteration).  d_status must be 0 before the call for it to be read
+ *   meaningfully.
+ * - Workspaces.  Each stepping call takes a caller-allocated device workspace
+ *   of at least the size reported by the matching *_workspace_size query.  It
+ *   must be zero-filled (cudaMemsetAsync) before its first use; the library
+ *   leaves it in that reusable state after every call that reported no device
+ *   error.  After a device error, zero it again before reuse.  One workspace
+ *   may serve any number of calls on the same scene, one call at a time.
+ */
+#ifndef NSF_H
+#define NSF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nsf_status {
+    NSF_OK = 0,
+    NSF_ERR_INVALID_ARG = -1,   /* bad pointer, size or descriptor field      */
+    NSF_ERR_CUDA = -2,          /* a CUDA runtime call or launch failed       */
+    NSF_ERR_OUT_OF_GRID = -3,   /* device: a particle stencil left the grid   */
+    NSF_ERR_NONFINITE = -4,     /* device: NaN or Inf in a field output       */
+    NSF_ERR_SINGULAR = -5,      /* device: Gauss-Newton matrix not SPD        */
+    NSF_ERR_ITER_CAP = -6,      /* device: a bounded wait gave up             */
+    NSF_ERR_UNSUPPORTED = -7,   /* valid request this build does not provide  */
+    NSF_ERR_NO_MEMORY = -8,     /* nsf_create_fields could not allocate       */
+    NSF_ERR_WORKSPACE = -9      /* workspace pointer NULL or too small        */
+} nsf_status;
+
+/* Field indices: g (deformation, 3 outputs), h (Kirchhoff stress, 6), l (affine, 9). */
+enum { NSF_FIELD_G = 0, NSF_FIELD_H = 1, NSF_FIELD_L = 2 };
+/* Arithmetic of the field networks. */
+enum { NSF_PREC_FP32 = 0, NSF_PREC_BF16 = 1 };
+
+#define NSF_MAX_R 16
+#define NSF_MAX_WIDTH 256
+#define NSF_MAX_DEPTH 8
+
+/*
+ * Neural fields g(X, z), h(X, z), l(X, z)  (paper §4.2-§4.4, App. E).
+ *
+ * Each field is an MLP on the input [X; z] (3 + r values) with depth[f] hidden
+ * layers of width[f] units, each followed by ELU(a) = a (a > 0), exp(a) - 1
+ * (a <= 0), and a linear output layer of 3 (g), 6 (h) or 9 (l) units.  The raw
+ * output y is de-normalised as  shift[f][o] + scale[f][o] * y[o]  (the paper
+ * trains on data normalised to zero mean / unit variance, App. D); with
+ * residual_g != 0 the deformation field returns X + that (x = X + MLP).
+ *
+ * Host weights of field f: one float32 array holding, for every linear layer
+ * l = 0 .. depth[f] in order, W_l row-major [out_l][in_l] then b_l [out_l].
+ *
+ * precision NSF_PREC_FP32: FP32 weights and arithmetic on the CUDA cores.
+ * precision NSF_PREC_BF16: weight matrices rounded to bfloat16 (nearest-even),
+ *   hidden-layer GEMMs on the tcgen05 tensor cores with FP32 accumulation in
+ *   tensor memory; biases, the K = 3 + r input layer, ELU and the output
+ *   de-normalisation stay FP32.
+ * Limits: 1 <= r <= NSF_MAX_R; width[f] a multiple of 16 in [16, NSF_MAX_WIDTH]
+ * (BF16: a multiple of 32 in [32, 256]); 1 <= depth[f] <= NSF_MAX_DEPTH.
+ */
+typedef struct nsf_fields_desc {
+    int r;
+    int width[3];
+    int depth[3];
+    int precision;
+    int residual_g;
+    float out_scale[3][9];
+    float out_shift[3][9];
+} nsf_fields_desc;
+
+typedef struct nsf_fields nsf_fields;   /* opaque; owns device copies of the weights */
+
+/* Validates desc, converts/packs the host weights and uploads them to the
+ * current CUDA device (synchronously).  The only allocating call besides
+ * nsf_destroy_fields.  *out is set only on NSF_OK. */
+nsf_status nsf_create_fields(const nsf_fields_desc *desc,
+                             const float *const host_weights[3],
+                             nsf_fields **out);
+void nsf_destroy_fields(nsf_fields *fields);
+nsf_status nsf_fields_get_desc(const nsf_fields *fields, nsf_fields_desc *out);
+
+/*
+ * Evaluate the fields at n reference points (paper §5.1, network inference).
+ * d_X: [3][n].  d_z: [r] (float64).  Each output may be NULL (not computed):
+ *   d_x    [3][n]   g(X, z)
+ *   d_tau6 [6][n]   h(X, z)
+ *   d_C9   [9][n]   l(X, z)
+ *   d_dxdz [3][r][n] dg_a/dz_k at component a * r + k (forward-mode chain rule)
+ * Non-finite outputs set NSF_ERR_NONFINITE in *d_status (d_status may be NULL).
+ */
+nsf_status nsf_eval_fields(const nsf_fields *fields, const float *d_X, int n,
+                           const double *d_z, float *d_x, float *d_tau6,
+                           float *d_C9, float *d_dxdz, int *d_status,
+                           void *stream);
+
+/*
+ * Background grid and boundary conditions (paper §3.3, grid update: "collision
+ * and Dirichlet boundary conditions are handled at this stage").
+ * Per step, for a node with m_i > 0:  v_i = p_i / m_i + dt * gravity, then
+ *  - walls: if wall_cells > 0, a node with index < wall_cells along an axis has
+ *    a negative velocity component along that axis set to 0, and a node with
+ *    index > n - 1 - wall_cells a positive one;
+ *  - blade (if blade_enable): nodes with |x_i - blade_x| < dx and
+ *    z_i > blade_z0 + blade_vz * t move with the blade, v_i = (0, 0, blade_vz),
+ *    where t is the time at the start of the step.
+ * Nodes with m_i = 0 keep v_i = 0.
+ */
+typedef struct nsf_grid_desc {
+    int n[3];
+    float dx;
+    float gravity[3];
+    int wall_cells;
+    int blade_enable;
+    float blade_x, blade_z0, blade_vz;
+} nsf_grid_desc;
+
+/*
+ * A reduced-order scene (paper §5): n_N integration particles, the first n_S of
+ * which are the sample particles (S is a prefix of N).  d_X: [3][n_N]
+ * reference positions X_p.  Uniform particle mass and initial volume V_p^0.
+ */
+typedef struct nsf_latent_scene {
+    int n_N;
+    int n_S;
+    const float *d_X;
+    float mass;
+    float vol0;
+    nsf_grid_desc grid;
+} nsf_latent_scene;
+
+/* Gauss-Newton options (paper §5.3): a fixed number of iterations (1..32, no
+ * early exit) of (J^T J + damping I) dz = -J^T res, z += dz, in float64. */
+typedef struct nsf_gn_opts {
+    int iters;
+    double damping;
+} nsf_gn_opts;
+
+/*
+ * Optional device buffers receiving intermediate results of the LAST step of a
+ * nsf_latent_step call (for testing and inspection).  Any member may be NULL.
+ * The dense grid taps hold (m, p_x, p_y, p_z) after P2G and (v_x, v_y, v_z, m)
+ * after the grid update per node, node (i, j, k) at ((i * n1 + j) * n2 + k) * 4;
+ * only nodes of grid blocks the step touched are written, so zero them first.
+ */
+/* Stages of a latent step, for the optional stage events of nsf_latent_taps. */
+enum {
+    NSF_STAGE_INFERENCE = 0,   /* field networks on N (§5.1)                 */
+    NSF_STAGE_BIN = 1,         /* particle binning by grid block             */
+    NSF_STAGE_P2G = 2,         /* P2G with the stress force (§3.3, Eq. 5)    */
+    NSF_STAGE_GRID = 3,        /* grid update                                */
+    NSF_STAGE_G2P = 4,         /* G2P on S                                   */
+    NSF_STAGE_GN = 5,          /* Gauss-Newton inversion (§5.3)              */
+    NSF_LATENT_STAGES = 6
+};
+
+typedef struct nsf_latent_taps {
+    float *u_n;       /* [3][n_N]  raw deformation-field value at z_n: x^n - X for a
+                                   residual g (the library works on displacements), x^n otherwise */
+    float *u_prev;    /* [3][n_N]  the same at z_{n-1}               */
+    float *tau6;      /* [6][n_N]  h(X, z_n)                         */
+    float *C9;        /* [9][n_N]  l(X, z_n)                         */
+    float *grid_mp;   /* [n0*n1*n2][4]                               */
+    float *grid_v;    /* [n0*n1*n2][4]                               */
+    float *u_next_S;  /* [3][n_S]  x^{n+1} - X on the sample particles (x^{n+1} for a
+                                   non-residual g): the Gauss-Newton target   */
+    double *z_iter;   /* [iters][r] z after each Gauss-Newton iteration */
+    /* cudaEvent_t handles (or NULL) recorded on the call's stream right before
+     * and right after each stage's launches of the last step (timing only). */
+    void *ev_begin[NSF_LATENT_STAGES];
+    void *ev_end[NSF_LATENT_STAGES];
+} nsf_latent_taps;
+
+/* Flags of nsf_latent_step. */
+enum {
+    /* The workspace still holds g(X, z_prev) from the previous nsf_latent_step
+     * call on the same fields, scene and workspace, and d_z_prev is that call's
+     * returned z_prev: the first step skips re-evaluating g(X, z_prev). */
+    NSF_LATENT_REUSE_PREV = 1
+};
+
+nsf_status nsf_latent_workspace_size(const nsf_fields *fields,
+                                     const nsf_latent_scene *scene,
+                                     size_t *bytes);
+
+/*
+ * nsteps latent steps z_n -> z_{n+1} (paper §5, Fig. "latent space dynamics"):
+ *  1. inference (§5.1): x^n = g(X, z_n), v^n = (g(X, z_n) - g(X, z_{n-1})) / dt,
+ *     tau^n = h(X, z_n), C^n = l(X, z_n) on all integration particles;
+ *  2. one MLS-MPM step (§3.3, §5.2) on N: particles binned by 4^3 grid block,
+ *     P2G of mass, APIC momentum and the stress force of the node force balance
+ *     (Eq. 5, MLS gradient w_ip (4/dx^2)(x_i - x_p)), grid update with gravity
+ *     and boundary conditions, G2P of x^{n+1} = x^n + dt sum_i w_ip v_i on S;
+ *  3. network inversion (§5.3, Eq. 9): opts->iters Gauss-Newton iterations from
+ *     z_n on the sample particles.
+ * In/out: d_z holds z_n on entry and z_{n+nsteps} on return; d_z_prev holds
+ * z_{n-1} on entry (pass a copy of z_0 on the first step: zero initial
+ * velocity) and z_{n+nsteps-1} on return.  g(X, z_{n-1}) is evaluated once per
+ * call unless flags has NSF_LATENT_REUSE_PREV; later steps of the same call
+ * reuse the previous step's g(X, z_n).  Every call leaves g(X, z_prev) of its
+ * returned z_prev in the workspace for a following NSF_LATENT_REUSE_PREV call.
+ * t0 is the time at the start of the first step (moves the blade).
+ * taps may be NULL.
+ */
+nsf_status nsf_latent_step(const nsf_fields *fields,
+                           const nsf_latent_scene *scene, double dt, double t0,
+                           int nsteps, unsigned int flags, double *d_z,
+                           double *d_z_prev,
+                           const nsf_gn_opts *opts, void *d_workspace,
+                           size_t workspace_bytes, int *d_status,
+                           const nsf_latent_taps *taps, void *stream);
+
+/*
+ * Network inversion alone (paper §5.3, Eq. 9): Gauss-Newton on
+ * min_z sum_p || g(X_p, z) - x_p ||^2 over n_S points, starting from *d_z_inout.
+ * d_X_S, d_x_target: [3][n_S].  Optional outputs (may be NULL):
+ * d_z_iter [iters][r] z after each iteration; d_residual [3][n_S] the final
+ * g(X_p, z) - x_p.
+ */
+nsf_status nsf_project_workspace_size(const nsf_fields *fields, int n_S,
+                                      size_t *bytes);
+nsf_status nsf_project(const nsf_fields *fields, const float *d_X_S,
+                       const float *d_x_target, int n_S, double *d_z_inout,
+                       const nsf_gn_opts *opts, double *d_z_iter,
+                       float *d_residual, void *d_workspace,
+                       size_t workspace_bytes, int *d_status, void *stream);
+
+/* Constitutive models of the full-order step (paper App. F; neo-Hookean is the
+ * textbook tau = mu (F F^T - I) + lambda ln(J) I).  The two plastic models use
+ * the Hencky (StVK, App. F.2) stress of F^E and return-map F in float64. */
+enum {
+    NSF_NEO_HOOKEAN = 0,
+    NSF_FIXED_COROTATED = 1,
+    NSF_VON_MISES = 2,        /* App. F.4, constant yield stress            */
+    NSF_DRUCKER_PRAGER = 3    /* App. F.3, friction angle in degrees        */
+};
+
+typedef struct nsf_material {
+    int model;
+    float E, nu;
+    float yield_stress;
+    float friction_deg;
+} nsf_material;
+
+/* Full-order particle state, device SoA: x, v [3][n]; C, F [9][n] (F is the
+ * elastic part F^E for the plastic models). */
+typedef struct nsf_particles {
+    int n;
+    float *d_x;
+    float *d_v;
+    float *d_C;
+    float *d_F;
+    float mass;
+    float vol0;
+} nsf_particles;
+
+typedef struct nsf_full_taps {
+    float *grid_mp;   /* as in nsf_latent_taps, last step */
+    float *grid_v;
+} nsf_full_taps;
+
+nsf_status nsf_full_workspace_size(const nsf_grid_desc *grid, int n,
+                                   size_t *bytes);
+
+/*
+ * nsteps full-order explicit MLS-MPM steps (paper §3.3): stress tau(F_p), P2G
+ * (mass, APIC momentum, MLS stress force), grid update, G2P of v, x,
+ * C = (4/dx^2) sum_i w_ip v_i (x_i - x_p)^T, F <- (I + dt C) F, then the
+ * material's return map.  Updates particles in place.  taps may be NULL.
+ */
+nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
+                         const nsf_particles *particles, double dt, double t0,
+                         int nsteps, void *d_workspace, size_t workspace_bytes,
+                         int *d_status, const nsf_full_taps *taps,
+                         void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *nsf_status_string(int status);
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int nsf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSF_H */

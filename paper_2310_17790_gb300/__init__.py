@@ -1,0 +1,260 @@
+"""GB300 (sm_103a) latent MPM step of Neural Stress Fields (Zong et al. 2023).
+
+Python binding of libnsf (include/nsf.h).  PyTorch only provides device memory
+and streams; every computation runs in the library's CUDA kernels, and the
+binding raises if the library is not built.  Particle arrays are float32
+component-major tensors of shape [k, n] on the current CUDA device; latent
+codes are float64 tensors of shape [r].
+
+The functions named after the C entry points (``nsf_latent_step`` ...) take
+torch tensors and forward them one to one; ``Fields``, ``LatentStepper`` and
+``FullStepper`` add ownership of the weights, the workspace and the status
+word.
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+from ._native import NsfError, check, status_string  # noqa: F401
+
+PRECISION = {"fp32": N.NSF_PREC_FP32, "bf16": N.NSF_PREC_BF16}
+MODELS = {"neo_hookean": N.NSF_NEO_HOOKEAN, "fixed_corotated": N.NSF_FIXED_COROTATED,
+          "von_mises": N.NSF_VON_MISES, "drucker_prager": N.NSF_DRUCKER_PRAGER}
+FIELD_NAMES = ("g", "h", "l")
+OUT_DIM = (3, 6, 9)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _as3(v):
+    return tuple(v) if np.ndim(v) else (int(v),) * 3
+
+
+class Fields:
+    """Owns an nsf_fields (device copies of the three field networks).
+
+    weights: mapping 'g'/'h'/'l' (or a sequence of three) -> flat float32 array
+    in the layout of nsf.h; width/depth: int or 3 ints; precision 'fp32'|'bf16'.
+    """
+
+    def __init__(self, r, width, depth, weights, precision="fp32", out_scale=None,
+                 out_shift=None, residual_g=True):
+        if isinstance(weights, dict):
+            weights = [weights[k] for k in FIELD_NAMES]
+        self.r = int(r)
+        self.width = _as3(width)
+        self.depth = _as3(depth)
+        self.precision = precision
+        d = N.nsf_fields_desc()
+        d.r = self.r
+        for f in range(3):
+            d.width[f] = self.width[f]
+            d.depth[f] = self.depth[f]
+            sc = np.ones(OUT_DIM[f]) if out_scale is None else np.asarray(
+                out_scale[FIELD_NAMES[f]] if isinstance(out_scale, dict) else out_scale[f])
+            sh = np.zeros(OUT_DIM[f]) if out_shift is None else np.asarray(
+                out_shift[FIELD_NAMES[f]] if isinstance(out_shift, dict) else out_shift[f])
+            for o in range(OUT_DIM[f]):
+                d.out_scale[f][o] = float(sc[o])
+                d.out_shift[f][o] = float(sh[o])
+        d.precision = PRECISION[precision]
+        d.residual_g = 1 if residual_g else 0
+        self._arrays = [np.ascontiguousarray(w, dtype=np.float32) for w in weights]
+        ptrs = (C.c_void_p * 3)(*[a.ctypes.data for a in self._arrays])
+        h = C.c_void_p()
+        check(N.lib.nsf_create_fields(C.byref(d), C.byref(ptrs), C.byref(h)), "nsf_create_fields")
+        self.handle = h
+        self.desc = d
+        self.residual_g = bool(residual_g)
+
+    @classmethod
+    def from_spec(cls, spec):
+        """Build from any object with r, width, depth, precision, weights,
+        out_scale, out_shift (and optionally residual_g) attributes."""
+        return cls(spec.r, spec.width, spec.depth, spec.weights, spec.precision,
+                   spec.out_scale, spec.out_shift, getattr(spec, "residual_g", True))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            N.lib.nsf_destroy_fields(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_desc(n, dx, gravity=(0.0, 0.0, -9.8), wall_cells=3, blade=None):
+    g = N.nsf_grid_desc()
+    for i, v in enumerate(_as3(n)):
+        g.n[i] = int(v)
+    g.dx = float(dx)
+    for i in range(3):
+        g.gravity[i] = float(gravity[i])
+    g.wall_cells = int(wall_cells)
+    if blade is not None:
+        g.blade_enable = 1
+        g.blade_x, g.blade_z0, g.blade_vz = float(blade["x"]), float(blade["z0"]), float(blade["vz"])
+    return g
+
+
+def latent_scene(X, n_S, mass, vol0, grid):
+    sc = N.nsf_latent_scene()
+    sc.n_N = int(X.shape[1])
+    sc.n_S = int(n_S)
+    sc.d_X = _ptr(X)
+    sc.mass = float(mass)
+    sc.vol0 = float(vol0)
+    sc.grid = grid
+    return sc
+
+
+def gn_opts(iters=5, damping=1e-6):
+    o = N.nsf_gn_opts()
+    o.iters = int(iters)
+    o.damping = float(damping)
+    return o
+
+
+# ------------------------------------------------ C-named thin wrappers ---
+def nsf_eval_fields(fields, X, z, x=None, tau6=None, C9=None, dxdz=None, status=None,
+                    stream=None):
+    check(N.lib.nsf_eval_fields(fields.handle, _ptr(X), int(X.shape[1]), _ptr(z), _ptr(x),
+                                _ptr(tau6), _ptr(C9), _ptr(dxdz), _ptr(status),
+                                _stream(stream)), "nsf_eval_fields")
+
+
+def nsf_latent_workspace_size(fields, scene):
+    b = C.c_size_t()
+    check(N.lib.nsf_latent_workspace_size(fields.handle, C.byref(scene), C.byref(b)),
+          "nsf_latent_workspace_size")
+    return b.value
+
+
+def nsf_latent_step(fields, scene, dt, t0, nsteps, z, z_prev, opts, workspace, status,
+                    taps=None, stream=None, flags=0):
+    check(N.lib.nsf_latent_step(fields.handle, C.byref(scene), float(dt), float(t0),
+                                int(nsteps), int(flags), _ptr(z), _ptr(z_prev), C.byref(opts),
+                                _ptr(workspace), workspace.numel(), _ptr(status),
+                                C.byref(taps) if taps is not None else None,
+                                _stream(stream)), "nsf_latent_step")
+
+
+def nsf_project_workspace_size(fields, n_S):
+    b = C.c_size_t()
+    check(N.lib.nsf_project_workspace_size(fields.handle, int(n_S), C.byref(b)),
+          "nsf_project_workspace_size")
+    return b.value
+
+
+def nsf_project(fields, X_S, x_target, z, opts, workspace, status, z_iter=None,
+                residual=None, stream=None):
+    check(N.lib.nsf_project(fields.handle, _ptr(X_S), _ptr(x_target), int(X_S.shape[1]),
+                            _ptr(z), C.byref(opts), _ptr(z_iter), _ptr(residual),
+                            _ptr(workspace), workspace.numel(), _ptr(status),
+                            _stream(stream)), "nsf_project")
+
+
+def nsf_full_workspace_size(grid, n):
+    b = C.c_size_t()
+    check(N.lib.nsf_full_workspace_size(C.byref(grid), int(n), C.byref(b)),
+          "nsf_full_workspace_size")
+    return b.value
+
+
+def material(model="neo_hookean", E=2e5, nu=0.3, yield_stress=0.0, friction_deg=30.0):
+    m = N.nsf_material()
+    m.model = MODELS[model]
+    m.E, m.nu = float(E), float(nu)
+    m.yield_stress, m.friction_deg = float(yield_stress), float(friction_deg)
+    return m
+
+
+def particles(x, v, Cm, F, mass, vol0):
+    p = N.nsf_particles()
+    p.n = int(x.shape[1])
+    p.d_x, p.d_v, p.d_C, p.d_F = _ptr(x), _ptr(v), _ptr(Cm), _ptr(F)
+    p.mass, p.vol0 = float(mass), float(vol0)
+    return p
+
+
+def nsf_full_step(grid, mat, parts, dt, t0, nsteps, workspace, status, taps=None,
+                  stream=None):
+    check(N.lib.nsf_full_step(C.byref(grid), C.byref(mat), C.byref(parts), float(dt),
+                              float(t0), int(nsteps), _ptr(workspace), workspace.numel(),
+                              _ptr(status), C.byref(taps) if taps is not None else None,
+                              _stream(stream)), "nsf_full_step")
+
+
+# ---------------------------------------------------------- ownership ---
+def _zeros_u8(nbytes, device):
+    torch = _torch()
+    return torch.zeros(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+class LatentStepper:
+    """Workspace + status word for repeated latent steps of one scene."""
+
+    def __init__(self, fields, X, n_S, mass, vol0, grid):
+        torch = _torch()
+        self.fields = fields
+        self.X = X
+        self.scene = latent_scene(X, n_S, mass, vol0, grid)
+        self.ws = _zeros_u8(nsf_latent_workspace_size(fields, self.scene), X.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=X.device)
+
+    def step(self, z, z_prev, dt, t0=0.0, nsteps=1, iters=5, damping=1e-6, taps=None,
+             stream=None, reuse_prev=False):
+        nsf_latent_step(self.fields, self.scene, dt, t0, nsteps, z, z_prev,
+                        gn_opts(iters, damping), self.ws, self.status, taps, stream,
+                        N.NSF_LATENT_REUSE_PREV if reuse_prev else 0)
+
+    def read_status(self):
+        return int(self.status.item())
+
+
+class FullStepper:
+    def __init__(self, grid, mat, x, v, Cm, F, mass, vol0):
+        torch = _torch()
+        self.grid, self.mat = grid, mat
+        self.tensors = (x, v, Cm, F)
+        self.parts = particles(x, v, Cm, F, mass, vol0)
+        self.ws = _zeros_u8(nsf_full_workspace_size(grid, x.shape[1]), x.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=x.device)
+
+    def step(self, dt, t0=0.0, nsteps=1, taps=None, stream=None):
+        nsf_full_step(self.grid, self.mat, self.parts, dt, t0, nsteps, self.ws, self.status,
+                      taps, stream)
+
+    def read_status(self):
+        return int(self.status.item())
+
+
+def project(fields, X_S, x_target, z, iters=5, damping=1e-6, z_iter=None, residual=None,
+            stream=None):
+    """Gauss-Newton network inversion (§5.3); updates z in place, returns status."""
+    torch = _torch()
+    ws = _zeros_u8(nsf_project_workspace_size(fields, X_S.shape[1]), X_S.device)
+    status = torch.zeros(1, dtype=torch.int32, device=X_S.device)
+    nsf_project(fields, X_S, x_target, z, gn_opts(iters, damping), ws, status, z_iter,
+                residual, stream)
+    return status

@@ -1,0 +1,619 @@
+// Host side of the libnsf C ABI (include/nsf.h): argument validation, weight
+// packing, workspace layout and the launch sequence of each call.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device_common.cuh"
+
+using namespace nsf;
+
+struct nsf_fields {
+    nsf_fields_desc desc;
+    FieldsDev dev;
+    void *d_mem;
+    size_t bytes;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+// Sequential sub-allocation of one caller workspace.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    }
+};
+
+bool valid_grid(const nsf_grid_desc *g) {
+    if (!g) return false;
+    for (int d = 0; d < 3; ++d)
+        if (g->n[d] < 8 || g->n[d] > 2048 || (g->n[d] & 3)) return false;
+    if (!(g->dx > 0.f) || !std::isfinite(g->dx)) return false;
+    if (g->wall_cells < 0) return false;
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(g->gravity[d])) return false;
+    size_t nodes = (size_t)g->n[0] * g->n[1] * g->n[2];
+    return nodes <= ((size_t)1 << 31) / 64;
+}
+
+GridParams make_params(const nsf_grid_desc *g) {
+    GridParams p;
+    p.dx = g->dx;
+    p.inv_dx = 1.f / g->dx;
+    p.gx = g->gravity[0];
+    p.gy = g->gravity[1];
+    p.gz = g->gravity[2];
+    p.wall_cells = g->wall_cells;
+    p.blade_enable = g->blade_enable;
+    p.blade_x = g->blade_x;
+    p.blade_z0 = g->blade_z0;
+    p.blade_vz = g->blade_vz;
+    return p;
+}
+
+// Grid part of a workspace.
+struct GridLayout {
+    size_t acc, vel, gstamp, cnt, blk_slot, plist, pcount, poff, glist, key, rank, perm, ctl;
+    int nblocks, max_pblocks, max_gblocks;
+};
+
+GridLayout carve_grid(Carver &c, const nsf_grid_desc *g, int n) {
+    GridLayout L;
+    size_t nodes = (size_t)g->n[0] * g->n[1] * g->n[2];
+    L.nblocks = (int)(nodes / 64);
+    L.max_pblocks = n < L.nblocks ? n : L.nblocks;
+    long long mg = 8LL * L.max_pblocks;
+    L.max_gblocks = mg < L.nblocks ? (int)mg : L.nblocks;
+    L.ctl = c.take(sizeof(Ctl));
+    L.acc = c.take(nodes * sizeof(float4));
+    L.vel = c.take(nodes * sizeof(float4));
+    L.gstamp = c.take((size_t)L.nblocks * 4);
+    L.cnt = c.take((size_t)L.nblocks * 4);
+    L.blk_slot = c.take((size_t)L.nblocks * 4);
+    L.plist = c.take((size_t)L.max_pblocks * 4);
+    L.pcount = c.take((size_t)L.max_pblocks * 4);
+    L.poff = c.take((size_t)(L.max_pblocks + 1) * 4);
+    L.glist = c.take((size_t)L.max_gblocks * 4);
+    L.key = c.take((size_t)n * 4);
+    L.rank = c.take((size_t)n * 4);
+    L.perm = c.take((size_t)n * 4);
+    return L;
+}
+
+GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
+    GridWs w;
+    w.n0 = g->n[0];
+    w.n1 = g->n[1];
+    w.n2 = g->n[2];
+    w.nb0 = w.n0 / 4;
+    w.nb1 = w.n1 / 4;
+    w.nb2 = w.n2 / 4;
+    w.nblocks = L.nblocks;
+    w.acc = reinterpret_cast<float4 *>(base + L.acc);
+    w.vel = reinterpret_cast<float4 *>(base + L.vel);
+    w.gstamp = reinterpret_cast<int *>(base + L.gstamp);
+    w.cnt = reinterpret_cast<int *>(base + L.cnt);
+    w.blk_slot = reinterpret_cast<int *>(base + L.blk_slot);
+    w.plist = reinterpret_cast<int *>(base + L.plist);
+    w.pcount = reinterpret_cast<int *>(base + L.pcount);
+    w.poff = reinterpret_cast<int *>(base + L.poff);
+    w.glist = reinterpret_cast<int *>(base + L.glist);
+    w.key = reinterpret_cast<int *>(base + L.key);
+    w.rank = reinterpret_cast<int *>(base + L.rank);
+    w.perm = reinterpret_cast<int *>(base + L.perm);
+    w.ctl = reinterpret_cast<Ctl *>(base + L.ctl);
+    w.max_p = n;
+    w.max_pblocks = L.max_pblocks;
+    w.max_gblocks = L.max_gblocks;
+    return w;
+}
+
+struct LatentLayout {
+    GridLayout grid;
+    size_t u[2], tau, C, dnext, partials, zgn, gnctl;
+    size_t total;
+};
+
+LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc) {
+    Carver c;
+    LatentLayout L;
+    L.grid = carve_grid(c, &sc->grid, sc->n_N);
+    size_t n = (size_t)sc->n_N;
+    L.u[0] = c.take(3 * n * 4);
+    L.u[1] = c.take(3 * n * 4);
+    L.tau = c.take(6 * n * 4);
+    L.C = c.take(9 * n * 4);
+    L.dnext = c.take(3 * (size_t)sc->n_S * 4);
+    int grid = f->dev.precision == NSF_PREC_BF16 ? jac_grid_size_tc(f->dev, sc->n_S)
+                                                 : jac_grid_size_simt(f->dev, sc->n_S);
+    L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
+    L.zgn = c.take(NSF_MAX_R * 8);
+    L.gnctl = c.take(64);
+    L.total = c.off;
+    return L;
+}
+
+struct ProjectLayout {
+    size_t target, u, partials, zgn, gnctl, total;
+};
+
+ProjectLayout project_layout(const nsf_fields *f, int n_S) {
+    Carver c;
+    ProjectLayout L;
+    L.target = c.take(3 * (size_t)n_S * 4);
+    L.u = c.take(3 * (size_t)n_S * 4);
+    int grid = f->dev.precision == NSF_PREC_BF16 ? jac_grid_size_tc(f->dev, n_S)
+                                                 : jac_grid_size_simt(f->dev, n_S);
+    L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
+    L.zgn = c.take(NSF_MAX_R * 8);
+    L.gnctl = c.take(64);
+    L.total = c.off;
+    return L;
+}
+
+struct FullLayout {
+    GridLayout grid;
+    size_t tau, total;
+};
+
+FullLayout full_layout(const nsf_grid_desc *g, int n) {
+    Carver c;
+    FullLayout L;
+    L.grid = carve_grid(c, g, n);
+    L.tau = c.take(6 * (size_t)n * 4);
+    L.total = c.off;
+    return L;
+}
+
+// ------------------------------------------------------- small kernels ---
+// out[i] = a[i] + s * b[i]  over `count` floats.
+__global__ void k_axpy(float *out, const float *a, const float *b, float s, int count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = a[i] + s * b[i];
+}
+
+cudaError_t axpy(float *out, const float *a, const float *b, float s, int count,
+                 cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_axpy<<<(count + 255) / 256, 256, 0, st>>>(out, a, b, s, count);
+    return cudaGetLastError();
+}
+
+cudaError_t run_fields(const FieldsDev &fd, const float *X, int n, int ld, int njobs,
+                       const FieldJob *jobs, int *status, cudaStream_t s) {
+    if (n <= 0 || njobs <= 0) return cudaSuccess;
+    if (fd.precision == NSF_PREC_BF16) return launch_fields_tc(fd, X, n, ld, njobs, jobs, status, s);
+    return launch_fields_simt(fd, X, n, ld, njobs, jobs, status, s);
+}
+
+cudaError_t run_jacobian(const FieldsDev &fd, const float *X, int n, int ld, const double *z,
+                         float *u, float *dudz, const GnArgs *gn, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (fd.precision == NSF_PREC_BF16)
+        return launch_jacobian_tc(fd, X, n, ld, z, u, dudz, gn, status, s);
+    return launch_jacobian_simt(fd, X, n, ld, z, u, dudz, gn, status, s);
+}
+
+bool valid_fields_desc(const nsf_fields_desc *d) {
+    if (!d) return false;
+    if (d->r < 1 || d->r > NSF_MAX_R) return false;
+    if (d->precision != NSF_PREC_FP32 && d->precision != NSF_PREC_BF16) return false;
+    for (int f = 0; f < 3; ++f) {
+        int w = d->width[f];
+        if (w < 16 || w > NSF_MAX_WIDTH || (w % 16)) return false;
+        if (d->depth[f] < 1 || d->depth[f] > NSF_MAX_DEPTH) return false;
+        for (int o = 0; o < kOutDim[f]; ++o)
+            if (!std::isfinite(d->out_scale[f][o]) || !std::isfinite(d->out_shift[f][o])) return false;
+    }
+    return true;
+}
+
+bool valid_gn(const nsf_gn_opts *o) {
+    return o && o->iters >= 1 && o->iters <= 32 && std::isfinite(o->damping) && o->damping >= 0.0;
+}
+
+#define NSF_CUDA_TRY(expr)                       \
+    do {                                         \
+        cudaError_t e_ = (expr);                 \
+        if (e_ != cudaSuccess) return NSF_ERR_CUDA; \
+    } while (0)
+
+}  // namespace
+
+// Defined in fields_tc.cu: packs one hidden layer [out][in] (fp32 host values)
+// into the bf16 tensor-core operand order; returns the element count written.
+namespace nsf {
+size_t tc_pack_size(int width);
+void tc_pack_layer(const float *W, int width, __nv_bfloat16 *dst);
+}
+
+extern "C" {
+
+int nsf_version(void) { return 100; }
+
+const char *nsf_status_string(int s) {
+    switch (s) {
+        case NSF_OK: return "ok";
+        case NSF_ERR_INVALID_ARG: return "invalid argument";
+        case NSF_ERR_CUDA: return "CUDA error";
+        case NSF_ERR_OUT_OF_GRID: return "particle stencil outside the grid";
+        case NSF_ERR_NONFINITE: return "non-finite value";
+        case NSF_ERR_SINGULAR: return "Gauss-Newton system not positive definite";
+        case NSF_ERR_ITER_CAP: return "bounded wait gave up";
+        case NSF_ERR_UNSUPPORTED: return "unsupported request";
+        case NSF_ERR_NO_MEMORY: return "out of device memory";
+        case NSF_ERR_WORKSPACE: return "workspace missing or too small";
+        default: return "unknown status";
+    }
+}
+
+nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const host_weights[3],
+                             nsf_fields **out) {
+    if (!out || !valid_fields_desc(desc) || !host_weights) return NSF_ERR_INVALID_ARG;
+    for (int f = 0; f < 3; ++f)
+        if (!host_weights[f]) return NSF_ERR_INVALID_ARG;
+    const bool bf16 = desc->precision == NSF_PREC_BF16;
+    const int r = desc->r;
+
+    // Host staging: float section then (bf16) packed section.
+    std::vector<float> fbuf;
+    std::vector<__nv_bfloat16> hbuf;
+    struct Off {
+        size_t W0, Wout, b[NSF_MAX_DEPTH + 1], Wt[NSF_MAX_DEPTH], Wtc[NSF_MAX_DEPTH];
+    } off[3];
+    auto push = [&](const float *src, size_t count) {
+        size_t o = fbuf.size();
+        fbuf.insert(fbuf.end(), src, src + count);
+        while (fbuf.size() % 64) fbuf.push_back(0.f);   // keep 256-byte alignment
+        return o;
+    };
+    auto round_bf16 = [](float v) { return __bfloat162float(__float2bfloat16_rn(v)); };
+    for (int f = 0; f < 3; ++f) {
+        const int W = desc->width[f], D = desc->depth[f], od = kOutDim[f];
+        const float *src = host_weights[f];
+        size_t pos = 0;
+        for (int l = 0; l <= D; ++l) {
+            int in = l == 0 ? 3 + r : W;
+            int o = l == D ? od : W;
+            std::vector<float> Wm(src + pos, src + pos + (size_t)in * o);
+            pos += (size_t)in * o;
+            for (float v : Wm)
+                if (!std::isfinite(v)) return NSF_ERR_INVALID_ARG;
+            if (bf16)
+                for (float &v : Wm) v = round_bf16(v);
+            if (l == 0) {
+                off[f].W0 = push(Wm.data(), Wm.size());
+            } else if (l == D) {
+                off[f].Wout = push(Wm.data(), Wm.size());
+            } else {
+                std::vector<float> Wt((size_t)W * W);
+                for (int j = 0; j < W; ++j)
+                    for (int k = 0; k < W; ++k) Wt[(size_t)k * W + j] = Wm[(size_t)j * W + k];
+                off[f].Wt[l] = push(Wt.data(), Wt.size());
+                if (bf16) {
+                    size_t o2 = hbuf.size();
+                    size_t cnt = tc_pack_size(W);
+                    hbuf.resize(o2 + cnt);
+                    tc_pack_layer(Wm.data(), W, hbuf.data() + o2);
+                    while (hbuf.size() % 128) hbuf.push_back(__float2bfloat16_rn(0.f));
+                    off[f].Wtc[l] = o2;
+                }
+            }
+            for (int q = 0; q < o; ++q)
+                if (!std::isfinite(src[pos + q])) return NSF_ERR_INVALID_ARG;
+            off[f].b[l] = push(src + pos, o);
+            pos += o;
+        }
+    }
+    size_t fbytes = fbuf.size() * sizeof(float);
+    size_t hbytes = hbuf.size() * sizeof(__nv_bfloat16);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, fbytes + hbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NSF_ERR_NO_MEMORY;
+    }
+    if (cudaMemcpy(mem, fbuf.data(), fbytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (hbytes && cudaMemcpy((char *)mem + fbytes, hbuf.data(), hbytes, cudaMemcpyHostToDevice) !=
+                       cudaSuccess)) {
+        cudaFree(mem);
+        return NSF_ERR_CUDA;
+    }
+    nsf_fields *F = new (std::nothrow) nsf_fields;
+    if (!F) {
+        cudaFree(mem);
+        return NSF_ERR_NO_MEMORY;
+    }
+    std::memset(F, 0, sizeof(*F));
+    F->desc = *desc;
+    F->d_mem = mem;
+    F->bytes = fbytes + hbytes;
+    const float *fb = static_cast<const float *>(mem);
+    const __nv_bfloat16 *hb = reinterpret_cast<const __nv_bfloat16 *>((char *)mem + fbytes);
+    F->dev.r = r;
+    F->dev.residual_g = desc->residual_g ? 1 : 0;
+    F->dev.precision = desc->precision;
+    for (int f = 0; f < 3; ++f) {
+        FieldDev &d = F->dev.f[f];
+        d.width = desc->width[f];
+        d.depth = desc->depth[f];
+        d.out_dim = kOutDim[f];
+        d.W0 = fb + off[f].W0;
+        d.Wout = fb + off[f].Wout;
+        for (int l = 0; l <= d.depth; ++l) d.b[l] = fb + off[f].b[l];
+        for (int l = 1; l < d.depth; ++l) {
+            d.Wt[l] = fb + off[f].Wt[l];
+            d.Wtc[l] = bf16 ? hb + off[f].Wtc[l] : nullptr;
+        }
+        for (int o = 0; o < 9; ++o) {
+            d.scale[o] = o < d.out_dim ? desc->out_scale[f][o] : 0.f;
+            d.shift[o] = o < d.out_dim ? desc->out_shift[f][o] : 0.f;
+        }
+    }
+    *out = F;
+    return NSF_OK;
+}
+
+void nsf_destroy_fields(nsf_fields *f) {
+    if (!f) return;
+    cudaFree(f->d_mem);
+    delete f;
+}
+
+nsf_status nsf_fields_get_desc(const nsf_fields *f, nsf_fields_desc *out) {
+    if (!f || !out) return NSF_ERR_INVALID_ARG;
+    *out = f->desc;
+    return NSF_OK;
+}
+
+nsf_status nsf_eval_fields(const nsf_fields *f, const float *d_X, int n, const double *d_z,
+                           float *d_x, float *d_tau6, float *d_C9, float *d_dxdz,
+                           int *d_status, void *stream) {
+    if (!f || n < 0 || (n > 0 && (!d_X || !d_z))) return NSF_ERR_INVALID_ARG;
+    if (n == 0) return NSF_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FieldJob jobs[3];
+    int nj = 0;
+    if (d_x) jobs[nj++] = FieldJob{NSF_FIELD_G, d_z, d_x};
+    if (d_tau6) jobs[nj++] = FieldJob{NSF_FIELD_H, d_z, d_tau6};
+    if (d_C9) jobs[nj++] = FieldJob{NSF_FIELD_L, d_z, d_C9};
+    NSF_CUDA_TRY(run_fields(f->dev, d_X, n, n, nj, jobs, d_status, s));
+    if (d_x && f->dev.residual_g) NSF_CUDA_TRY(axpy(d_x, d_x, d_X, 1.f, 3 * n, s));
+    if (d_dxdz) NSF_CUDA_TRY(run_jacobian(f->dev, d_X, n, n, d_z, nullptr, d_dxdz, nullptr, d_status, s));
+    return NSF_OK;
+}
+
+nsf_status nsf_latent_workspace_size(const nsf_fields *f, const nsf_latent_scene *sc, size_t *bytes) {
+    if (!f || !sc || !bytes || sc->n_N < 1 || sc->n_S < 1 || sc->n_S > sc->n_N ||
+        !valid_grid(&sc->grid))
+        return NSF_ERR_INVALID_ARG;
+    *bytes = latent_layout(f, sc).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, double dt, double t0,
+                           int nsteps, unsigned int flags, double *d_z, double *d_z_prev,
+                           const nsf_gn_opts *opts,
+                           void *d_ws, size_t ws_bytes, int *d_status,
+                           const nsf_latent_taps *taps, void *stream) {
+    if (!f || !sc || !d_z || !d_z_prev || !valid_gn(opts) || nsteps < 0 || !sc->d_X ||
+        sc->n_N < 1 || sc->n_S < 1 || sc->n_S > sc->n_N || !valid_grid(&sc->grid) ||
+        !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0) || !(sc->mass > 0.f) ||
+        !(sc->vol0 > 0.f) || (flags & ~(unsigned)NSF_LATENT_REUSE_PREV))
+        return NSF_ERR_INVALID_ARG;
+    if (nsteps == 0) return NSF_OK;
+    LatentLayout L = latent_layout(f, sc);
+    if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    GridWs g = grid_ws(base, L.grid, &sc->grid, sc->n_N);
+    GridParams gp = make_params(&sc->grid);
+    const int nN = sc->n_N, nS = sc->n_S, r = f->desc.r;
+    float *ub[2] = {reinterpret_cast<float *>(base + L.u[0]), reinterpret_cast<float *>(base + L.u[1])};
+    float *tau = reinterpret_cast<float *>(base + L.tau);
+    float *C9 = reinterpret_cast<float *>(base + L.C);
+    float *dnext = reinterpret_cast<float *>(base + L.dnext);
+    double *partials = reinterpret_cast<double *>(base + L.partials);
+    double *zgn = reinterpret_cast<double *>(base + L.zgn);
+    int *gn_counter = reinterpret_cast<int *>(base + L.gnctl);
+    const float *Xoff = f->dev.residual_g ? sc->d_X : nullptr;
+    // ub[1] holds g(X, z_prev) between calls; step s writes g(X, z_n) to ub[s & 1 ^ 0]
+    // and reads g(X, z_{n-1}) from the other buffer.
+    const bool reuse = (flags & NSF_LATENT_REUSE_PREV) != 0;
+    int cur = 0;
+    // Stage events; under stream capture they become external event-record
+    // nodes so that they still time each replay.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (taps) NSF_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                   : cudaEventRecordDefault;
+    auto ev = [&](bool on, void *const *arr, int stage) -> cudaError_t {
+        if (!on || !arr[stage]) return cudaSuccess;
+        return cudaEventRecordWithFlags(static_cast<cudaEvent_t>(arr[stage]), s, ev_flags);
+    };
+    for (int step = 0; step < nsteps; ++step) {
+        const bool last = step == nsteps - 1;
+        const bool tev = last && taps;
+        float *u_n = ub[cur], *u_prev = ub[cur ^ 1];
+        // 1. inference (§5.1)
+        FieldJob jobs[4] = {{NSF_FIELD_G, d_z, u_n}, {NSF_FIELD_H, d_z, tau}, {NSF_FIELD_L, d_z, C9},
+                            {NSF_FIELD_G, d_z_prev, u_prev}};
+        const int njobs = (step == 0 && !reuse) ? 4 : 3;
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_INFERENCE));
+        NSF_CUDA_TRY(run_fields(f->dev, sc->d_X, nN, nN, njobs, jobs, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_INFERENCE));
+        // 2. MPM step on N (§5.2)
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_BIN));
+        NSF_CUDA_TRY(launch_bin(g, Xoff, u_n, nN, gp.inv_dx, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_BIN));
+        P2gLatentArgs pa;
+        pa.X = Xoff;
+        pa.u = u_n;
+        pa.u_prev = u_prev;
+        pa.tau6 = tau;
+        pa.C9 = C9;
+        pa.n = nN;
+        pa.mass = sc->mass;
+        pa.vol0 = sc->vol0;
+        pa.inv_dt = (float)(1.0 / dt);
+        pa.dt = (float)dt;
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_P2G));
+        NSF_CUDA_TRY(launch_p2g_latent(g, gp, pa, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_P2G));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GRID));
+        NSF_CUDA_TRY(launch_grid_update(g, gp, (float)dt, t0 + step * dt,
+                                        last && taps ? taps->grid_mp : nullptr,
+                                        last && taps ? taps->grid_v : nullptr, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_GRID));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_G2P));
+        NSF_CUDA_TRY(launch_g2p_latent(g, gp, Xoff, u_n, nN, nS, (float)dt, dnext, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_G2P));
+        if (last && taps) {
+            if (taps->u_n) NSF_CUDA_TRY(cudaMemcpyAsync(taps->u_n, u_n, 12 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
+            if (taps->u_prev) NSF_CUDA_TRY(cudaMemcpyAsync(taps->u_prev, u_prev, 12 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
+            if (taps->u_next_S) NSF_CUDA_TRY(cudaMemcpyAsync(taps->u_next_S, dnext, 12 * (size_t)nS, cudaMemcpyDeviceToDevice, s));
+            if (taps->tau6) NSF_CUDA_TRY(cudaMemcpyAsync(taps->tau6, tau, 24 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
+            if (taps->C9) NSF_CUDA_TRY(cudaMemcpyAsync(taps->C9, C9, 36 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
+        }
+        // 3. network inversion (§5.3), Gauss-Newton from z_n
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GN));
+        for (int it = 0; it < opts->iters; ++it) {
+            const bool fin = it == opts->iters - 1;
+            GnArgs gn;
+            gn.target = dnext;
+            gn.target_ld = nS;
+            gn.z_in = it == 0 ? d_z : zgn;
+            gn.z_out = fin ? d_z : zgn;
+            gn.z_prev_out = fin ? d_z_prev : nullptr;
+            gn.z_first = d_z;
+            gn.z_tap = (last && taps && taps->z_iter) ? taps->z_iter + (size_t)it * r : nullptr;
+            gn.partials = partials;
+            gn.counter = gn_counter;
+            gn.damping = opts->damping;
+            NSF_CUDA_TRY(run_jacobian(f->dev, sc->d_X, nS, nN, gn.z_in, nullptr, nullptr, &gn, d_status, s));
+        }
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_GN));
+        cur ^= 1;
+    }
+    // keep g(X, z_prev) of the returned z_prev in ub[1] for a NSF_LATENT_REUSE_PREV call
+    if (((nsteps - 1) & 1) == 0)
+        NSF_CUDA_TRY(cudaMemcpyAsync(ub[1], ub[0], 12 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
+    return NSF_OK;
+}
+
+nsf_status nsf_project_workspace_size(const nsf_fields *f, int n_S, size_t *bytes) {
+    if (!f || !bytes || n_S < 1) return NSF_ERR_INVALID_ARG;
+    *bytes = project_layout(f, n_S).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x_target, int n_S,
+                       double *d_z_inout, const nsf_gn_opts *opts, double *d_z_iter,
+                       float *d_residual, void *d_ws, size_t ws_bytes, int *d_status,
+                       void *stream) {
+    if (!f || !d_X_S || !d_x_target || n_S < 1 || !d_z_inout || !valid_gn(opts))
+        return NSF_ERR_INVALID_ARG;
+    ProjectLayout L = project_layout(f, n_S);
+    if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    float *target = reinterpret_cast<float *>(base + L.target);
+    float *u = reinterpret_cast<float *>(base + L.u);
+    double *partials = reinterpret_cast<double *>(base + L.partials);
+    int *counter = reinterpret_cast<int *>(base + L.gnctl);
+    const int r = f->desc.r;
+    // residual fields work on displacements: d = x_target - X
+    if (f->dev.residual_g) NSF_CUDA_TRY(axpy(target, d_x_target, d_X_S, -1.f, 3 * n_S, s));
+    else NSF_CUDA_TRY(cudaMemcpyAsync(target, d_x_target, 12 * (size_t)n_S, cudaMemcpyDeviceToDevice, s));
+    for (int it = 0; it < opts->iters; ++it) {
+        GnArgs gn;
+        gn.target = target;
+        gn.target_ld = n_S;
+        gn.z_in = d_z_inout;
+        gn.z_out = d_z_inout;
+        gn.z_prev_out = nullptr;
+        gn.z_first = d_z_inout;
+        gn.z_tap = d_z_iter ? d_z_iter + (size_t)it * r : nullptr;
+        gn.partials = partials;
+        gn.counter = counter;
+        gn.damping = opts->damping;
+        NSF_CUDA_TRY(run_jacobian(f->dev, d_X_S, n_S, n_S, d_z_inout, nullptr, nullptr, &gn, d_status, s));
+    }
+    if (d_residual) {
+        FieldJob job{NSF_FIELD_G, d_z_inout, u};
+        NSF_CUDA_TRY(run_fields(f->dev, d_X_S, n_S, n_S, 1, &job, d_status, s));
+        NSF_CUDA_TRY(axpy(d_residual, u, target, -1.f, 3 * n_S, s));
+    }
+    return NSF_OK;
+}
+
+nsf_status nsf_full_workspace_size(const nsf_grid_desc *g, int n, size_t *bytes) {
+    if (!valid_grid(g) || n < 1 || !bytes) return NSF_ERR_INVALID_ARG;
+    *bytes = full_layout(g, n).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
+                         const nsf_particles *P, double dt, double t0, int nsteps, void *d_ws,
+                         size_t ws_bytes, int *d_status, const nsf_full_taps *taps,
+                         void *stream) {
+    if (!valid_grid(grid) || !mat || !P || P->n < 1 || !P->d_x || !P->d_v || !P->d_C || !P->d_F ||
+        nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0) ||
+        !(P->mass > 0.f) || !(P->vol0 > 0.f) || !(mat->E > 0.f) || !(mat->nu > -1.f) ||
+        !(mat->nu < 0.5f))
+        return NSF_ERR_INVALID_ARG;
+    if (mat->model != NSF_NEO_HOOKEAN) return NSF_ERR_UNSUPPORTED;
+    if (nsteps == 0) return NSF_OK;
+    FullLayout L = full_layout(grid, P->n);
+    if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    GridWs g = grid_ws(base, L.grid, grid, P->n);
+    GridParams gp = make_params(grid);
+    const float mu = mat->E / (2.f * (1.f + mat->nu));
+    const float lam = mat->E * mat->nu / ((1.f + mat->nu) * (1.f - 2.f * mat->nu));
+    for (int step = 0; step < nsteps; ++step) {
+        const bool last = step == nsteps - 1;
+        NSF_CUDA_TRY(launch_bin(g, nullptr, P->d_x, P->n, gp.inv_dx, d_status, s));
+        P2gFullArgs pa;
+        pa.x = P->d_x;
+        pa.v = P->d_v;
+        pa.C = P->d_C;
+        pa.F = P->d_F;
+        pa.tau6 = nullptr;
+        pa.n = P->n;
+        pa.mass = P->mass;
+        pa.vol0 = P->vol0;
+        pa.dt = (float)dt;
+        pa.mu = mu;
+        pa.lam = lam;
+        NSF_CUDA_TRY(launch_p2g_full(g, gp, pa, s));
+        NSF_CUDA_TRY(launch_grid_update(g, gp, (float)dt, t0 + step * dt,
+                                        last && taps ? taps->grid_mp : nullptr,
+                                        last && taps ? taps->grid_v : nullptr, s));
+        G2pFullArgs ga;
+        ga.x = P->d_x;
+        ga.v = P->d_v;
+        ga.C = P->d_C;
+        ga.F = P->d_F;
+        ga.tau6 = nullptr;
+        ga.n = P->n;
+        ga.dt = (float)dt;
+        ga.model = mat->model;
+        ga.mu = mu;
+        ga.lam = lam;
+        ga.yield_stress = mat->yield_stress;
+        ga.friction_deg = mat->friction_deg;
+        NSF_CUDA_TRY(launch_g2p_full(g, gp, ga, d_status, s));
+    }
+    return NSF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Device helpers shared by the kernels of libnsf.
+#pragma once
+
+#include "internal.h"
+
+namespace nsf {
+
+// First error wins: the status word only moves away from NSF_OK once.
+__device__ __forceinline__ void set_status(int *status, int code) {
+    if (status) atomicCAS(status, NSF_OK, code);
+}
+
+// ELU of the field networks (App. E): a for a > 0, exp(a) - 1 otherwise.
+__device__ __forceinline__ float elu(float a) { return a > 0.f ? a : expm1f(a); }
+// Its derivative, from the pre-activation: 1 for a > 0, exp(a) otherwise.
+__device__ __forceinline__ float elu_grad(float a) { return a > 0.f ? 1.f : expf(a); }
+
+// Upper-triangle (i <= j) packed index of an r x r symmetric matrix.
+__host__ __device__ __forceinline__ int tri_index(int i, int j, int r) {
+    // rows 0 .. i-1 hold r, r-1, ..., r-i+1 entries
+    return i * r - (i * (i - 1)) / 2 + (j - i);
+}
+
+// Quadratic B-spline stencil along one axis (§3.2, b = 2):
+// base = floor(s - 0.5) with s = x / dx, fx = s - base in [0.5, 1.5).
+struct Axis {
+    int base;
+    float fx;
+    float w[3];
+};
+
+__device__ __forceinline__ Axis bspline_axis(float x, float inv_dx) {
+    Axis a;
+    float s = x * inv_dx;
+    a.base = __float2int_rd(s - 0.5f);
+    a.fx = s - (float)a.base;
+    float t0 = 1.5f - a.fx, t1 = a.fx - 1.0f, t2 = a.fx - 0.5f;
+    a.w[0] = 0.5f * t0 * t0;
+    a.w[1] = 0.75f - t1 * t1;
+    a.w[2] = 0.5f * t2 * t2;
+    return a;
+}
+
+// Block-linear address of node (i, j, k) of the workspace grid.
+__device__ __forceinline__ int node_addr(const GridWs &g, int i, int j, int k) {
+    int b = ((i >> 2) * g.nb1 + (j >> 2)) * g.nb2 + (k >> 2);
+    return b * 64 + (((i & 3) * 4 + (j & 3)) * 4 + (k & 3));
+}
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) {
+    return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+}  // namespace nsf

@@ -1,0 +1,173 @@
+// Internal declarations of libnsf shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "nsf.h"
+
+namespace nsf {
+
+constexpr int kMaxR = NSF_MAX_R;
+constexpr int kMaxWidth = NSF_MAX_WIDTH;
+constexpr int kMaxDepth = NSF_MAX_DEPTH;
+constexpr int kOutDim[3] = {3, 6, 9};
+
+// ---------------------------------------------------------------- fields ---
+// One field network in device memory.  FP32 layout (CUDA-core path):
+//   W0  [width][3 + r] row-major (input layer, as given),
+//   Wt[l] for hidden layers l = 1 .. depth-1: transposed, [in = width][out = width],
+//   Wout [out_dim][width] row-major, b[l] biases of layer l (l = 0 .. depth).
+// BF16 layout (tensor-core path): every hidden matrix is also stored as bf16 in
+// the canonical K-major no-swizzle core-matrix order consumed by tcgen05.mma
+// (see fields_tc.cu), and W0 / Wout / biases stay FP32 (W0 and Wout rounded to
+// bf16 values).
+struct FieldDev {
+    int width, depth, out_dim;
+    const float *W0;
+    const float *Wt[kMaxDepth];
+    const float *Wout;
+    const float *b[kMaxDepth + 1];
+    const __nv_bfloat16 *Wtc[kMaxDepth];   // BF16 packed hidden layers (or null)
+    float scale[9], shift[9];
+};
+
+struct FieldsDev {
+    int r;
+    int residual_g;
+    int precision;
+    FieldDev f[3];
+};
+
+// ------------------------------------------------------------- workspace ---
+struct Ctl {
+    int epoch;          // incremented once per MPM step (grid-block stamps)
+    int n_p_atomic;     // particle-block counter filled by the binning pass
+    int n_pblocks;      // active particle blocks of the current step
+    int n_gblocks;      // active grid blocks of the current step
+    int gn_counter;     // arrival counter of the fused Gauss-Newton solve
+    int pad[3];
+};
+
+// Sparse-in-use, dense-in-address background grid.  Nodes are stored
+// block-linear: 4x4x4-node blocks, block (bx, by, bz) at
+// ((bx * nb1 + by) * nb2 + bz), node (lx, ly, lz) inside at (lx * 4 + ly) * 4 + lz.
+struct GridWs {
+    int n0, n1, n2;
+    int nb0, nb1, nb2, nblocks;
+    float4 *acc;        // (m, p) accumulators; all zero between steps
+    float4 *vel;        // (v, m) after the grid update; valid on touched blocks
+    int *gstamp;        // epoch stamp of each grid block
+    int *cnt;           // particles per particle block; all zero between steps
+    int *blk_slot;      // particle block -> slot in plist
+    int *plist;         // active particle blocks (slot order)
+    int *pcount;        // particles per slot
+    int *poff;          // first sorted index per slot
+    int *glist;         // active grid blocks
+    int *key;           // particle -> particle block (or -1)
+    int *rank;          // particle -> rank inside its block
+    int *perm;          // sorted index -> particle
+    Ctl *ctl;
+    int max_p, max_pblocks, max_gblocks;
+};
+
+struct GridParams {
+    float dx, inv_dx;
+    float gx, gy, gz;
+    int wall_cells;
+    int blade_enable;
+    float blade_x, blade_z0, blade_vz;
+};
+
+// ------------------------------------------------------------- launchers ---
+// All return cudaGetLastError() of their launches.
+
+// Field evaluation on n points for up to 4 (field, z) jobs (value only).
+struct FieldJob {
+    int field;
+    const double *z;
+    float *out;          // [out_dim][ld]; for a residual g this is the displacement u
+};
+
+// Value + forward-mode Jacobian of g on n points.
+//  - eval mode (gn == null): writes u [3][n] (if u) and dudz [3][r][n] (if dudz).
+//  - Gauss-Newton mode (gn != null): per-CTA float64 partial normal
+//    equations, and the last CTA to finish solves and updates z.
+struct GnArgs {
+    const float *target;      // [3][target_ld] target displacement d (x^{n+1} - X for residual g)
+    int target_ld;
+    const double *z_in;       // z used by this iteration
+    double *z_out;            // z after this iteration
+    double *z_prev_out;       // if non-null: receives z_first (last iteration of a latent step)
+    const double *z_first;    // z at the start of the step
+    double *z_tap;            // [r] optional copy of z_out
+    double *partials;         // [grid][gn_partial_stride(r)]
+    int *counter;             // arrival counter, zero before and after
+    double damping;
+};
+int gn_partial_stride(int r);
+
+// CUDA-core FP32 path (fields_simt.cu).
+int jac_grid_size_simt(const FieldsDev &fd, int n);
+cudaError_t launch_fields_simt(const FieldsDev &fd, const float *X, int n, int ld,
+                               int njobs, const FieldJob *jobs, int *status,
+                               cudaStream_t s);
+cudaError_t launch_jacobian_simt(const FieldsDev &fd, const float *X, int n, int ld,
+                                 const double *z, float *u, float *dudz,
+                                 const GnArgs *gn, int *status, cudaStream_t s);
+
+// Tensor-core BF16 path (fields_tc.cu).
+int jac_grid_size_tc(const FieldsDev &fd, int n);
+cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld,
+                             int njobs, const FieldJob *jobs, int *status,
+                             cudaStream_t s);
+cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int ld,
+                               const double *z, float *u, float *dudz,
+                               const GnArgs *gn, int *status, cudaStream_t s);
+
+// MPM transfer kernels.
+cudaError_t launch_bin(const GridWs &g, const float *X, const float *u, int n,
+                       float inv_dx, int *status, cudaStream_t s);
+struct P2gLatentArgs {
+    const float *X;       // [3][n] or null (non-residual g: u is the position)
+    const float *u;       // [3][n] displacement at z_n
+    const float *u_prev;  // [3][n] displacement at z_{n-1}
+    const float *tau6;    // [6][n]
+    const float *C9;      // [9][n]
+    int n;
+    float mass, vol0;
+    float inv_dt;
+    float dt;
+};
+cudaError_t launch_p2g_latent(const GridWs &g, const GridParams &gp,
+                              const P2gLatentArgs &a, cudaStream_t s);
+struct P2gFullArgs {
+    const float *x, *v, *C, *F;   // SoA
+    const float *tau6;            // [6][n] precomputed stress, or null (neo-Hookean inline)
+    int n;
+    float mass, vol0, dt;
+    float mu, lam;
+};
+cudaError_t launch_p2g_full(const GridWs &g, const GridParams &gp,
+                            const P2gFullArgs &a, cudaStream_t s);
+cudaError_t launch_grid_update(const GridWs &g, const GridParams &gp, float dt,
+                               double t, float *tap_mp, float *tap_v,
+                               cudaStream_t s);
+cudaError_t launch_g2p_latent(const GridWs &g, const GridParams &gp,
+                              const float *X, const float *u, int ld, int n_S,
+                              float dt, float *d_next, int *status, cudaStream_t s);
+struct G2pFullArgs {
+    float *x, *v, *C, *F;
+    float *tau6;                  // [6][n] written for the next step (SVD models) or null
+    int n;
+    float dt;
+    int model;
+    float mu, lam, yield_stress, friction_deg;
+};
+cudaError_t launch_g2p_full(const GridWs &g, const GridParams &gp,
+                            const G2pFullArgs &a, int *status, cudaStream_t s);
+cudaError_t launch_stress(const float *F, float *tau6, int n, int model,
+                          float mu, float lam, cudaStream_t s);
+
+}  // namespace nsf

@@ -1,0 +1,251 @@
+"""GPU parity of one latent step (§5) against the FP64 oracle, stage by stage.
+
+Each stage is compared with the oracle fed the GPU's own inputs to that stage
+(teacher forcing), so every tolerance measures one kernel:
+  fields (§5.1)          1e-5 relative (FP32 fields)
+  P2G grid m, p (§3.3)   1e-5 relative, norm-wise over all nodes
+  grid update v          1e-5 relative
+  G2P x^{n+1} on S       1e-5 dx
+  Gauss-Newton z (§5.3)  1e-4 max(1, |z|_inf)
+and the whole step end to end against the oracle's own step within 1e-4 on z.
+"""
+
+import numpy as np
+import pytest
+
+from _support import aos, grid_desc, oracle_fields, oracle_grid, rel, soa
+from oracle import fields as ofields, latent as olatent, mpm as ompm
+from scenes.synthetic import GridSpec, latent_config1, latent_config3, tiny_latent
+
+pytestmark = pytest.mark.gpu
+
+GRID_TOL = 1e-5
+FIELD_TOL = 1e-5
+Z_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def nsf():
+    import paper_2310_17790_gb300 as m
+    return m
+
+
+def _run_step(nsf, sc, z0, zp, nsteps=1, taps=True, t0=0.0, iters=None):
+    import torch
+    F = nsf.Fields.from_spec(sc.fields)
+    X = soa(sc.X)
+    gd = grid_desc(nsf, sc.grid)
+    st = nsf.LatentStepper(F, X, sc.n_S, sc.mass, sc.vol0, gd)
+    n, nS, r = sc.X.shape[0], sc.n_S, sc.fields.r
+    nodes = int(np.prod(sc.grid.n))
+    iters = sc.gn_iters if iters is None else iters
+    buf = {}
+    tp = None
+    if taps:
+        buf = dict(u_n=torch.zeros(3, n, device="cuda"), u_prev=torch.zeros(3, n, device="cuda"),
+                   tau6=torch.zeros(6, n, device="cuda"), C9=torch.zeros(9, n, device="cuda"),
+                   grid_mp=torch.zeros(nodes * 4, device="cuda"),
+                   grid_v=torch.zeros(nodes * 4, device="cuda"),
+                   u_next_S=torch.zeros(3, nS, device="cuda"),
+                   z_iter=torch.zeros(iters, r, dtype=torch.float64, device="cuda"))
+        tp = nsf._native.nsf_latent_taps()
+        for k, v in buf.items():
+            setattr(tp, k, v.data_ptr())
+    z = torch.tensor(z0, dtype=torch.float64, device="cuda")
+    zpv = torch.tensor(zp, dtype=torch.float64, device="cuda")
+    st.step(z, zpv, sc.dt, t0=t0, nsteps=nsteps, iters=iters, damping=sc.damping, taps=tp)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy().astype(np.float64) for k, v in buf.items()}
+    out["status"] = st.read_status()
+    out["z"] = z.cpu().numpy()
+    out["z_prev"] = zpv.cpu().numpy()
+    return out, st
+
+
+def _check_stages(sc, z0, zp, out, t0=0.0):
+    of = oracle_fields(sc.fields)
+    og = oracle_grid(sc.grid)
+    X = sc.X.astype(np.float64)
+    nS, dt = sc.n_S, sc.dt
+    assert out["status"] == 0
+    # 1. inference (§5.1)
+    inf = olatent.inference(of, X, z0, zp, dt)
+    u_n, u_prev = out["u_n"].T, out["u_prev"].T
+    assert rel(u_n, inf["x_n"] - X) < FIELD_TOL
+    assert rel(u_prev, inf["x_prev"] - X) < FIELD_TOL
+    assert rel(out["tau6"].T, inf["tau6"]) < FIELD_TOL
+    assert rel(out["C9"].T, inf["C9"]) < FIELD_TOL
+    # 2. P2G, teacher-forced from the GPU's field values
+    x_n = X + u_n
+    v_n = (u_n - u_prev) / dt
+    tau = ofields.voigt_to_sym(out["tau6"].T)
+    Cm = out["C9"].T.reshape(-1, 3, 3)
+    m, p, ok = ompm.p2g(x_n, v_n, Cm, tau, sc.mass, sc.vol0, dt, og)
+    assert ok.all()
+    gmp = out["grid_mp"].reshape(*sc.grid.n, 4)
+    assert rel(gmp[..., 0], m) < GRID_TOL
+    assert rel(gmp[..., 1:], p) < GRID_TOL
+    # 3. grid update from the GPU's (m, p)
+    vg = ompm.grid_update(gmp[..., 0], gmp[..., 1:], dt, og, t0)
+    gv = out["grid_v"].reshape(*sc.grid.n, 4)
+    assert rel(gv[..., :3], vg) < GRID_TOL
+    np.testing.assert_array_equal(gv[..., 3], gmp[..., 0])
+    # 4. G2P on S from the GPU's grid velocities
+    x_next, ok = ompm.g2p(x_n[:nS], gv[..., :3], dt, og)
+    assert ok.all()
+    err_dx = np.abs(out["u_next_S"].T - (x_next - X[:nS])).max() / sc.grid.dx
+    assert err_dx < 1e-5, err_dx
+    # 5. Gauss-Newton from the GPU's x^{n+1}
+    z, hist, _ = olatent.gauss_newton(of.g, X[:nS], X[:nS] + out["u_next_S"].T, z0,
+                                      sc.gn_iters, sc.damping)
+    scale = max(1.0, np.abs(z).max())
+    assert np.abs(out["z_iter"] - np.array(hist)).max() < Z_TOL * scale
+    assert np.abs(out["z"] - z).max() < Z_TOL * scale
+    np.testing.assert_array_equal(out["z_prev"], z0)
+    return z
+
+
+def _perturbed_prev(sc, seed, eps=2e-3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return sc.z0 - eps * rng.normal(size=sc.z0.size)
+
+
+def test_latent_step_stages_config1_1024_particles(nsf):
+    sc = latent_config1()
+    zp = _perturbed_prev(sc, 1)
+    out, _ = _run_step(nsf, sc, sc.z0, zp)
+    _check_stages(sc, sc.z0, zp, out)
+    # and end to end against the oracle's own step
+    z_ref, _ = olatent.latent_step(oracle_fields(sc.fields), sc.X.astype(np.float64), sc.n_S,
+                                   sc.mass, sc.vol0, sc.z0, zp, sc.dt, oracle_grid(sc.grid))
+    assert np.abs(out["z"] - z_ref).max() < Z_TOL * max(1.0, np.abs(z_ref).max())
+
+
+@pytest.mark.parametrize("seed,n_N,n_S,r,width,depth,n_grid", [
+    (11, 200, 60, 6, 32, 2, 16), (12, 333, 1, 6, 48, 3, 16), (13, 97, 97, 16, 64, 2, 16),
+    (14, 1500, 150, 3, 32, 3, 32)])
+def test_latent_step_stages_small_scenes(nsf, seed, n_N, n_S, r, width, depth, n_grid):
+    sc = tiny_latent(seed, n_N=n_N, n_S=n_S, r=r, width=width, depth=depth, n_grid=n_grid)
+    zp = _perturbed_prev(sc, seed)
+    out, _ = _run_step(nsf, sc, sc.z0, zp)
+    _check_stages(sc, sc.z0, zp, out)
+
+
+def test_latent_step_with_blade_boundary(nsf):
+    sc = tiny_latent(21, n_N=800, n_S=200, n_grid=32, lo=0.3, hi=0.7)
+    sc.grid = GridSpec(n=(32, 32, 32), dx=1.0 / 32, wall_cells=3,
+                       blade=dict(x=0.5, z0=0.55, vz=-1.0))
+    zp = _perturbed_prev(sc, 21)
+    out, _ = _run_step(nsf, sc, sc.z0, zp, t0=0.01)
+    _check_stages(sc, sc.z0, zp, out, t0=0.01)
+
+
+def test_latent_step_config3_scale_fp32(nsf):
+    # 10,000 integration / 700 sample particles of the 200k slab, 128^3 grid
+    sc = latent_config3(precision="fp32")
+    zp = _perturbed_prev(sc, 3, eps=1e-3)
+    out, _ = _run_step(nsf, sc, sc.z0, zp)
+    _check_stages(sc, sc.z0, zp, out)
+
+
+def test_multi_step_matches_repeated_single_steps(nsf):
+    # nsteps = 3 in one call equals three calls of one step (cache reuse of
+    # g(X, z_n) as the next step's g(X, z_{n-1}))
+    sc = tiny_latent(31, n_N=400, n_S=100)
+    zp = _perturbed_prev(sc, 31)
+    a, _ = _run_step(nsf, sc, sc.z0, zp, nsteps=3, taps=False)
+    z, zpv = sc.z0.copy(), zp.copy()
+    for s in range(3):
+        b, _ = _run_step(nsf, sc, z, zpv, nsteps=1, taps=False, t0=s * sc.dt)
+        z, zpv = b["z"], b["z_prev"]
+    assert np.abs(a["z"] - z).max() < 1e-6
+    assert np.abs(a["z_prev"] - zpv).max() < 1e-6
+
+
+def test_reuse_prev_flag_continues_a_call(nsf):
+    # a 1-step call followed by a NSF_LATENT_REUSE_PREV call equals one 2-step call
+    import torch
+    sc = tiny_latent(32, n_N=350, n_S=90)
+    zp = _perturbed_prev(sc, 32)
+    a, _ = _run_step(nsf, sc, sc.z0, zp, nsteps=2, taps=False)
+    F = nsf.Fields.from_spec(sc.fields)
+    st = nsf.LatentStepper(F, soa(sc.X), sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid))
+    z = torch.tensor(sc.z0, device="cuda"); zpv = torch.tensor(zp, device="cuda")
+    st.step(z, zpv, sc.dt, nsteps=1)
+    st.step(z, zpv, sc.dt, t0=sc.dt, nsteps=1, reuse_prev=True)
+    torch.cuda.synchronize()
+    assert st.read_status() == 0
+    assert np.abs(z.cpu().numpy() - a["z"]).max() < 1e-6
+    assert np.abs(zpv.cpu().numpy() - a["z_prev"]).max() < 1e-6
+
+
+def test_five_steps_track_oracle_trajectory(nsf):
+    # drift of an unpinned multi-step trajectory (reported, loosely bounded)
+    sc = tiny_latent(41, n_N=600, n_S=150)
+    zp = _perturbed_prev(sc, 41)
+    out, _ = _run_step(nsf, sc, sc.z0, zp, nsteps=5, taps=False)
+    of, og = oracle_fields(sc.fields), oracle_grid(sc.grid)
+    z, zpv = sc.z0.copy(), zp.copy()
+    for s in range(5):
+        zn, _ = olatent.latent_step(of, sc.X.astype(np.float64), sc.n_S, sc.mass, sc.vol0, z,
+                                    zpv, sc.dt, og, t=s * sc.dt)
+        z, zpv = zn, z
+    assert np.abs(out["z"] - z).max() < 1e-3 * max(1.0, np.abs(z).max())
+
+
+def test_closed_form_translation_field(nsf):
+    # g = X + z, h = l = 0: the latent step is z_{n+1} = 2 z_n - z_{n-1} + dt^2 g
+    r, width = 3, 16
+    W0 = np.zeros((width, 3 + r)); W0[:3, 3:] = np.eye(3)
+    b0 = np.full(width, 20.0)
+    W1 = np.eye(width); b1 = np.zeros(width)
+    W2 = np.zeros((3, width)); W2[:, :3] = np.eye(3)
+    b2 = np.full(3, -20.0)
+    g = np.concatenate([W0.ravel(), b0, W1.ravel(), b1, W2.ravel(), b2]).astype(np.float32)
+    zeros = lambda od: np.zeros(ofields.n_params(r, width, 2, od), np.float32)
+    F = nsf.Fields(r, width, 2, {"g": g, "h": zeros(6), "l": zeros(9)})
+    import torch
+    rng = np.random.Generator(np.random.PCG64(5))
+    Xn = rng.uniform(0.35, 0.65, size=(500, 3)).astype(np.float32)
+    gd = nsf.grid_desc(16, 1.0 / 16, gravity=(0.0, -3.0, -9.8), wall_cells=0)
+    st = nsf.LatentStepper(F, soa(Xn), 120, 0.01, 1e-5, gd)
+    zp = np.array([0.01, -0.02, 0.005]); zn = np.array([0.012, -0.019, 0.004])
+    z = torch.tensor(zn, device="cuda"); zpv = torch.tensor(zp, device="cuda")
+    dt = 1e-3
+    st.step(z, zpv, dt, nsteps=1, iters=3, damping=1e-6)
+    torch.cuda.synchronize()
+    assert st.read_status() == 0
+    expect = 2 * zn - zp + dt * dt * np.array([0.0, -3.0, -9.8])
+    # FP32 positions near 0.5 carry ~3e-8 absolute rounding
+    assert np.abs(z.cpu().numpy() - expect).max() < 2e-7
+    np.testing.assert_array_equal(zpv.cpu().numpy(), zn)
+
+
+def test_out_of_grid_particle_sets_status(nsf):
+    import torch
+    sc = tiny_latent(51, n_N=100, n_S=20)
+    X = sc.X.copy()
+    X[7] = [0.01, 0.5, 0.5]               # stencil leaves the 16^3 grid
+    F = nsf.Fields.from_spec(sc.fields)
+    st = nsf.LatentStepper(F, soa(X), sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid))
+    z = torch.tensor(sc.z0, device="cuda"); zp = z.clone()
+    st.step(z, zp, sc.dt)
+    torch.cuda.synchronize()
+    assert st.read_status() == nsf._native.NSF_ERR_OUT_OF_GRID
+    assert torch.isfinite(z).all()
+
+
+def test_invalid_arguments_are_rejected(nsf):
+    import torch
+    sc = tiny_latent(61, n_N=50, n_S=10)
+    F = nsf.Fields.from_spec(sc.fields)
+    st = nsf.LatentStepper(F, soa(sc.X), sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid))
+    z = torch.tensor(sc.z0, device="cuda"); zp = z.clone()
+    with pytest.raises(nsf.NsfError):
+        st.step(z, zp, -1e-4)
+    with pytest.raises(nsf.NsfError):
+        st.step(z, zp, sc.dt, iters=0)
+    small = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(nsf.NsfError) as e:
+        nsf.nsf_latent_step(F, st.scene, sc.dt, 0.0, 1, z, zp, nsf.gn_opts(), small, st.status)
+    assert e.value.status == nsf._native.NSF_ERR_WORKSPACE

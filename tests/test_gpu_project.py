@@ -1,0 +1,77 @@
+"""GPU network inversion (§5.3, Eq. 9) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from _support import oracle_fields, soa
+from oracle import latent as olatent
+from scenes.synthetic import make_fields
+
+pytestmark = pytest.mark.gpu
+
+Z_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def nsf():
+    import paper_2310_17790_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("r,n_S,width,depth", [(6, 700, 128, 5), (16, 90, 64, 3), (1, 3, 32, 2),
+                                               (6, 2, 32, 2)])
+def test_project_matches_oracle_gauss_newton(nsf, r, n_S, width, depth):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(200 + r + n_S))
+    spec = make_fields(rng, r, width, depth, "fp32", {"g": 1e-2, "h": 1.0, "l": 1.0})
+    of = oracle_fields(spec)
+    X = rng.uniform(0.3, 0.7, size=(n_S, 3)).astype(np.float32)
+    z_star = rng.normal(0, 0.3, size=r)
+    target = (of.g.value(X, z_star) + 1e-4 * rng.normal(size=(n_S, 3))).astype(np.float32)
+    z0 = z_star + 0.05 * rng.normal(size=r)
+    F = nsf.Fields.from_spec(spec)
+    z = torch.tensor(z0, device="cuda")
+    zi = torch.zeros(5, r, dtype=torch.float64, device="cuda")
+    res = torch.zeros(3, n_S, device="cuda")
+    st = nsf.project(F, soa(X), soa(target), z, iters=5, damping=1e-6, z_iter=zi, residual=res)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    zr, hist, resid = olatent.gauss_newton(of.g, X.astype(np.float64), target.astype(np.float64),
+                                           z0, 5, 1e-6)
+    scale = max(1.0, np.abs(zr).max())
+    assert np.abs(z.cpu().numpy() - zr).max() < Z_TOL * scale
+    assert np.abs(zi.cpu().numpy() - np.array(hist)).max() < Z_TOL * scale
+    assert np.abs(res.cpu().numpy().T - resid).max() < 1e-6
+
+
+def test_project_recovers_zero_residual_code(nsf):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(300))
+    spec = make_fields(rng, 6, 64, 4, "fp32", {"g": 1e-2, "h": 1.0, "l": 1.0})
+    of = oracle_fields(spec)
+    X = rng.uniform(0.3, 0.7, size=(500, 3)).astype(np.float32)
+    z_star = rng.normal(0, 0.3, size=6)
+    target = of.g.value(X, z_star).astype(np.float32)
+    F = nsf.Fields.from_spec(spec)
+    z = torch.tensor(z_star + 0.02 * rng.normal(size=6), device="cuda")
+    st = nsf.project(F, soa(X), soa(target), z, iters=5, damping=1e-6)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    assert np.abs(z.cpu().numpy() - z_star).max() < Z_TOL
+
+
+def test_project_singular_system_sets_status(nsf):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(301))
+    spec = make_fields(rng, 6, 32, 2, "fp32", {"g": 1e-2, "h": 1.0, "l": 1.0})
+    # g ignores z (zero z-columns of its input layer): J = 0 exactly, A = 0
+    W0 = spec.weights["g"][:32 * 9].reshape(32, 9)
+    W0[:, 3:] = 0.0
+    F = nsf.Fields.from_spec(spec)
+    X = rng.uniform(0.3, 0.7, size=(4, 3)).astype(np.float32)
+    z0 = np.zeros(6)
+    z = torch.tensor(z0, device="cuda")
+    st = nsf.project(F, soa(X), soa(X), z, iters=1, damping=0.0)
+    torch.cuda.synchronize()
+    assert st.item() == nsf._native.NSF_ERR_SINGULAR
+    np.testing.assert_array_equal(z.cpu().numpy(), z0)
