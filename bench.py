@@ -345,7 +345,8 @@ def run_oracle(args, budget_s):
                 w[off:off + a * b] = ofields.round_to_bf16(w[off:off + a * b])
                 off += a * b + b
         fl.append(ofields.Field(w, fs.r, fs.width[i], fs.depth[i], ofields.OUT_DIM[k],
-                                fs.out_scale[k], fs.out_shift[k], residual=(k == "g")))
+                                fs.out_scale[k], fs.out_shift[k], residual=(k == "g"),
+                                bf16_operands=(fs.precision == "bf16")))
     of = olatent.Fields(*fl)
     g = sc.grid
     og = ompm.Grid(g.n, g.dx, g.gravity, g.wall_cells, g.blade)

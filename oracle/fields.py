@@ -18,6 +18,14 @@ field is residual when requested: x = X + y.
 The Jacobian dg/dz is the analytic chain rule through the layers (forward mode).
 An independent reverse-mode vector-Jacobian product is provided so that the two
 can pin each other, alongside central finite differences.
+
+BF16 reading.  A field evaluated "in BF16 with FP32 accumulation" multiplies
+bfloat16 operands: its weight matrices are bfloat16 values and every
+activation (or tangent) that enters a matrix product is rounded to bfloat16
+first, while sums, biases and the activation function stay in higher
+precision.  ``Field(..., bf16_operands=True)`` evaluates exactly that
+definition (in float64 otherwise); the caller passes weights already rounded
+with ``round_to_bf16``.
 """
 
 import numpy as np
@@ -76,16 +84,23 @@ def elu_prime(a):
     return np.where(a > 0.0, 1.0, np.exp(np.minimum(a, 0.0)))
 
 
-def mlp_value(layers, inp):
-    """Plain forward pass.  inp: [n, in_dim] -> [n, out_dim]."""
+def _identity(a):
+    return a
+
+
+def mlp_value(layers, inp, op_round=_identity):
+    """Plain forward pass.  inp: [n, in_dim] -> [n, out_dim].
+
+    op_round is applied to every hidden activation before it enters the next
+    matrix product (identity, or round_to_bf16 for the BF16 reading)."""
     h = np.asarray(inp, dtype=np.float64)
     for W, b in layers[:-1]:
-        h = elu(h @ W.T + b)
+        h = op_round(elu(h @ W.T + b))
     W, b = layers[-1]
     return h @ W.T + b
 
 
-def mlp_jvp(layers, inp, tin):
+def mlp_jvp(layers, inp, tin, op_round=_identity):
     """Forward-mode derivative.
 
     inp: [n, in_dim];  tin: [in_dim, k] input tangents (shared by all points).
@@ -98,8 +113,8 @@ def mlp_jvp(layers, inp, tin):
     for W, b in layers[:-1]:
         a = h @ W.T + b
         da = np.einsum("oi,nik->nok", W, t)
-        h = elu(a)
-        t = elu_prime(a)[:, :, None] * da
+        h = op_round(elu(a))
+        t = op_round(elu_prime(a)[:, :, None] * da)
     W, b = layers[-1]
     return h @ W.T + b, np.einsum("oi,nik->nok", W, t)
 
@@ -140,12 +155,13 @@ class Field:
     """
 
     def __init__(self, flat, r, width, depth, out_dim, scale=None, shift=None,
-                 residual=False):
+                 residual=False, bf16_operands=False):
         self.r, self.width, self.depth, self.out_dim = r, width, depth, out_dim
         self.layers = unpack(flat, r, width, depth, out_dim)
         self.scale = np.ones(out_dim) if scale is None else np.asarray(scale, np.float64)[:out_dim]
         self.shift = np.zeros(out_dim) if shift is None else np.asarray(shift, np.float64)[:out_dim]
         self.residual = bool(residual)
+        self.op_round = round_to_bf16 if bf16_operands else _identity
         if self.residual and out_dim != 3:
             raise ValueError("only a 3-output field can be residual")
 
@@ -158,7 +174,7 @@ class Field:
 
     def value(self, X, z):
         X, inp = self._inp(X, z)
-        y = self.shift + self.scale * mlp_value(self.layers, inp)
+        y = self.shift + self.scale * mlp_value(self.layers, inp, self.op_round)
         return X + y if self.residual else y
 
     def value_and_jac_z(self, X, z):
@@ -166,7 +182,7 @@ class Field:
         X, inp = self._inp(X, z)
         tin = np.zeros((3 + self.r, self.r))
         tin[3:, :] = np.eye(self.r)
-        out, dout = mlp_jvp(self.layers, inp, tin)
+        out, dout = mlp_jvp(self.layers, inp, tin, self.op_round)
         y = self.shift + self.scale * out
         J = self.scale[None, :, None] * dout
         return (X + y if self.residual else y), J

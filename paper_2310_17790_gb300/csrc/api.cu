@@ -228,11 +228,12 @@ bool valid_gn(const nsf_gn_opts *o) {
 
 }  // namespace
 
-// Defined in fields_tc.cu: packs one hidden layer [out][in] (fp32 host values)
-// into the bf16 tensor-core operand order; returns the element count written.
+// Defined in fields_tc.cu: the bf16 tensor-core operand order of one matrix
+// [rows][k] (fp32 host values, rows padded with zeros to rows_pad), and the
+// shared memory a field needs on the tensor-core path (0: does not fit).
 namespace nsf {
-size_t tc_pack_size(int width);
-void tc_pack_layer(const float *W, int width, __nv_bfloat16 *dst);
+void tc_pack_matrix(const float *W, int rows, int rows_pad, int k, __nv_bfloat16 *dst);
+size_t tc_smem_bytes(int r, int width, int depth);
 }
 
 extern "C" {
@@ -267,7 +268,7 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
     std::vector<float> fbuf;
     std::vector<__nv_bfloat16> hbuf;
     struct Off {
-        size_t W0, Wout, b[NSF_MAX_DEPTH + 1], Wt[NSF_MAX_DEPTH], Wtc[NSF_MAX_DEPTH];
+        size_t W0, Wout, b[NSF_MAX_DEPTH + 1], Wt[NSF_MAX_DEPTH], blob, blob_elems;
     } off[3];
     auto push = [&](const float *src, size_t count) {
         size_t o = fbuf.size();
@@ -276,10 +277,14 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
         return o;
     };
     auto round_bf16 = [](float v) { return __bfloat162float(__float2bfloat16_rn(v)); };
+    if (bf16)
+        for (int f = 0; f < 3; ++f)
+            if (tc_smem_bytes(r, desc->width[f], desc->depth[f]) == 0) return NSF_ERR_UNSUPPORTED;
     for (int f = 0; f < 3; ++f) {
         const int W = desc->width[f], D = desc->depth[f], od = kOutDim[f];
         const float *src = host_weights[f];
         size_t pos = 0;
+        off[f].blob = hbuf.size();
         for (int l = 0; l <= D; ++l) {
             int in = l == 0 ? 3 + r : W;
             int o = l == D ? od : W;
@@ -293,6 +298,11 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 off[f].W0 = push(Wm.data(), Wm.size());
             } else if (l == D) {
                 off[f].Wout = push(Wm.data(), Wm.size());
+                if (bf16) {
+                    size_t o2 = hbuf.size();
+                    hbuf.resize(o2 + (size_t)16 * W);
+                    tc_pack_matrix(Wm.data(), od, 16, W, hbuf.data() + o2);
+                }
             } else {
                 std::vector<float> Wt((size_t)W * W);
                 for (int j = 0; j < W; ++j)
@@ -300,11 +310,8 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 off[f].Wt[l] = push(Wt.data(), Wt.size());
                 if (bf16) {
                     size_t o2 = hbuf.size();
-                    size_t cnt = tc_pack_size(W);
-                    hbuf.resize(o2 + cnt);
-                    tc_pack_layer(Wm.data(), W, hbuf.data() + o2);
-                    while (hbuf.size() % 128) hbuf.push_back(__float2bfloat16_rn(0.f));
-                    off[f].Wtc[l] = o2;
+                    hbuf.resize(o2 + (size_t)W * W);
+                    tc_pack_matrix(Wm.data(), W, W, W, hbuf.data() + o2);
                 }
             }
             for (int q = 0; q < o; ++q)
@@ -312,6 +319,8 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
             off[f].b[l] = push(src + pos, o);
             pos += o;
         }
+        off[f].blob_elems = hbuf.size() - off[f].blob;
+        while (hbuf.size() % 128) hbuf.push_back(__float2bfloat16_rn(0.f));
     }
     size_t fbytes = fbuf.size() * sizeof(float);
     size_t hbytes = hbuf.size() * sizeof(__nv_bfloat16);
@@ -348,10 +357,9 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
         d.W0 = fb + off[f].W0;
         d.Wout = fb + off[f].Wout;
         for (int l = 0; l <= d.depth; ++l) d.b[l] = fb + off[f].b[l];
-        for (int l = 1; l < d.depth; ++l) {
-            d.Wt[l] = fb + off[f].Wt[l];
-            d.Wtc[l] = bf16 ? hb + off[f].Wtc[l] : nullptr;
-        }
+        for (int l = 1; l < d.depth; ++l) d.Wt[l] = fb + off[f].Wt[l];
+        d.tc_blob = bf16 ? hb + off[f].blob : nullptr;
+        d.tc_blob_bytes = bf16 ? (int)(off[f].blob_elems * sizeof(__nv_bfloat16)) : 0;
         for (int o = 0; o < 9; ++o) {
             d.scale[o] = o < d.out_dim ? desc->out_scale[f][o] : 0.f;
             d.shift[o] = o < d.out_dim ? desc->out_shift[f][o] : 0.f;

@@ -26,7 +26,7 @@ struct GnShared {
 
 // Called by every thread of every CTA after the CTA wrote its partials.
 // Returns after the last CTA has finished the solve (others return at once).
-__device__ void gn_arrive_and_finish(const GnArgs &g, int r, int *status,
+__device__ inline void gn_arrive_and_finish(const GnArgs &g, int r, int *status,
                                      GnShared &sh) {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;

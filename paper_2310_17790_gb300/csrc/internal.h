@@ -19,17 +19,19 @@ constexpr int kOutDim[3] = {3, 6, 9};
 //   W0  [width][3 + r] row-major (input layer, as given),
 //   Wt[l] for hidden layers l = 1 .. depth-1: transposed, [in = width][out = width],
 //   Wout [out_dim][width] row-major, b[l] biases of layer l (l = 0 .. depth).
-// BF16 layout (tensor-core path): every hidden matrix is also stored as bf16 in
-// the canonical K-major no-swizzle core-matrix order consumed by tcgen05.mma
-// (see fields_tc.cu), and W0 / Wout / biases stay FP32 (W0 and Wout rounded to
-// bf16 values).
+// BF16 layout (tensor-core path): one contiguous blob per field holding the
+// hidden matrices l = 1 .. depth-1 and the output matrix (zero-padded to 16
+// rows) as bf16 in the K-major no-swizzle core-matrix order of tcgen05.mma
+// (see fields_tc.cu); it is copied verbatim into shared memory.  W0 and the
+// biases stay FP32 (W0 holding bf16-rounded values).
 struct FieldDev {
     int width, depth, out_dim;
     const float *W0;
     const float *Wt[kMaxDepth];
     const float *Wout;
     const float *b[kMaxDepth + 1];
-    const __nv_bfloat16 *Wtc[kMaxDepth];   // BF16 packed hidden layers (or null)
+    const __nv_bfloat16 *tc_blob;          // BF16 packed weights (or null)
+    int tc_blob_bytes;
     float scale[9], shift[9];
 };
 

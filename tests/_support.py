@@ -24,7 +24,11 @@ def bf16_weights(flat, r, width, depth, out_dim):
     return flat
 
 
-def oracle_fields(spec):
+def oracle_fields(spec, bf16_operands=None):
+    """Oracle fields for a FieldSpec.  A bf16 spec uses bf16-rounded weight
+    matrices and (by default) the BF16 reading of the products."""
+    if bf16_operands is None:
+        bf16_operands = spec.precision == "bf16"
     fs = []
     for i, k in enumerate(FIELD_KEYS):
         w = np.asarray(spec.weights[k], np.float64)
@@ -32,7 +36,8 @@ def oracle_fields(spec):
             w = bf16_weights(w, spec.r, spec.width[i], spec.depth[i], ofields.OUT_DIM[k])
         fs.append(ofields.Field(w, spec.r, spec.width[i], spec.depth[i], ofields.OUT_DIM[k],
                                 spec.out_scale[k], spec.out_shift[k],
-                                residual=(k == "g" and spec.residual_g)))
+                                residual=(k == "g" and spec.residual_g),
+                                bf16_operands=bf16_operands))
     return olatent.Fields(*fs)
 
 

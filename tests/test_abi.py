@@ -16,8 +16,8 @@ HEADER = os.path.join(ROOT, "include", "nsf.h")
 
 @pytest.fixture(scope="module")
 def native():
-    from paper_2310_17790_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2310_17790_gb300 import _native
     return _native
 

@@ -54,7 +54,10 @@ def test_fp32_fields_and_jacobian_match_oracle(nsf, r, width, depth, n):
     of = oracle_fields(spec)
     Xo = X.astype(np.float64)
     xo, Jo = of.g.value_and_jac_z(Xo, z)
-    assert rel(x - Xo, xo - Xo) < FP32_TOL
+    # x = X + u is returned in float32: besides the network error it carries the
+    # rounding of X + u (half an ulp of |x| < 1, <= 6e-8 per coordinate)
+    dx = x - xo
+    assert np.linalg.norm(dx) <= FP32_TOL * np.linalg.norm(xo - Xo) + 6e-8 * np.sqrt(dx.size)
     assert rel(tau, of.h.value(Xo, z)) < FP32_TOL
     assert rel(Cm, of.l.value(Xo, z)) < FP32_TOL
     assert rel(J, Jo) < FP32_TOL
@@ -80,3 +83,29 @@ def test_nonfinite_weights_rejected_on_create(nsf):
     spec.weights["h"][5] = np.nan
     with pytest.raises(nsf.NsfError):
         nsf.Fields.from_spec(spec)
+
+
+@pytest.mark.parametrize("r,width,depth,n", [
+    (6, 128, 5, 1000), (6, 64, 4, 129), (16, 32, 2, 77), (3, 96, 3, 300), (1, 256, 2, 130),
+    (6, (64, 128, 96), (4, 5, 3), 257)])
+def test_bf16_fields_and_jacobian_match_oracle(nsf, r, width, depth, n):
+    """BF16 tensor-core fields: within 2e-2 of the FP64 network on the original
+    float32 weights, and within 2e-3 of the oracle's BF16 reading."""
+    rng = np.random.Generator(np.random.PCG64(500 + r + n))
+    spec = make_fields(rng, r, width, depth, "bf16", {"g": 1e-2, "h": 1e3, "l": 1.0})
+    X = rng.uniform(0.3, 0.7, size=(n, 3)).astype(np.float32)
+    z = rng.normal(0, 0.3, size=r)
+    x, tau, Cm, J = _eval(nsf, spec, X, z)
+    Xo = X.astype(np.float64)
+    exact = oracle_fields(spec)                      # BF16 reading
+    spec32 = make_fields(np.random.Generator(np.random.PCG64(0)), r, width, depth, "fp32",
+                         {"g": 1.0, "h": 1.0, "l": 1.0})
+    spec32.weights, spec32.out_scale, spec32.out_shift = spec.weights, spec.out_scale, spec.out_shift
+    plain = oracle_fields(spec32)                    # FP64 network, float32 weights
+    for of, tol in ((exact, 2e-3), (plain, 2e-2)):
+        xo, Jo = of.g.value_and_jac_z(Xo, z)
+        dx = x - xo
+        assert np.linalg.norm(dx) <= tol * np.linalg.norm(xo - Xo) + 6e-8 * np.sqrt(dx.size)
+        assert rel(tau, of.h.value(Xo, z)) < tol
+        assert rel(Cm, of.l.value(Xo, z)) < tol
+        assert rel(J, Jo) < tol

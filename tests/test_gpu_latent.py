@@ -62,7 +62,7 @@ def _run_step(nsf, sc, z0, zp, nsteps=1, taps=True, t0=0.0, iters=None):
     return out, st
 
 
-def _check_stages(sc, z0, zp, out, t0=0.0):
+def _check_stages(sc, z0, zp, out, t0=0.0, field_tol=FIELD_TOL, z_tol=Z_TOL):
     of = oracle_fields(sc.fields)
     og = oracle_grid(sc.grid)
     X = sc.X.astype(np.float64)
@@ -71,10 +71,10 @@ def _check_stages(sc, z0, zp, out, t0=0.0):
     # 1. inference (§5.1)
     inf = olatent.inference(of, X, z0, zp, dt)
     u_n, u_prev = out["u_n"].T, out["u_prev"].T
-    assert rel(u_n, inf["x_n"] - X) < FIELD_TOL
-    assert rel(u_prev, inf["x_prev"] - X) < FIELD_TOL
-    assert rel(out["tau6"].T, inf["tau6"]) < FIELD_TOL
-    assert rel(out["C9"].T, inf["C9"]) < FIELD_TOL
+    assert rel(u_n, inf["x_n"] - X) < field_tol
+    assert rel(u_prev, inf["x_prev"] - X) < field_tol
+    assert rel(out["tau6"].T, inf["tau6"]) < field_tol
+    assert rel(out["C9"].T, inf["C9"]) < field_tol
     # 2. P2G, teacher-forced from the GPU's field values
     x_n = X + u_n
     v_n = (u_n - u_prev) / dt
@@ -99,8 +99,9 @@ def _check_stages(sc, z0, zp, out, t0=0.0):
     z, hist, _ = olatent.gauss_newton(of.g, X[:nS], X[:nS] + out["u_next_S"].T, z0,
                                       sc.gn_iters, sc.damping)
     scale = max(1.0, np.abs(z).max())
-    assert np.abs(out["z_iter"] - np.array(hist)).max() < Z_TOL * scale
-    assert np.abs(out["z"] - z).max() < Z_TOL * scale
+    print(f"z error vs oracle Gauss-Newton: {np.abs(out['z'] - z).max():.3e}")
+    assert np.abs(out["z_iter"] - np.array(hist)).max() < z_tol * scale
+    assert np.abs(out["z"] - z).max() < z_tol * scale
     np.testing.assert_array_equal(out["z_prev"], z0)
     return z
 
@@ -146,6 +147,21 @@ def test_latent_step_config3_scale_fp32(nsf):
     zp = _perturbed_prev(sc, 3, eps=1e-3)
     out, _ = _run_step(nsf, sc, sc.z0, zp)
     _check_stages(sc, sc.z0, zp, out)
+
+
+@pytest.mark.parametrize("width,depth,r", [(128, 5, 6), (64, 4, 12), (32, 2, 16)])
+def test_latent_step_config3_scale_bf16(nsf, width, depth, r):
+    # BF16 tensor-core fields: stages against the oracle's BF16 reading (bf16
+    # weights and GEMM operands, float64 sums)
+    sc = latent_config3(precision="bf16", width=width, depth=depth)
+    if r != 6:
+        from scenes.synthetic import latent_scene
+        sc = latent_scene(2400 + r, 3000, 300, r, width, depth, "bf16", sc.grid, 5e-5,
+                          X=sc.X[:3000], E=2e5, vol_total=sc.vol0 * 200000,
+                          n_total=200000)
+    zp = _perturbed_prev(sc, 4, eps=1e-3)
+    out, _ = _run_step(nsf, sc, sc.z0, zp)
+    _check_stages(sc, sc.z0, zp, out, field_tol=2e-3, z_tol=1e-3)
 
 
 def test_multi_step_matches_repeated_single_steps(nsf):
@@ -197,10 +213,10 @@ def test_closed_form_translation_field(nsf):
     # g = X + z, h = l = 0: the latent step is z_{n+1} = 2 z_n - z_{n-1} + dt^2 g
     r, width = 3, 16
     W0 = np.zeros((width, 3 + r)); W0[:3, 3:] = np.eye(3)
-    b0 = np.full(width, 20.0)
+    b0 = np.full(width, 1.0)            # keeps every ELU in its linear branch
     W1 = np.eye(width); b1 = np.zeros(width)
     W2 = np.zeros((3, width)); W2[:, :3] = np.eye(3)
-    b2 = np.full(3, -20.0)
+    b2 = np.full(3, -1.0)
     g = np.concatenate([W0.ravel(), b0, W1.ravel(), b1, W2.ravel(), b2]).astype(np.float32)
     zeros = lambda od: np.zeros(ofields.n_params(r, width, 2, od), np.float32)
     F = nsf.Fields(r, width, 2, {"g": g, "h": zeros(6), "l": zeros(9)})
@@ -216,8 +232,8 @@ def test_closed_form_translation_field(nsf):
     torch.cuda.synchronize()
     assert st.read_status() == 0
     expect = 2 * zn - zp + dt * dt * np.array([0.0, -3.0, -9.8])
-    # FP32 positions near 0.5 carry ~3e-8 absolute rounding
-    assert np.abs(z.cpu().numpy() - expect).max() < 2e-7
+    # float32 displacements z + 1 - 1 carry ~1e-7 absolute rounding
+    assert np.abs(z.cpu().numpy() - expect).max() < 5e-7
     np.testing.assert_array_equal(zpv.cpu().numpy(), zn)
 
 

@@ -86,3 +86,27 @@ def test_voigt_roundtrip(rng):
     assert np.allclose(T, np.transpose(T, (0, 2, 1)))
     assert T[0, 1, 2] == t6[0, 3] and T[0, 0, 2] == t6[0, 4] and T[0, 0, 1] == t6[0, 5]
     np.testing.assert_array_equal(fields.sym_to_voigt(T), t6)
+
+
+def test_bf16_operand_reading_against_hand_computed_network():
+    # same network as the layout test, with every GEMM operand rounded to bf16:
+    # the hidden activation is rounded before the output product, the output
+    # itself is not; the tangent is rounded the same way
+    W0 = np.array([[1.0, 0.0, 0.0, 2.0],
+                   [0.0, -1.0, 0.0, 0.0]])
+    b0 = np.array([0.5, -0.25])
+    W1 = np.array([[1.0, 0.0], [0.0, 1.0], [2.0, -3.0]])
+    b1 = np.array([0.1, 0.2, 0.3])
+    flat = np.concatenate([W0.ravel(), b0, W1.ravel(), b1])
+    f = fields.Field(flat, r=1, width=2, depth=1, out_dim=3, residual=False,
+                     bf16_operands=True)
+    X = np.array([[0.2, 0.3, 0.4]])
+    z = np.array([-0.4])
+    a0, a1 = 0.2 + 2 * (-0.4) + 0.5, -0.3 - 0.25
+    h = fields.round_to_bf16(np.array([np.expm1(a0), np.expm1(a1)]))
+    expect = np.array([h[0] + 0.1, h[1] + 0.2, 2 * h[0] - 3 * h[1] + 0.3])
+    np.testing.assert_allclose(f.value(X, z)[0], expect, rtol=1e-15)
+    assert not np.allclose(expect, fields.Field(flat, 1, 2, 1, 3).value(X, z)[0], rtol=1e-6)
+    t0 = fields.round_to_bf16(np.exp(a0) * 2.0)
+    _, J = f.value_and_jac_z(X, z)
+    np.testing.assert_allclose(J[0, :, 0], [t0, 0.0, 2.0 * t0], rtol=1e-15)
