@@ -243,30 +243,38 @@ struct TcJobs {
     FieldJob job[4];
 };
 
+// ELU on the BF16 path: one exponential per element (the result is rounded to
+// bf16 right after, so exp(a) - 1 is as good as expm1 here).
+__device__ __forceinline__ float elu_fast(float a, float &grad) {
+    const float e = __expf(fminf(a, 0.f));
+    grad = a > 0.f ? 1.f : e;
+    return a > 0.f ? a : e - 1.f;
+}
+
 // Activation of one 32-column chunk for all rows: value rows h = ELU(pre),
 // tangent rows h = ELU'(pre of the point's value row) * pre.  In Jacobian mode
-// the value rows publish ELU'(pre) through DV (two named barriers).
+// the value rows publish ELU'(pre) through DV[column][point] (two named
+// barriers; consecutive points are consecutive words, so no bank conflicts).
 template <int MODE>
 __device__ __forceinline__ void activate_chunk(float (&v)[32], bool value_row, int lp,
                                                float *DV) {
+    float g;
     if (MODE == 0) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = elu(v[i]);
+        for (int i = 0; i < 32; ++i) v[i] = elu_fast(v[i], g);
         return;
     }
     if (value_row) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-            const float pre = v[i];
-            const float d = pre > 0.f ? 1.f : __expf(pre);
-            DV[lp * kChunkCols + i] = d;
-            v[i] = pre > 0.f ? pre : expm1f(pre);
+            v[i] = elu_fast(v[i], g);
+            DV[i * (kM / 2) + lp] = g;
         }
     }
     named_sync(1);
     if (!value_row) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] *= DV[lp * kChunkCols + i];
+        for (int i = 0; i < 32; ++i) v[i] *= DV[i * (kM / 2) + lp];
     }
     named_sync(1);
 }
@@ -345,12 +353,9 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         for (int k = 0; k < r; ++k) a = fmaf(W0s[(3 + k) * W + j], (float)z[k], a);
         c0[j] = a;
     }
-    bool ok = mbar_wait(bar_w, 0);
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
-        mbar_wait(bar_w, 0);            // bounded: let the copy land before leaving
-        goto teardown;
-    }
+    bool ok = true;
+    bool weights_ready = false;
+    __syncthreads();
 
     {
         const uint32_t a_addr = smem_u32(A);
@@ -391,6 +396,16 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
             }
             fence_proxy_async();
             __syncthreads();
+            if (!weights_ready) {
+                // the weight copy overlapped the first tile's input layer
+                ok = mbar_wait(bar_w, 0);
+                if (!__syncthreads_and(ok)) {
+                    if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+                    mbar_wait(bar_w, 0);      // bounded: let the copy land before leaving
+                    goto teardown;
+                }
+                weights_ready = true;
+            }
 
             // ---- hidden layers, then the output layer (l == D)
             for (int l = 1; l <= D; ++l) {
@@ -497,6 +512,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     }
 
 teardown:
+    // a CTA must not leave while its weight copy may still be landing
+    if (!weights_ready) mbar_wait(bar_w, 0);
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
