@@ -194,12 +194,20 @@ cudaError_t run_fields(const FieldsDev &fd, const float *X, int n, int ld, int n
     return launch_fields_simt(fd, X, n, ld, njobs, jobs, status, s);
 }
 
+// Evaluation (gn == null) or a whole Gauss-Newton run of gn->iters iterations:
+// one cooperative launch on the tensor-core path, one launch per iteration on
+// the CUDA-core path.
 cudaError_t run_jacobian(const FieldsDev &fd, const float *X, int n, int ld, const double *z,
                          float *u, float *dudz, const GnArgs *gn, int *status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (fd.precision == NSF_PREC_BF16)
         return launch_jacobian_tc(fd, X, n, ld, z, u, dudz, gn, status, s);
-    return launch_jacobian_simt(fd, X, n, ld, z, u, dudz, gn, status, s);
+    if (!gn) return launch_jacobian_simt(fd, X, n, ld, z, u, dudz, nullptr, 0, status, s);
+    for (int it = 0; it < gn->iters; ++it) {
+        cudaError_t e = launch_jacobian_simt(fd, X, n, ld, z, u, dudz, gn, it, status, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 bool valid_fields_desc(const nsf_fields_desc *d) {
@@ -423,7 +431,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
     char *base = static_cast<char *>(d_ws);
     GridWs g = grid_ws(base, L.grid, &sc->grid, sc->n_N);
     GridParams gp = make_params(&sc->grid);
-    const int nN = sc->n_N, nS = sc->n_S, r = f->desc.r;
+    const int nN = sc->n_N, nS = sc->n_S;
     float *ub[2] = {reinterpret_cast<float *>(base + L.u[0]), reinterpret_cast<float *>(base + L.u[1])};
     float *tau = reinterpret_cast<float *>(base + L.tau);
     float *C9 = reinterpret_cast<float *>(base + L.C);
@@ -492,20 +500,21 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         }
         // 3. network inversion (§5.3), Gauss-Newton from z_n
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GN));
-        for (int it = 0; it < opts->iters; ++it) {
-            const bool fin = it == opts->iters - 1;
+        {
             GnArgs gn;
             gn.target = dnext;
             gn.target_ld = nS;
-            gn.z_in = it == 0 ? d_z : zgn;
-            gn.z_out = fin ? d_z : zgn;
-            gn.z_prev_out = fin ? d_z_prev : nullptr;
-            gn.z_first = d_z;
-            gn.z_tap = (last && taps && taps->z_iter) ? taps->z_iter + (size_t)it * r : nullptr;
+            gn.iters = opts->iters;
+            gn.z_start = d_z;
+            gn.z_buf = zgn;
+            gn.z_out = d_z;
+            gn.z_prev_out = d_z_prev;
+            gn.z_taps = (last && taps) ? taps->z_iter : nullptr;
             gn.partials = partials;
             gn.counter = gn_counter;
+            gn.flag = gn_counter + 4;
             gn.damping = opts->damping;
-            NSF_CUDA_TRY(run_jacobian(f->dev, sc->d_X, nS, nN, gn.z_in, nullptr, nullptr, &gn, d_status, s));
+            NSF_CUDA_TRY(run_jacobian(f->dev, sc->d_X, nS, nN, d_z, nullptr, nullptr, &gn, d_status, s));
         }
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_GN));
         cur ^= 1;
@@ -535,22 +544,24 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
     float *target = reinterpret_cast<float *>(base + L.target);
     float *u = reinterpret_cast<float *>(base + L.u);
     double *partials = reinterpret_cast<double *>(base + L.partials);
+    double *zgn = reinterpret_cast<double *>(base + L.zgn);
     int *counter = reinterpret_cast<int *>(base + L.gnctl);
-    const int r = f->desc.r;
     // residual fields work on displacements: d = x_target - X
     if (f->dev.residual_g) NSF_CUDA_TRY(axpy(target, d_x_target, d_X_S, -1.f, 3 * n_S, s));
     else NSF_CUDA_TRY(cudaMemcpyAsync(target, d_x_target, 12 * (size_t)n_S, cudaMemcpyDeviceToDevice, s));
-    for (int it = 0; it < opts->iters; ++it) {
+    {
         GnArgs gn;
         gn.target = target;
         gn.target_ld = n_S;
-        gn.z_in = d_z_inout;
+        gn.iters = opts->iters;
+        gn.z_start = d_z_inout;
+        gn.z_buf = zgn;
         gn.z_out = d_z_inout;
         gn.z_prev_out = nullptr;
-        gn.z_first = d_z_inout;
-        gn.z_tap = d_z_iter ? d_z_iter + (size_t)it * r : nullptr;
+        gn.z_taps = d_z_iter;
         gn.partials = partials;
         gn.counter = counter;
+        gn.flag = counter + 4;
         gn.damping = opts->damping;
         NSF_CUDA_TRY(run_jacobian(f->dev, d_X_S, n_S, n_S, d_z_inout, nullptr, nullptr, &gn, d_status, s));
     }

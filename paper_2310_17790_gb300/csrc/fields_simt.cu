@@ -186,7 +186,7 @@ constexpr int kJacRows = 64;
 __global__ void __launch_bounds__(kThreads)
 k_jacobian(const __grid_constant__ FieldsDev fd, const float *__restrict__ X,
            int n, int ld, const double *__restrict__ z, float *u, float *dudz,
-           const __grid_constant__ GnArgs gn, int gn_on, int *status) {
+           const __grid_constant__ GnArgs gn, int gn_on, int it, int *status) {
     extern __shared__ float smem[];
     __shared__ GnShared gsh;
     __shared__ float RES[kJacRows][3];
@@ -248,7 +248,7 @@ k_jacobian(const __grid_constant__ FieldsDev fd, const float *__restrict__ X,
         }
         gn.partials[(size_t)blockIdx.x * stride + e] = s;
     }
-    gn_arrive_and_finish(gn, r, status, gsh);
+    gn_arrive_and_solve(gn, r, it, status, gsh);
 }
 
 }  // namespace
@@ -285,7 +285,7 @@ cudaError_t launch_fields_simt(const FieldsDev &fd, const float *X, int n,
 
 cudaError_t launch_jacobian_simt(const FieldsDev &fd, const float *X, int n,
                                  int ld, const double *z, float *u, float *dudz,
-                                 const GnArgs *gn, int *status,
+                                 const GnArgs *gn, int it, int *status,
                                  cudaStream_t s) {
     const int W = fd.f[NSF_FIELD_G].width;
     size_t sm = SimtSmem<kJacRows>::bytes(W);
@@ -298,7 +298,8 @@ cudaError_t launch_jacobian_simt(const FieldsDev &fd, const float *X, int n,
     int grid = jac_grid_size_simt(fd, n);
     GnArgs g{};
     if (gn) g = *gn;
-    k_jacobian<<<grid, kThreads, sm, s>>>(fd, X, n, ld, z, u, dudz, g, gn ? 1 : 0, status);
+    k_jacobian<<<grid, kThreads, sm, s>>>(fd, X, n, ld, gn ? gn_z_in(*gn, it) : z, u, dudz, g,
+                                          gn ? 1 : 0, it, status);
     return cudaGetLastError();
 }
 

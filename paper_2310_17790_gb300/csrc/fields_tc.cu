@@ -3,8 +3,9 @@
 // Paper §4.2-§4.4, App. E (fields are ELU MLPs on [X; z]), §5.1 (inference on
 // the integration particles) and §5.3 (g and dg/dz on the sample particles).
 //
-// One CTA = one warpgroup (128 threads); thread t owns row t of a 128-row tile
-// and TMEM lane t.  Per tile:
+// One CTA = four warpgroups (512 threads).  Thread t owns row t % 128 of a
+// 128-row tile (TMEM lane t % 128) and the column quarter t / 128 of every
+// layer, so each scheduler keeps four warps to hide latency.  Per tile:
 //   layer 0 (K = 3 + r)  on the CUDA cores in FP32, written as bf16 into the
 //                        shared-memory A operand;
 //   hidden layers        tcgen05.mma M = 128, N = width, K = 16 steps, FP32
@@ -49,14 +50,17 @@ void tc_pack_matrix(const float *W, int rows, int rows_pad, int k, __nv_bfloat16
 namespace {
 
 constexpr int kM = 128;
-constexpr int kThreads = 128;
-constexpr int kChunkCols = 32;
+constexpr int kWG = 4;                    // warpgroups; each owns a quarter of the columns
+constexpr int kWgThreads = 128;
+constexpr int kThreads = kWG * kWgThreads;
+constexpr int kGroup = 16;                // columns per epilogue group
+constexpr int kMaxPts = kM / 2;           // points per tile in Jacobian mode (S >= 2)
 constexpr int kMaxSmem = 227 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 // Shared-memory carve of one CTA (byte offsets from a 1024-aligned base).
 struct TcLayout {
-    int a, blob, w0, c0, bias, dv, o3, part, bars, tmem, total;
+    int a, blob, w0, c0, bias, dv, o3, part, pe, bars, tmem, total;
 };
 
 __host__ __device__ inline int align_to(int v, int a) { return (v + a - 1) / a * a; }
@@ -66,12 +70,13 @@ __host__ __device__ inline TcLayout tc_layout(int r, int W, int D) {
     int o = 0;
     L.a = o;    o = align_to(o + kM * W * 2, 128);
     L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + 16 * W * 2, 128);
-    L.w0 = o;   o = align_to(o + (3 + r) * W * 4, 16);
+    L.w0 = o;   o = align_to(o + (3 + r) * (W + 1) * 4, 16);
     L.c0 = o;   o = align_to(o + W * 4, 16);
     L.bias = o; o = align_to(o + ((D - 1) * W + 16) * 4, 16);
-    L.dv = o;   o = align_to(o + (kM / 2) * kChunkCols * 4, 16);
+    L.dv = o;   o = align_to(o + kWG * kGroup * kMaxPts * 4, 16);
     L.o3 = o;   o = align_to(o + kM * 3 * 4, 16);
     L.part = o; o = align_to(o + (kMaxR * (kMaxR + 1) / 2 + kMaxR + 1) * 8, 16);
+    L.pe = o;   o = align_to(o + kThreads * 8, 16);
     L.bars = o; o = align_to(o + 2 * 8, 16);
     L.tmem = o; o = align_to(o + 16, 16);
     L.total = o + 1024;   // room to align the dynamic base to 1024 bytes
@@ -184,58 +189,38 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+          "=r"(r[7])
         : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-__device__ __forceinline__ void named_sync(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kThreads) : "memory");
-}
-
-// Store 32 activations of row m (columns c0 .. c0 + 31) as bf16 into the A tile.
-__device__ __forceinline__ void store_a_chunk(uint8_t *A, int m, int c0, const float (&h)[32]) {
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const int k8 = (c0 >> 3) + g;
-        uint4 q;
-        __nv_bfloat162 b0 = __floats2bfloat162_rn(h[8 * g + 0], h[8 * g + 1]);
-        __nv_bfloat162 b1 = __floats2bfloat162_rn(h[8 * g + 2], h[8 * g + 3]);
-        __nv_bfloat162 b2 = __floats2bfloat162_rn(h[8 * g + 4], h[8 * g + 5]);
-        __nv_bfloat162 b3 = __floats2bfloat162_rn(h[8 * g + 6], h[8 * g + 7]);
-        q.x = *reinterpret_cast<uint32_t *>(&b0);
-        q.y = *reinterpret_cast<uint32_t *>(&b1);
-        q.z = *reinterpret_cast<uint32_t *>(&b2);
-        q.w = *reinterpret_cast<uint32_t *>(&b3);
-        *reinterpret_cast<uint4 *>(A + ((k8 * (kM / 8) + (m >> 3)) * 128 + (m & 7) * 16)) = q;
-    }
+// Store 8 activations of row m (columns c .. c + 7, c a multiple of 8) as bf16
+// into the A tile: one 16-byte row of one core matrix.
+__device__ __forceinline__ void store_a8(uint8_t *A, int m, int c, const float *h) {
+    uint4 q;
+    __nv_bfloat162 b0 = __floats2bfloat162_rn(h[0], h[1]);
+    __nv_bfloat162 b1 = __floats2bfloat162_rn(h[2], h[3]);
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(h[4], h[5]);
+    __nv_bfloat162 b3 = __floats2bfloat162_rn(h[6], h[7]);
+    q.x = *reinterpret_cast<uint32_t *>(&b0);
+    q.y = *reinterpret_cast<uint32_t *>(&b1);
+    q.z = *reinterpret_cast<uint32_t *>(&b2);
+    q.w = *reinterpret_cast<uint32_t *>(&b3);
+    *reinterpret_cast<uint4 *>(A + (((c >> 3) * (kM / 8) + (m >> 3)) * 128 + (m & 7) * 16)) = q;
 }
 
 struct TcJobs {
@@ -251,33 +236,42 @@ __device__ __forceinline__ float elu_fast(float a, float &grad) {
     return a > 0.f ? a : e - 1.f;
 }
 
-// Activation of one 32-column chunk for all rows: value rows h = ELU(pre),
+// Activation of a group of kGroup columns of one row: value rows h = ELU(pre),
 // tangent rows h = ELU'(pre of the point's value row) * pre.  In Jacobian mode
-// the value rows publish ELU'(pre) through DV[column][point] (two named
-// barriers; consecutive points are consecutive words, so no bank conflicts).
+// the value rows publish ELU'(pre) through DVg[column][point] of their
+// warpgroup (named barrier per warpgroup; consecutive points are consecutive
+// words, so no bank conflicts).
 template <int MODE>
-__device__ __forceinline__ void activate_chunk(float (&v)[32], bool value_row, int lp,
-                                               float *DV) {
+__device__ __forceinline__ void activate_group(float *v, int ncol, bool value_row, int lp,
+                                               float *DVg, int bar_id) {
     float g;
     if (MODE == 0) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = elu_fast(v[i], g);
+        for (int i = 0; i < kGroup; ++i)
+            if (i < ncol) v[i] = elu_fast(v[i], g);
         return;
     }
     if (value_row) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            v[i] = elu_fast(v[i], g);
-            DV[i * (kM / 2) + lp] = g;
-        }
+        for (int i = 0; i < kGroup; ++i)
+            if (i < ncol) {
+                v[i] = elu_fast(v[i], g);
+                DVg[i * kMaxPts + lp] = g;
+            }
     }
-    named_sync(1);
+    named_sync(bar_id, kWgThreads);
     if (!value_row) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] *= DV[i * (kM / 2) + lp];
+        for (int i = 0; i < kGroup; ++i)
+            if (i < ncol) v[i] *= DVg[i * kMaxPts + lp];
     }
-    named_sync(1);
+    named_sync(bar_id, kWgThreads);
 }
+
+// Row of a 128-row tile that holds slot `slot` (0 = value, 1 + k = tangent
+// d/dz_k) of local point q.  Value rows come first so that most warps hold
+// rows of one kind only.
+__device__ __forceinline__ int tile_row(int q, int slot, int P) { return slot * P + q; }
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -286,46 +280,55 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
          const __grid_constant__ GnArgs gn, int gn_on, int *status) {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ GnShared gsh;
-    __shared__ int s_fail;
+    __shared__ int s_abort;
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
 
     const int fidx = MODE == 0 ? jobs.job[blockIdx.y].field : NSF_FIELD_G;
-    const double *z = MODE == 0 ? jobs.job[blockIdx.y].z : zj;
     const FieldDev &F = fd.f[fidx];
     const int W = F.width, D = F.depth, r = fd.r;
     const int S = MODE == 0 ? 1 : 1 + r;
     const int P = kM / S;
     const int tiles = (n + P - 1) / P;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x;
+    const int wg = tid >> 7;                 // warpgroup: column quarter
+    const int row = tid & (kM - 1);          // tile row == TMEM lane
+    const int wq = (tid >> 5) & 3;           // warp within the warpgroup
+    const int cw = W / kWG;                  // columns per warpgroup (multiple of 8)
+    const int cbeg = wg * cw;
+    const int ldw0 = W + 1;                  // padded row of W0s (no bank conflicts)
     const TcLayout L = tc_layout(r, W, D);
     uint8_t *A = base + L.a;
     uint8_t *blob = base + L.blob;
-    float *W0s = reinterpret_cast<float *>(base + L.w0);     // [3 + r][W]
+    float *W0s = reinterpret_cast<float *>(base + L.w0);     // [3 + r][W + 1]
     float *c0 = reinterpret_cast<float *>(base + L.c0);      // [W]
     float *bias = reinterpret_cast<float *>(base + L.bias);  // [D - 1][W], then out [16]
-    float *DV = reinterpret_cast<float *>(base + L.dv);
+    float *DVg = reinterpret_cast<float *>(base + L.dv) + wg * kGroup * kMaxPts;
     float *O3 = reinterpret_cast<float *>(base + L.o3);      // [128][3]
     double *part = reinterpret_cast<double *>(base + L.part);
+    double *pe = reinterpret_cast<double *>(base + L.pe);    // [kThreads]
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(base + L.bars);
     uint64_t *bar_mma = bar_w + 1;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + L.tmem);
     uint32_t ncols = 32;
     while ((int)ncols < W) ncols <<= 1;
+    const int bar_id = 1 + wg;
+    const int n_iter = (MODE == 1 && gn_on) ? gn.iters : 1;
 
     if (tid == 0) {
-        s_fail = 0;
+        s_abort = 0;
         mbar_init(bar_w, 1);
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tmem_holder, ncols);
+    if (tid < 32) tmem_alloc(tmem_holder, ncols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    // Weights: one bulk copy of the packed blob, issued by thread 0.
+    // Weights: one bulk copy of the packed blob, issued by thread 0; it lands
+    // while the CTA prepares its FP32 data and the first tile's input layer.
     if (tid == 0) {
         const uint32_t bytes = (uint32_t)F.tc_blob_bytes;
         mbar_expect_tx(bar_w, bytes);
@@ -335,69 +338,78 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
             bulk_g2s(blob + off, src + off, len, bar_w);
         }
     }
-    // FP32 side data while the copy is in flight.
     const int in0 = 3 + r;
     for (int idx = tid; idx < in0 * W; idx += kThreads) {
         int d = idx / W, j = idx - d * W;
-        W0s[idx] = F.W0[(size_t)j * in0 + d];
+        W0s[d * ldw0 + j] = F.W0[(size_t)j * in0 + d];
     }
     for (int l = 1; l < D; ++l)
         for (int j = tid; j < W; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
     for (int o = tid; o < 16; o += kThreads) bias[(D - 1) * W + o] = o < F.out_dim ? F.b[D][o] : 0.f;
     const int T = r * (r + 1) / 2, stride = T + r + 1;
-    if (MODE == 1)
-        for (int e = tid; e < stride; e += kThreads) part[e] = 0.0;
-    __syncthreads();
-    for (int j = tid; j < W; j += kThreads) {
-        float a = F.b[0][j];
-        for (int k = 0; k < r; ++k) a = fmaf(W0s[(3 + k) * W + j], (float)z[k], a);
-        c0[j] = a;
-    }
     bool ok = true;
     bool weights_ready = false;
-    __syncthreads();
 
-    {
-        const uint32_t a_addr = smem_u32(A);
-        const uint32_t b_addr = smem_u32(blob);
-        const uint32_t lbo_a = (kM / 8) * 128;
-        const uint32_t lbo_w = (uint32_t)(W / 8) * 128;
-        const uint32_t idesc_h = idesc_bf16(kM, W);
-        const uint32_t idesc_o = idesc_bf16(kM, 16);
-        const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
-        uint32_t phase = 0;
-        const int row = tid;
-        const int lp = row / S, slot = row - lp * S;
-        const bool value_row = slot == 0;
+    const uint32_t a_addr = smem_u32(A);
+    const uint32_t b_addr = smem_u32(blob);
+    const uint32_t lbo_a = (kM / 8) * 128;
+    const uint32_t lbo_w = (uint32_t)(W / 8) * 128;
+    const uint32_t idesc_h = idesc_bf16(kM, W);
+    const uint32_t idesc_o = idesc_bf16(kM, 16);
+    const uint32_t tlane = tmem + ((uint32_t)(wq * 32) << 16);
+    uint32_t phase = 0;
+    // this thread's point and slot
+    const int slot = MODE == 0 ? 0 : row / P;
+    const int lp = MODE == 0 ? row : row - slot * P;
+    const bool value_row = slot == 0;
+    const bool live_row = slot < S;          // rows past P * S are padding
+
+    for (int it = 0; it < n_iter; ++it) {
+        const double *z = MODE == 0 ? jobs.job[blockIdx.y].z
+                                    : (gn_on ? gn_z_in(gn, it) : zj);
+        __syncthreads();
+        for (int j = tid; j < W; j += kThreads) {
+            float a = F.b[0][j];
+            for (int k = 0; k < r; ++k) a = fmaf(W0s[(3 + k) * ldw0 + j], (float)__ldcg(&z[k]), a);
+            c0[j] = a;
+        }
+        if (MODE == 1)
+            for (int e = tid; e < stride; e += kThreads) part[e] = 0.0;
+        __syncthreads();
 
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             const int p0 = tile * P;
             const int p = p0 + lp;
-            const bool valid = lp < P && p < n;
-            // ---- layer 0 on the CUDA cores
+            const bool valid = live_row && lp < P && p < n;
+            // ---- layer 0 on the CUDA cores (this thread: its row, its columns)
             float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (valid && value_row) {
                 x0 = X[p];
                 x1 = X[ld + p];
                 x2 = X[2 * ld + p];
             }
-            for (int cc = 0; cc < W; cc += kChunkCols) {
-                float v[32];
+            const float *w0t = W0s + (live_row && !value_row ? (3 + slot - 1) * ldw0 : 0);
+            for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
+                const int nc = min(kGroup, cbeg + cw - cc);
+                float v[kGroup];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < kGroup; ++i) {
                     const int j = cc + i;
-                    if (value_row)
-                        v[i] = fmaf(W0s[j], x0, fmaf(W0s[W + j], x1, fmaf(W0s[2 * W + j], x2, c0[j])));
-                    else
-                        v[i] = W0s[(3 + slot - 1) * W + j];
+                    if (i < nc) {
+                        if (value_row)
+                            v[i] = fmaf(W0s[j], x0, fmaf(W0s[ldw0 + j], x1,
+                                                         fmaf(W0s[2 * ldw0 + j], x2, c0[j])));
+                        else
+                            v[i] = live_row ? w0t[j] : 0.f;
+                    }
                 }
-                activate_chunk<MODE>(v, value_row, lp, DV);
-                store_a_chunk(A, row, cc, v);
+                activate_group<MODE>(v, nc, value_row, lp, DVg, bar_id);
+                store_a8(A, row, cc, v);
+                if (nc > 8) store_a8(A, row, cc + 8, v + 8);
             }
             fence_proxy_async();
             __syncthreads();
             if (!weights_ready) {
-                // the weight copy overlapped the first tile's input layer
                 ok = mbar_wait(bar_w, 0);
                 if (!__syncthreads_and(ok)) {
                     if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
@@ -432,81 +444,142 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 tc_fence_after();
                 if (!out_layer) {
                     const float *bl = bias + (l - 1) * W;
-                    for (int cc = 0; cc < W; cc += kChunkCols) {
-                        float v[32];
-                        tmem_ld32(tlane + cc, v);
+                    for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
+                        const int nc = min(kGroup, cbeg + cw - cc);
+                        float v[kGroup];
+                        tmem_ld8(tlane + cc, v);
+                        if (nc > 8) tmem_ld8(tlane + cc + 8, v + 8);
+                        tmem_wait_ld();
                         if (value_row) {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) v[i] += bl[cc + i];
+                            for (int i = 0; i < kGroup; ++i)
+                                if (i < nc) v[i] += bl[cc + i];
                         }
-                        activate_chunk<MODE>(v, value_row, lp, DV);
-                        store_a_chunk(A, row, cc, v);
+                        activate_group<MODE>(v, nc, value_row, lp, DVg, bar_id);
+                        store_a8(A, row, cc, v);
+                        if (nc > 8) store_a8(A, row, cc + 8, v + 8);
                     }
                     tc_fence_before();
                     fence_proxy_async();
                     __syncthreads();
                 } else {
-                    float v[16];
-                    tmem_ld16(tlane, v);
-                    tc_fence_before();
                     const float *bo = bias + (D - 1) * W;
                     bool bad = false;
-                    if (MODE == 0) {
-                        const FieldJob &job = jobs.job[blockIdx.y];
-                        if (valid) {
-                            for (int o = 0; o < F.out_dim; ++o) {
-                                float y = fmaf(F.scale[o], v[o] + bo[o], F.shift[o]);
-                                bad |= !isfinite(y);
-                                job.out[(size_t)o * ld + p] = y;
-                            }
-                        }
-                    } else {
+                    if (wg == 0) {
+                        float v[16];
+                        tmem_ld8(tlane, v);
+                        tmem_ld8(tlane + 8, v + 8);
+                        tmem_wait_ld();
+                        if (MODE == 0) {
+                            const FieldJob &job = jobs.job[blockIdx.y];
+                            if (valid) {
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            float y = value_row ? fmaf(F.scale[a], v[a] + bo[a], F.shift[a])
-                                                : F.scale[a] * v[a];
-                            if (valid) bad |= !isfinite(y);
-                            if (valid && value_row) {
-                                if (u) u[(size_t)a * ld + p] = y;
-                                if (gn_on) y -= gn.target[(size_t)a * gn.target_ld + p];
+                                for (int o = 0; o < 9; ++o) {
+                                    if (o < F.out_dim) {
+                                        float y = fmaf(F.scale[o], v[o] + bo[o], F.shift[o]);
+                                        bad |= !isfinite(y);
+                                        job.out[(size_t)o * ld + p] = y;
+                                    }
+                                }
                             }
-                            if (valid && !value_row && dudz)
-                                dudz[(size_t)(a * r + slot - 1) * ld + p] = y;
-                            O3[row * 3 + a] = valid ? y : 0.f;
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                float y = value_row ? fmaf(F.scale[a], v[a] + bo[a], F.shift[a])
+                                                    : F.scale[a] * v[a];
+                                if (valid) bad |= !isfinite(y);
+                                if (valid && value_row) {
+                                    if (u) u[(size_t)a * ld + p] = y;
+                                    if (gn_on) y -= gn.target[(size_t)a * gn.target_ld + p];
+                                }
+                                if (valid && !value_row && dudz)
+                                    dudz[(size_t)(a * r + slot - 1) * ld + p] = y;
+                                O3[row * 3 + a] = valid ? y : 0.f;
+                            }
                         }
                     }
+                    tc_fence_before();
                     if (bad) set_status(status, NSF_ERR_NONFINITE);
                     __syncthreads();
                     if (MODE == 1 && gn_on) {
-                        // float64 partial normal equations of this tile's points
+                        // float64 partial normal equations of this tile's points:
+                        // thread t takes entry e = t % stride for the points
+                        // q = t / stride, + G, ... (G = threads per entry), then
+                        // one thread per entry sums the G partial values in order
                         const int npts = max(0, min(P, n - p0));
-                        for (int e = tid; e < stride; e += kThreads) {
-                            double s = 0.0;
+                        const int G = kThreads / stride;
+                        const int e = tid % stride, g0 = tid / stride;
+                        if (g0 < G) {
+                            int ii = -1, jj = -1;
                             if (e < T) {
                                 int i = 0, off = 0;
                                 while (e >= off + (r - i)) { off += r - i; ++i; }
-                                const int j = i + (e - off);
-                                for (int q = 0; q < npts; ++q)
-                                    for (int a = 0; a < 3; ++a)
-                                        s = fma((double)O3[(q * S + 1 + i) * 3 + a],
-                                                (double)O3[(q * S + 1 + j) * 3 + a], s);
+                                ii = i;
+                                jj = i + (e - off);
                             } else if (e < T + r) {
-                                const int k = e - T;
-                                for (int q = 0; q < npts; ++q)
-                                    for (int a = 0; a < 3; ++a)
-                                        s = fma((double)O3[(q * S + 1 + k) * 3 + a],
-                                                (double)O3[(q * S) * 3 + a], s);
-                            } else {
-                                for (int q = 0; q < npts; ++q)
-                                    for (int a = 0; a < 3; ++a)
-                                        s = fma((double)O3[(q * S) * 3 + a],
-                                                (double)O3[(q * S) * 3 + a], s);
+                                ii = e - T;
                             }
-                            part[e] += s;
+                            double s = 0.0;
+                            for (int q = g0; q < npts; q += G) {
+                                const float *vr = O3 + tile_row(q, 0, P) * 3;
+                                if (e < T) {
+                                    const float *ri = O3 + tile_row(q, 1 + ii, P) * 3;
+                                    const float *rj = O3 + tile_row(q, 1 + jj, P) * 3;
+                                    s = fma((double)ri[0], (double)rj[0], s);
+                                    s = fma((double)ri[1], (double)rj[1], s);
+                                    s = fma((double)ri[2], (double)rj[2], s);
+                                } else if (e < T + r) {
+                                    const float *ri = O3 + tile_row(q, 1 + ii, P) * 3;
+                                    s = fma((double)ri[0], (double)vr[0], s);
+                                    s = fma((double)ri[1], (double)vr[1], s);
+                                    s = fma((double)ri[2], (double)vr[2], s);
+                                } else {
+                                    s = fma((double)vr[0], (double)vr[0], s);
+                                    s = fma((double)vr[1], (double)vr[1], s);
+                                    s = fma((double)vr[2], (double)vr[2], s);
+                                }
+                            }
+                            pe[g0 * stride + e] = s;
+                        }
+                        __syncthreads();
+                        if (tid < stride) {
+                            double s = part[tid];
+                            for (int g = 0; g < G; ++g) s += pe[g * stride + tid];
+                            part[tid] = s;
                         }
                     }
                     __syncthreads();
                 }
+            }
+        }
+
+        if (MODE == 1 && gn_on) {
+            // Gauss-Newton iteration `it`: publish this CTA's partials; the last
+            // CTA to arrive solves and releases the others (grid barrier of a
+            // cooperative launch; every wait is bounded).
+            for (int e = tid; e < stride; e += kThreads)
+                gn.partials[(size_t)blockIdx.x * stride + e] = part[e];
+            const bool last = gn_arrive_and_solve(gn, r, it, status, gsh);
+            if (it + 1 < n_iter) {
+                if (last) {
+                    if (tid == 0) atomicExch(gn.flag, it + 1);
+                } else {
+                    if (tid == 0) {
+                        const unsigned long long t0 = now_ns();
+                        while (atomicAdd(gn.flag, 0) < it + 1) {
+                            if (now_ns() - t0 > kWaitNs) {
+                                set_status(status, NSF_ERR_ITER_CAP);
+                                s_abort = 1;
+                                break;
+                            }
+                        }
+                        __threadfence();
+                    }
+                    __syncthreads();
+                    if (s_abort) goto teardown;
+                }
+            } else if (last && tid == 0) {
+                atomicExch(gn.flag, 0);      // ready for the next launch
             }
         }
     }
@@ -515,14 +588,9 @@ teardown:
     // a CTA must not leave while its weight copy may still be landing
     if (!weights_ready) mbar_wait(bar_w, 0);
     __syncthreads();
-    if (warp == 0) {
+    if (tid < 32) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
-    }
-    if (MODE == 1 && gn_on) {
-        for (int e = tid; e < stride; e += kThreads)
-            gn.partials[(size_t)blockIdx.x * stride + e] = part[e];
-        gn_arrive_and_finish(gn, r, status, gsh);
     }
 }
 
@@ -600,9 +668,21 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
     TcJobs tj{};
     GnArgs g{};
     if (gn) g = *gn;
+    int gn_on = gn ? 1 : 0;
     const int grid = jac_grid_size_tc(fd, n);
-    k_mlp_tc<1><<<grid, kThreads, sm, s>>>(fd, X, n, ld, tj, z, u, dudz, g, gn ? 1 : 0, status);
-    return cudaGetLastError();
+    // The Gauss-Newton run waits between iterations on a grid barrier, so all
+    // CTAs must be co-resident: cooperative launch (one CTA per SM).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = gn_on ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_mlp_tc<1>, fd, X, n, ld, tj, z, u, dudz, g, gn_on, status);
 }
 
 }  // namespace nsf

@@ -1,116 +1,161 @@
 // Gauss-Newton normal equations of the network inversion (§5.3, Eq. 9), in
 // float64, finished by the last CTA of the Jacobian kernel that produced the
-// per-CTA partial sums.
+// per-CTA partial sums of an iteration.
 //
 // Partial layout per CTA (stride gn_partial_stride(r)):
 //   [0, T)            sum_p J_p^T J_p, upper triangle (i <= j), T = r (r + 1) / 2
 //   [T, T + r)        sum_p J_p^T res_p
 //   [T + r]           sum_p |res_p|^2
-// The system (A + damping I) dz = -b is solved by a right-looking Cholesky
-// factorisation with one thread per entry, then column-oriented triangular
-// solves; z_out = z_in + dz.  A non-positive or non-finite pivot sets
-// NSF_ERR_SINGULAR and leaves z unchanged.
+// The system (A + damping I) dz = -b is solved by a column-parallel Cholesky
+// factorisation and two triangular solves; z_new = z + dz.  Dependent float64
+// operations are slow on this part, so every step keeps the chain short: the
+// CTA reduction is a tree, each pivot costs one reciprocal square root
+// (float32 estimate + Newton steps) and no division is used.  A non-positive
+// or non-finite pivot sets NSF_ERR_SINGULAR and leaves z unchanged for that
+// iteration.
 #pragma once
 
 #include "device_common.cuh"
 
 namespace nsf {
 
+// 1 / sqrt(d) for d > 0 in float64: Newton-Raphson on f(y) = y^-2 - d,
+// y <- y (3 - d y^2) / 2, from the float32 reciprocal square root (relative
+// error ~1e-7); one step gives ~1e-14 (quadratic convergence), the second the
+// float64 rounding.  Values outside the float32 range start from the float64
+// library square root instead.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    const float df = (float)d;
+    double y;
+    if (df > 1e-30f && df < 1e30f) y = (double)rsqrtf(df);
+    else y = 1.0 / sqrt(d);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    return y;
+}
+
 struct GnShared {
     double sum[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
+    double red[512];
     double A[kMaxR * kMaxR];
     double y[kMaxR];
+    double inv[kMaxR];
     int singular;
     int is_last;
 };
 
-// Called by every thread of every CTA after the CTA wrote its partials.
-// Returns after the last CTA has finished the solve (others return at once).
-__device__ inline void gn_arrive_and_finish(const GnArgs &g, int r, int *status,
-                                     GnShared &sh) {
+// z used by iteration `it` of a Gauss-Newton run.
+__host__ __device__ __forceinline__ const double *gn_z_in(const GnArgs &g, int it) {
+    return it == 0 ? g.z_start : g.z_buf;
+}
+
+// Called by every thread of every CTA after the CTA wrote its partials of
+// iteration `it`.  The last CTA to arrive solves the system and writes the new
+// z; the function returns true in that CTA only, after the new z is written.
+// Other CTAs return false at once.  blockDim.x must be <= 512.
+__device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *status,
+                                           GnShared &sh) {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
     const int T = r * (r + 1) / 2;
     const int stride = T + r + 1;
+    const int nblk = (int)gridDim.x;
     __threadfence();
     __syncthreads();
     if (tid == 0) {
         int ticket = atomicAdd(g.counter, 1);
-        sh.is_last = (ticket == (int)gridDim.x - 1);
+        sh.is_last = (ticket == nblk - 1);
         sh.singular = 0;
     }
     __syncthreads();
-    if (!sh.is_last) return;
+    if (!sh.is_last) return false;
     __threadfence();
 
-    // Deterministic reduction over CTAs in index order.
-    for (int e = tid; e < stride; e += nthreads) {
+    // Tree reduction over CTAs: thread t sums CTAs c, c + C, ... of entry
+    // e = t % stride (c = t / stride), then the C values of each entry are
+    // combined pairwise in a fixed order (deterministic).
+    const int C = nthreads / stride;
+    const int e_t = tid % stride, c_t = tid / stride;
+    if (c_t < C) {
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&g.partials[(size_t)b * stride + e]);
-        sh.sum[e] = s;
+        for (int b = c_t; b < nblk; b += C) s += __ldcg(&g.partials[(size_t)b * stride + e_t]);
+        sh.red[c_t * stride + e_t] = s;
     }
     __syncthreads();
+    for (int half = 1; half < C; half <<= 1) {
+        if (c_t < C && (c_t % (2 * half)) == 0 && c_t + half < C)
+            sh.red[c_t * stride + e_t] += sh.red[(c_t + half) * stride + e_t];
+        __syncthreads();
+    }
     for (int idx = tid; idx < r * r; idx += nthreads) {
         int i = idx / r, j = idx - i * r;
         int e = i <= j ? tri_index(i, j, r) : tri_index(j, i, r);
-        sh.A[idx] = sh.sum[e] + (i == j ? g.damping : 0.0);
+        sh.A[idx] = sh.red[e] + (i == j ? g.damping : 0.0);
     }
-    for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.sum[T + k];
+    for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.red[T + k];
     __syncthreads();
 
-    // Cholesky A = L L^T, L stored in the lower triangle of A.
+    // Right-looking Cholesky A = L L^T (L in the lower triangle of A).
     for (int j = 0; j < r; ++j) {
         if (tid == 0) {
-            double d = sh.A[j * r + j];
+            const double d = sh.A[j * r + j];
             if (!(d > 0.0) || !isfinite(d)) {
                 sh.singular = 1;
-                sh.A[j * r + j] = 1.0;
             } else {
-                sh.A[j * r + j] = sqrt(d);
+                const double rs = rsqrt_newton(d);
+                sh.inv[j] = rs;
+                sh.A[j * r + j] = d * rs;
             }
         }
         __syncthreads();
         if (sh.singular) break;
-        for (int i = j + 1 + tid; i < r; i += nthreads) sh.A[i * r + j] /= sh.A[j * r + j];
+        for (int i = j + 1 + tid; i < r; i += nthreads) sh.A[i * r + j] *= sh.inv[j];
         __syncthreads();
         const int m = r - j - 1;
         for (int idx = tid; idx < m * m; idx += nthreads) {
-            int i = j + 1 + idx / m, k = j + 1 + idx % m;
-            if (k <= i) sh.A[i * r + k] -= sh.A[i * r + j] * sh.A[k * r + j];
+            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
+            if (k <= i) sh.A[i * r + k] = fma(-sh.A[i * r + j], sh.A[k * r + j], sh.A[i * r + k]);
         }
         __syncthreads();
     }
     const bool singular = sh.singular != 0;
     if (!singular) {
-        // Forward solve L y = -b (column oriented).
-        for (int k = 0; k < r; ++k) {
-            if (tid == 0) sh.y[k] /= sh.A[k * r + k];
+        for (int k = 0; k < r; ++k) {                  // L y = -b
+            if (tid == 0) sh.y[k] *= sh.inv[k];
             __syncthreads();
-            for (int i = k + 1 + tid; i < r; i += nthreads) sh.y[i] -= sh.A[i * r + k] * sh.y[k];
+            for (int i = k + 1 + tid; i < r; i += nthreads)
+                sh.y[i] = fma(-sh.A[i * r + k], sh.y[k], sh.y[i]);
             __syncthreads();
         }
-        // Back solve L^T dz = y.
-        for (int k = r - 1; k >= 0; --k) {
-            if (tid == 0) sh.y[k] /= sh.A[k * r + k];
+        for (int k = r - 1; k >= 0; --k) {             // L^T dz = y
+            if (tid == 0) sh.y[k] *= sh.inv[k];
             __syncthreads();
-            for (int i = tid; i < k; i += nthreads) sh.y[i] -= sh.A[k * r + i] * sh.y[k];
+            for (int i = tid; i < k; i += nthreads)
+                sh.y[i] = fma(-sh.A[k * r + i], sh.y[k], sh.y[i]);
             __syncthreads();
         }
     } else if (tid == 0) {
         set_status(status, NSF_ERR_SINGULAR);
     }
+
+    const bool fin = it == g.iters - 1;
+    const double *zin = gn_z_in(g, it);
+    double *zout = fin ? g.z_out : g.z_buf;
     for (int k = tid; k < r; k += nthreads) {
-        double z0 = __ldcg(&g.z_in[k]);
+        const double z0 = __ldcg(&zin[k]);
         double zn = singular ? z0 : z0 + sh.y[k];
         if (!isfinite(zn)) {
             set_status(status, NSF_ERR_NONFINITE);
             zn = z0;
         }
-        if (g.z_prev_out) g.z_prev_out[k] = __ldcg(&g.z_first[k]);
-        g.z_out[k] = zn;
-        if (g.z_tap) g.z_tap[k] = zn;
+        if (fin && g.z_prev_out) g.z_prev_out[k] = __ldcg(&g.z_start[k]);
+        zout[k] = zn;
+        if (g.z_taps) g.z_taps[(size_t)it * r + k] = zn;
     }
     if (tid == 0) *g.counter = 0;
+    __threadfence();
+    __syncthreads();
+    return true;
 }
 
 }  // namespace nsf

@@ -99,13 +99,15 @@ struct FieldJob {
 struct GnArgs {
     const float *target;      // [3][target_ld] target displacement d (x^{n+1} - X for residual g)
     int target_ld;
-    const double *z_in;       // z used by this iteration
-    double *z_out;            // z after this iteration
-    double *z_prev_out;       // if non-null: receives z_first (last iteration of a latent step)
-    const double *z_first;    // z at the start of the step
-    double *z_tap;            // [r] optional copy of z_out
+    int iters;                // Gauss-Newton iterations of the run
+    const double *z_start;    // z at the start of the run (iteration 0 input)
+    double *z_buf;            // z between iterations (workspace)
+    double *z_out;            // z after the last iteration (may alias z_start)
+    double *z_prev_out;       // if non-null: receives z_start after the last iteration
+    double *z_taps;           // [iters][r] optional copy of z after every iteration
     double *partials;         // [grid][gn_partial_stride(r)]
     int *counter;             // arrival counter, zero before and after
+    int *flag;                // iteration release flag (persistent kernel), zero before and after
     double damping;
 };
 int gn_partial_stride(int r);
@@ -115,15 +117,19 @@ int jac_grid_size_simt(const FieldsDev &fd, int n);
 cudaError_t launch_fields_simt(const FieldsDev &fd, const float *X, int n, int ld,
                                int njobs, const FieldJob *jobs, int *status,
                                cudaStream_t s);
+// Eval mode (gn == null) or one Gauss-Newton iteration `it` (z read from
+// gn_z_in(gn, it)); the host launches it once per iteration.
 cudaError_t launch_jacobian_simt(const FieldsDev &fd, const float *X, int n, int ld,
                                  const double *z, float *u, float *dudz,
-                                 const GnArgs *gn, int *status, cudaStream_t s);
+                                 const GnArgs *gn, int it, int *status, cudaStream_t s);
 
 // Tensor-core BF16 path (fields_tc.cu).
 int jac_grid_size_tc(const FieldsDev &fd, int n);
 cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld,
                              int njobs, const FieldJob *jobs, int *status,
                              cudaStream_t s);
+// Eval mode (gn == null) or all gn->iters Gauss-Newton iterations in one
+// cooperative launch (a grid barrier between iterations).
 cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int ld,
                                const double *z, float *u, float *dudz,
                                const GnArgs *gn, int *status, cudaStream_t s);
