@@ -255,6 +255,33 @@ nsf_status nsf_project(const nsf_fields *fields, const float *d_X_S,
                        float *d_residual, void *d_workspace,
                        size_t workspace_bytes, int *d_status, void *stream);
 
+/*
+ * No-allocation form of nsf_project.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory at the point where
+ * they need the inversion -- an application whose memory manager owns every
+ * device allocation, a real-time loop that must never enter the CUDA
+ * allocator, a plugin with nowhere to keep a workspace alive between calls.
+ *
+ * Same arguments and results as nsf_project minus the workspace.  The scratch
+ * is a fixed array of NSF_PROJECT_STATIC_BYTES bytes inside the library, which
+ * every GPU that loads the library holds until the process exits.  n_S above
+ * NSF_PROJECT_STATIC_MAX_S, or a (fields, n_S) pair whose scratch would exceed
+ * the array, is rejected with NSF_ERR_WORKSPACE before any device work.  The
+ * call allocates nothing: it clears the part of the array it uses on the
+ * caller's stream and then runs nsf_project there.  Its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, so calls that can overlap on the GPU (unordered streams) race
+ * with each other: order them.
+ */
+#define NSF_PROJECT_STATIC_MAX_S 2048
+#define NSF_PROJECT_STATIC_BYTES (1 << 20)
+nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
+                              const float *d_x_target, int n_S,
+                              double *d_z_inout, const nsf_gn_opts *opts,
+                              double *d_z_iter, float *d_residual,
+                              int *d_status, void *stream);
+
 /* Constitutive models of the full-order step (paper App. F; neo-Hookean is the
  * textbook tau = mu (F F^T - I) + lambda ln(J) I).  The two plastic models use
  * the Hencky (StVK, App. F.2) stress of F^E and return-map F in float64. */

@@ -174,6 +174,16 @@ def nsf_project(fields, X_S, x_target, z, opts, workspace, status, z_iter=None,
                             _stream(stream)), "nsf_project")
 
 
+def nsf_project_static(fields, X_S, x_target, z, opts, status, z_iter=None, residual=None,
+                       stream=None):
+    """nsf_project without a workspace: the scratch is a fixed array inside
+    the library (for callers that cannot allocate device memory)."""
+    check(N.lib.nsf_project_static(fields.handle, _ptr(X_S), _ptr(x_target),
+                                   int(X_S.shape[1]), _ptr(z), C.byref(opts), _ptr(z_iter),
+                                   _ptr(residual), _ptr(status), _stream(stream)),
+          "nsf_project_static")
+
+
 def nsf_full_workspace_size(grid, n):
     b = C.c_size_t()
     check(N.lib.nsf_full_workspace_size(C.byref(grid), int(n), C.byref(b)),

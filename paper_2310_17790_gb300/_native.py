@@ -30,6 +30,8 @@ NSF_MAX_R, NSF_MAX_WIDTH, NSF_MAX_DEPTH = 16, 256, 8
 NSF_STAGE_NAMES = ("inference", "bin", "p2g", "grid", "g2p", "gauss_newton")
 NSF_LATENT_STAGES = 6
 NSF_LATENT_REUSE_PREV = 1
+NSF_PROJECT_STATIC_MAX_S = 2048
+NSF_PROJECT_STATIC_BYTES = 1 << 20
 
 
 class nsf_fields_desc(C.Structure):
@@ -93,6 +95,7 @@ SIGNATURES = [
                               C.POINTER(nsf_gn_opts), _P, _S, _P, C.POINTER(nsf_latent_taps), _P]),
     ("nsf_project_workspace_size", _ST, [_P, _I, C.POINTER(_S)]),
     ("nsf_project", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _S, _P, _P]),
+    ("nsf_project_static", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _P]),
     ("nsf_full_workspace_size", _ST, [C.POINTER(nsf_grid_desc), _I, C.POINTER(_S)]),
     ("nsf_full_step", _ST, [C.POINTER(nsf_grid_desc), C.POINTER(nsf_material),
                             C.POINTER(nsf_particles), _D, _D, _I, _P, _S, _P,
