@@ -83,11 +83,14 @@ enum { NSF_PREC_FP32 = 0, NSF_PREC_BF16 = 1 };
  *
  * precision NSF_PREC_FP32: FP32 weights and arithmetic on the CUDA cores.
  * precision NSF_PREC_BF16: weight matrices rounded to bfloat16 (nearest-even),
- *   hidden-layer GEMMs on the tcgen05 tensor cores with FP32 accumulation in
- *   tensor memory; biases, the K = 3 + r input layer, ELU and the output
- *   de-normalisation stay FP32.
+ *   hidden- and output-layer GEMMs on the tcgen05 tensor cores with FP32
+ *   accumulation in tensor memory, activations entering them rounded to bf16;
+ *   the K = 3 + r input layer, ELU and the output de-normalisation stay FP32,
+ *   and biases keep ~16 significant bits (a bf16 head and tail).
  * Limits: 1 <= r <= NSF_MAX_R; width[f] a multiple of 16 in [16, NSF_MAX_WIDTH]
- * (BF16: a multiple of 32 in [32, 256]); 1 <= depth[f] <= NSF_MAX_DEPTH.
+ * (BF16: 64, 128 or 192 for any depth, 256 while the field's weights fit in
+ * shared memory; otherwise nsf_create_fields returns NSF_ERR_UNSUPPORTED);
+ * 1 <= depth[f] <= NSF_MAX_DEPTH.
  */
 typedef struct nsf_fields_desc {
     int r;

@@ -240,7 +240,9 @@ bool valid_gn(const nsf_gn_opts *o) {
 // [rows][k] (fp32 host values, rows padded with zeros to rows_pad), and the
 // shared memory a field needs on the tensor-core path (0: does not fit).
 namespace nsf {
-void tc_pack_matrix(const float *W, int rows, int rows_pad, int k, __nv_bfloat16 *dst);
+size_t tc_layer_elems(int rows_pad, int k);
+void tc_pack_layer(const float *W, const float *b, int rows, int rows_pad, int k,
+                   __nv_bfloat16 *dst);
 size_t tc_smem_bytes(int r, int width, int depth);
 }
 
@@ -308,8 +310,8 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 off[f].Wout = push(Wm.data(), Wm.size());
                 if (bf16) {
                     size_t o2 = hbuf.size();
-                    hbuf.resize(o2 + (size_t)16 * W);
-                    tc_pack_matrix(Wm.data(), od, 16, W, hbuf.data() + o2);
+                    hbuf.resize(o2 + tc_layer_elems(16, W));
+                    tc_pack_layer(Wm.data(), src + pos, od, 16, W, hbuf.data() + o2);
                 }
             } else {
                 std::vector<float> Wt((size_t)W * W);
@@ -318,8 +320,8 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 off[f].Wt[l] = push(Wt.data(), Wt.size());
                 if (bf16) {
                     size_t o2 = hbuf.size();
-                    hbuf.resize(o2 + (size_t)W * W);
-                    tc_pack_matrix(Wm.data(), W, W, W, hbuf.data() + o2);
+                    hbuf.resize(o2 + tc_layer_elems(W, W));
+                    tc_pack_layer(Wm.data(), src + pos, W, W, W, hbuf.data() + o2);
                 }
             }
             for (int q = 0; q < o; ++q)

@@ -19,11 +19,16 @@
 // records NSF_ERR_ITER_CAP, waits (bounded) for its outstanding operations,
 // frees its tensor memory and returns.
 //
-// Jacobian mode (Gauss-Newton): each point owns S = 1 + r rows, its value row
-// and one forward-mode tangent row per latent component.  Tangent rows share
-// the GEMMs (without bias); their activation is ELU'(a_value) * t, where the
-// value row publishes ELU'(a_value) through shared memory, so only value rows
-// evaluate exp().
+// Biases of the hidden and output layers ride in the MMA: the A operand carries
+// 16 extra K columns, two of them 1 on value rows (0 on tangent rows), and the
+// weight operand holds each bias split into a bf16 head and a bf16 tail there,
+// so the bias keeps ~16 significant bits and the epilogue needs no bias add.
+//
+// Jacobian mode (Gauss-Newton): each point owns L consecutive rows (L the
+// smallest power of two >= 1 + r, so they sit in one warp): its value row and
+// one forward-mode tangent row per latent component.  Tangent rows share the
+// GEMMs (and get no bias); their activation is ELU'(a_value) * t, which they
+// take from their value row by a warp shuffle, so all rows run the same code.
 //
 // Operand layout (K-major, no swizzle): 8-row x 16-byte core matrices stored as
 // contiguous 128-byte blocks.  A (activations, 128 x width): core (m8, k8) at
@@ -36,15 +41,31 @@
 namespace nsf {
 
 // ------------------------------------------------------------ packing ----
-void tc_pack_matrix(const float *W, int rows, int rows_pad, int k, __nv_bfloat16 *dst) {
+// One layer [rows][k] (fp32 host values) and its bias [rows] in the bf16
+// tensor-core operand order, K-major no-swizzle core matrices, with 16 extra K
+// columns: column k holds bf16(b), column k + 1 holds bf16(b - bf16(b)), the
+// rest zero; rows are zero-padded to rows_pad.  Core (n / 8, c / 8) sits at
+// ((c / 8) * rows_pad / 8 + n / 8) * 64 elements.
+size_t tc_layer_elems(int rows_pad, int k) { return (size_t)rows_pad * (k + 16); }
+
+void tc_pack_layer(const float *W, const float *b, int rows, int rows_pad, int k,
+                   __nv_bfloat16 *dst) {
     const int g = rows_pad / 8;
-    for (int n = 0; n < rows_pad; ++n)
-        for (int c = 0; c < k; ++c) {
-            size_t core = (size_t)(c / 8) * g + (n / 8);
-            size_t idx = core * 64 + (n % 8) * 8 + (c % 8);
-            float v = n < rows ? W[(size_t)n * k + c] : 0.f;
-            dst[idx] = __float2bfloat16_rn(v);
+    const int ka = k + 16;
+    for (int n = 0; n < rows_pad; ++n) {
+        const float bias = n < rows ? b[n] : 0.f;
+        const __nv_bfloat16 head = __float2bfloat16_rn(bias);
+        const __nv_bfloat16 tail = __float2bfloat16_rn(bias - __bfloat162float(head));
+        for (int c = 0; c < ka; ++c) {
+            __nv_bfloat16 v;
+            if (c < k) v = __float2bfloat16_rn(n < rows ? W[(size_t)n * k + c] : 0.f);
+            else if (c == k) v = head;
+            else if (c == k + 1) v = tail;
+            else v = __float2bfloat16_rn(0.f);
+            const size_t core = (size_t)(c / 8) * g + (n / 8);
+            dst[core * 64 + (n % 8) * 8 + (c % 8)] = v;
         }
+    }
 }
 
 namespace {
@@ -54,26 +75,25 @@ constexpr int kWG = 4;                    // warpgroups; each owns a quarter of 
 constexpr int kWgThreads = 128;
 constexpr int kThreads = kWG * kWgThreads;
 constexpr int kGroup = 16;                // columns per epilogue group
-constexpr int kMaxPts = kM / 2;           // points per tile in Jacobian mode (S >= 2)
 constexpr int kMaxSmem = 227 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 // Shared-memory carve of one CTA (byte offsets from a 1024-aligned base).
 struct TcLayout {
-    int a, blob, w0, c0, bias, dv, o3, part, pe, bars, tmem, total;
+    int a, blob, w0v, w0t, o3, part, pe, bars, tmem, total;
 };
 
 __host__ __device__ inline int align_to(int v, int a) { return (v + a - 1) / a * a; }
 
+// Operand sizes: A is 128 x (W + 16) bf16; each hidden layer W x (W + 16);
+// the output layer 16 x (W + 16).
 __host__ __device__ inline TcLayout tc_layout(int r, int W, int D) {
     TcLayout L;
     int o = 0;
-    L.a = o;    o = align_to(o + kM * W * 2, 128);
-    L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + 16 * W * 2, 128);
-    L.w0 = o;   o = align_to(o + (3 + r) * (W + 1) * 4, 16);
-    L.c0 = o;   o = align_to(o + W * 4, 16);
-    L.bias = o; o = align_to(o + ((D - 1) * W + 16) * 4, 16);
-    L.dv = o;   o = align_to(o + kWG * kGroup * kMaxPts * 4, 16);
+    L.a = o;    o = align_to(o + kM * (W + 16) * 2, 128);
+    L.blob = o; o = align_to(o + (D - 1) * W * (W + 16) * 2 + 16 * (W + 16) * 2, 128);
+    L.w0v = o;  o = align_to(o + W * 16, 16);                 // float4 {w_x, w_y, w_z, c0}
+    L.w0t = o;  o = align_to(o + r * (W + 1) * 4, 16);        // tangent inputs W0[:, 3 + k]
     L.o3 = o;   o = align_to(o + kM * 3 * 4, 16);
     L.part = o; o = align_to(o + (kMaxR * (kMaxR + 1) / 2 + kMaxR + 1) * 8, 16);
     L.pe = o;   o = align_to(o + kThreads * 8, 16);
@@ -204,9 +224,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 // Store 8 activations of row m (columns c .. c + 7, c a multiple of 8) as bf16
 // into the A tile: one 16-byte row of one core matrix.
@@ -236,42 +253,33 @@ __device__ __forceinline__ float elu_fast(float a, float &grad) {
     return a > 0.f ? a : e - 1.f;
 }
 
-// Activation of a group of kGroup columns of one row: value rows h = ELU(pre),
-// tangent rows h = ELU'(pre of the point's value row) * pre.  In Jacobian mode
-// the value rows publish ELU'(pre) through DVg[column][point] of their
-// warpgroup (named barrier per warpgroup; consecutive points are consecutive
-// words, so no bank conflicts).
+// Activation of kGroup pre-activations of one row.  Value rows: ELU.  Tangent
+// rows (Jacobian mode): ELU'(pre-activation of the point's value row) * t, the
+// derivative taken from the value lane `vlane` of the same warp by a shuffle.
+// Every lane runs the same instructions.
 template <int MODE>
-__device__ __forceinline__ void activate_group(float *v, int ncol, bool value_row, int lp,
-                                               float *DVg, int bar_id) {
-    float g;
-    if (MODE == 0) {
+__device__ __forceinline__ void activate_group(float *v, bool value_row, int vlane) {
 #pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < ncol) v[i] = elu_fast(v[i], g);
-        return;
+    for (int i = 0; i < kGroup; ++i) {
+        float g;
+        const float h = elu_fast(v[i], g);
+        if (MODE == 0) {
+            v[i] = h;
+        } else {
+            const float gv = __shfl_sync(0xffffffffu, g, vlane);
+            v[i] = value_row ? h : gv * v[i];
+        }
     }
-    if (value_row) {
-#pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < ncol) {
-                v[i] = elu_fast(v[i], g);
-                DVg[i * kMaxPts + lp] = g;
-            }
-    }
-    named_sync(bar_id, kWgThreads);
-    if (!value_row) {
-#pragma unroll
-        for (int i = 0; i < kGroup; ++i)
-            if (i < ncol) v[i] *= DVg[i * kMaxPts + lp];
-    }
-    named_sync(bar_id, kWgThreads);
 }
 
-// Row of a 128-row tile that holds slot `slot` (0 = value, 1 + k = tangent
-// d/dz_k) of local point q.  Value rows come first so that most warps hold
-// rows of one kind only.
-__device__ __forceinline__ int tile_row(int q, int slot, int P) { return slot * P + q; }
+// Rows per point: 1 in value mode; in Jacobian mode the smallest power of two
+// >= 1 + r, so that a point's rows (value row first) share one warp.
+__host__ __device__ __forceinline__ int rows_per_point(int mode, int r) {
+    if (mode == 0) return 1;
+    int L = 2;
+    while (L < 1 + r) L <<= 1;
+    return L;
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -287,8 +295,9 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const int fidx = MODE == 0 ? jobs.job[blockIdx.y].field : NSF_FIELD_G;
     const FieldDev &F = fd.f[fidx];
     const int W = F.width, D = F.depth, r = fd.r;
-    const int S = MODE == 0 ? 1 : 1 + r;
-    const int P = kM / S;
+    const int KA = W + 16;                   // K of every tensor-core product
+    const int Lp = rows_per_point(MODE, r);
+    const int P = kM / Lp;
     const int tiles = (n + P - 1) / P;
     const int tid = threadIdx.x;
     const int wg = tid >> 7;                 // warpgroup: column quarter
@@ -296,14 +305,12 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const int wq = (tid >> 5) & 3;           // warp within the warpgroup
     const int cw = W / kWG;                  // columns per warpgroup (multiple of 8)
     const int cbeg = wg * cw;
-    const int ldw0 = W + 1;                  // padded row of W0s (no bank conflicts)
+    const int ldt = W + 1;                   // padded row of the tangent inputs
     const TcLayout L = tc_layout(r, W, D);
     uint8_t *A = base + L.a;
     uint8_t *blob = base + L.blob;
-    float *W0s = reinterpret_cast<float *>(base + L.w0);     // [3 + r][W + 1]
-    float *c0 = reinterpret_cast<float *>(base + L.c0);      // [W]
-    float *bias = reinterpret_cast<float *>(base + L.bias);  // [D - 1][W], then out [16]
-    float *DVg = reinterpret_cast<float *>(base + L.dv) + wg * kGroup * kMaxPts;
+    float4 *W0v = reinterpret_cast<float4 *>(base + L.w0v); // [W] {W0[j][0..2], c0[j]}
+    float *W0t = reinterpret_cast<float *>(base + L.w0t);    // [r][W + 1]: W0[j][3 + k]
     float *O3 = reinterpret_cast<float *>(base + L.o3);      // [128][3]
     double *part = reinterpret_cast<double *>(base + L.part);
     double *pe = reinterpret_cast<double *>(base + L.pe);    // [kThreads]
@@ -312,7 +319,6 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + L.tmem);
     uint32_t ncols = 32;
     while ((int)ncols < W) ncols <<= 1;
-    const int bar_id = 1 + wg;
     const int n_iter = (MODE == 1 && gn_on) ? gn.iters : 1;
 
     if (tid == 0) {
@@ -339,13 +345,11 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         }
     }
     const int in0 = 3 + r;
-    for (int idx = tid; idx < in0 * W; idx += kThreads) {
-        int d = idx / W, j = idx - d * W;
-        W0s[d * ldw0 + j] = F.W0[(size_t)j * in0 + d];
+    for (int j = tid; j < W; j += kThreads) {
+        const float *w = F.W0 + (size_t)j * in0;
+        W0v[j] = make_float4(w[0], w[1], w[2], 0.f);
+        for (int k = 0; k < r; ++k) W0t[k * ldt + j] = w[3 + k];
     }
-    for (int l = 1; l < D; ++l)
-        for (int j = tid; j < W; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
-    for (int o = tid; o < 16; o += kThreads) bias[(D - 1) * W + o] = o < F.out_dim ? F.b[D][o] : 0.f;
     const int T = r * (r + 1) / 2, stride = T + r + 1;
     bool ok = true;
     bool weights_ready = false;
@@ -359,10 +363,11 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const uint32_t tlane = tmem + ((uint32_t)(wq * 32) << 16);
     uint32_t phase = 0;
     // this thread's point and slot
-    const int slot = MODE == 0 ? 0 : row / P;
-    const int lp = MODE == 0 ? row : row - slot * P;
+    const int slot = row & (Lp - 1);
+    const int lp = row / Lp;
     const bool value_row = slot == 0;
-    const bool live_row = slot < S;          // rows past P * S are padding
+    const bool live_row = slot < 1 + r;      // rows past 1 + r of a point are padding
+    const int vlane = (row & 31) & ~(Lp - 1);
 
     for (int it = 0; it < n_iter; ++it) {
         const double *z = MODE == 0 ? jobs.job[blockIdx.y].z
@@ -370,8 +375,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         __syncthreads();
         for (int j = tid; j < W; j += kThreads) {
             float a = F.b[0][j];
-            for (int k = 0; k < r; ++k) a = fmaf(W0s[(3 + k) * ldw0 + j], (float)__ldcg(&z[k]), a);
-            c0[j] = a;
+            for (int k = 0; k < r; ++k) a = fmaf(W0t[k * ldt + j], (float)__ldcg(&z[k]), a);
+            W0v[j].w = a;
         }
         if (MODE == 1)
             for (int e = tid; e < stride; e += kThreads) part[e] = 0.0;
@@ -380,7 +385,7 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
             const int p0 = tile * P;
             const int p = p0 + lp;
-            const bool valid = live_row && lp < P && p < n;
+            const bool valid = live_row && p < n;
             // ---- layer 0 on the CUDA cores (this thread: its row, its columns)
             float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (valid && value_row) {
@@ -388,24 +393,30 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 x1 = X[ld + p];
                 x2 = X[2 * ld + p];
             }
-            const float *w0t = W0s + (live_row && !value_row ? (3 + slot - 1) * ldw0 : 0);
+            const float *w0t = W0t + (live_row && !value_row ? (slot - 1) * ldt : 0);
             for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
-                const int nc = min(kGroup, cbeg + cw - cc);
                 float v[kGroup];
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i) {
                     const int j = cc + i;
-                    if (i < nc) {
-                        if (value_row)
-                            v[i] = fmaf(W0s[j], x0, fmaf(W0s[ldw0 + j], x1,
-                                                         fmaf(W0s[2 * ldw0 + j], x2, c0[j])));
-                        else
-                            v[i] = live_row ? w0t[j] : 0.f;
+                    if (value_row) {
+                        const float4 w = W0v[j];
+                        v[i] = fmaf(w.x, x0, fmaf(w.y, x1, fmaf(w.z, x2, w.w)));
+                    } else {
+                        v[i] = live_row ? w0t[j] : 0.f;
                     }
                 }
-                activate_group<MODE>(v, nc, value_row, lp, DVg, bar_id);
+                activate_group<MODE>(v, value_row, vlane);
                 store_a8(A, row, cc, v);
-                if (nc > 8) store_a8(A, row, cc + 8, v + 8);
+                store_a8(A, row, cc + 8, v + 8);
+            }
+            if (wg == 0) {
+                // bias columns of the A operand: 1, 1 on value rows, 0 elsewhere
+                float ones[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                ones[0] = ones[1] = value_row ? 1.f : 0.f;
+                store_a8(A, row, W, ones);
+                ones[0] = ones[1] = 0.f;
+                store_a8(A, row, W + 8, ones);
             }
             fence_proxy_async();
             __syncthreads();
@@ -424,10 +435,10 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 const bool out_layer = l == D;
                 if (tid == 0) {
                     tc_fence_after();
-                    const uint32_t boff = (uint32_t)((l - 1) * W * W * 2);
+                    const uint32_t boff = (uint32_t)((l - 1) * W * KA * 2);
                     const uint32_t lbo_b = out_layer ? 2u * 128u : lbo_w;
                     const uint32_t idesc = out_layer ? idesc_o : idesc_h;
-                    for (int ks = 0; ks < W / 16; ++ks) {
+                    for (int ks = 0; ks < KA / 16; ++ks) {
                         uint64_t ad = smem_desc(a_addr + ks * 2 * lbo_a, lbo_a, 128);
                         uint64_t bd = smem_desc(b_addr + boff + ks * 2 * lbo_b, lbo_b, 128);
                         mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
@@ -443,27 +454,19 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 }
                 tc_fence_after();
                 if (!out_layer) {
-                    const float *bl = bias + (l - 1) * W;
                     for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
-                        const int nc = min(kGroup, cbeg + cw - cc);
                         float v[kGroup];
                         tmem_ld8(tlane + cc, v);
-                        if (nc > 8) tmem_ld8(tlane + cc + 8, v + 8);
+                        tmem_ld8(tlane + cc + 8, v + 8);
                         tmem_wait_ld();
-                        if (value_row) {
-#pragma unroll
-                            for (int i = 0; i < kGroup; ++i)
-                                if (i < nc) v[i] += bl[cc + i];
-                        }
-                        activate_group<MODE>(v, nc, value_row, lp, DVg, bar_id);
+                        activate_group<MODE>(v, value_row, vlane);
                         store_a8(A, row, cc, v);
-                        if (nc > 8) store_a8(A, row, cc + 8, v + 8);
+                        store_a8(A, row, cc + 8, v + 8);
                     }
                     tc_fence_before();
                     fence_proxy_async();
                     __syncthreads();
                 } else {
-                    const float *bo = bias + (D - 1) * W;
                     bool bad = false;
                     if (wg == 0) {
                         float v[16];
@@ -476,7 +479,7 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
 #pragma unroll
                                 for (int o = 0; o < 9; ++o) {
                                     if (o < F.out_dim) {
-                                        float y = fmaf(F.scale[o], v[o] + bo[o], F.shift[o]);
+                                        float y = fmaf(F.scale[o], v[o], F.shift[o]);
                                         bad |= !isfinite(y);
                                         job.out[(size_t)o * ld + p] = y;
                                     }
@@ -485,7 +488,7 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                         } else {
 #pragma unroll
                             for (int a = 0; a < 3; ++a) {
-                                float y = value_row ? fmaf(F.scale[a], v[a] + bo[a], F.shift[a])
+                                float y = value_row ? fmaf(F.scale[a], v[a], F.shift[a])
                                                     : F.scale[a] * v[a];
                                 if (valid) bad |= !isfinite(y);
                                 if (valid && value_row) {
@@ -521,15 +524,15 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                             }
                             double s = 0.0;
                             for (int q = g0; q < npts; q += G) {
-                                const float *vr = O3 + tile_row(q, 0, P) * 3;
+                                const float *vr = O3 + (q * Lp) * 3;
                                 if (e < T) {
-                                    const float *ri = O3 + tile_row(q, 1 + ii, P) * 3;
-                                    const float *rj = O3 + tile_row(q, 1 + jj, P) * 3;
+                                    const float *ri = O3 + (q * Lp + 1 + ii) * 3;
+                                    const float *rj = O3 + (q * Lp + 1 + jj) * 3;
                                     s = fma((double)ri[0], (double)rj[0], s);
                                     s = fma((double)ri[1], (double)rj[1], s);
                                     s = fma((double)ri[2], (double)rj[2], s);
                                 } else if (e < T + r) {
-                                    const float *ri = O3 + tile_row(q, 1 + ii, P) * 3;
+                                    const float *ri = O3 + (q * Lp + 1 + ii) * 3;
                                     s = fma((double)ri[0], (double)vr[0], s);
                                     s = fma((double)ri[1], (double)vr[1], s);
                                     s = fma((double)ri[2], (double)vr[2], s);
@@ -624,12 +627,12 @@ size_t tc_smem_bytes(int r, int width, int depth) {
     TcLayout L = tc_layout(r, width, depth);
     const size_t static_bytes = sizeof(GnShared) + 64;
     if ((size_t)L.total + static_bytes > (size_t)kMaxSmem) return 0;
-    if (width % 32 || width > 256) return 0;
+    if (width % 64 || width > 256) return 0;
     return (size_t)L.total;
 }
 
 int jac_grid_size_tc(const FieldsDev &fd, int n) {
-    const int P = kM / (1 + fd.r);
+    const int P = kM / rows_per_point(1, fd.r);
     const int tiles = (n + P - 1) / P;
     return tiles < sm_count() ? tiles : sm_count();
 }
