@@ -3,9 +3,9 @@
 // Paper §4.2-§4.4, App. E (fields are ELU MLPs on [X; z]), §5.1 (inference on
 // the integration particles) and §5.3 (g and dg/dz on the sample particles).
 //
-// One CTA = four warpgroups (512 threads).  Thread t owns row t % 128 of a
-// 128-row tile (TMEM lane t % 128) and the column quarter t / 128 of every
-// layer, so each scheduler keeps four warps to hide latency.  Per tile:
+// One CTA = eight warpgroups (1024 threads).  Thread t owns row t % 128 of a
+// 128-row tile (TMEM lane t % 128) and the column eighth t / 128 of every
+// layer, so each scheduler keeps eight warps to hide latency.  Per tile:
 //   layer 0 (K = 3 + r)  on the CUDA cores in FP32, written as bf16 into the
 //                        shared-memory A operand;
 //   hidden layers        tcgen05.mma M = 128, N = width, K = 16 steps, FP32
@@ -71,10 +71,10 @@ void tc_pack_layer(const float *W, const float *b, int rows, int rows_pad, int k
 namespace {
 
 constexpr int kM = 128;
-constexpr int kWG = 4;                    // warpgroups; each owns a quarter of the columns
+constexpr int kWG = 8;                    // warpgroups; each owns an eighth of the columns
 constexpr int kWgThreads = 128;
 constexpr int kThreads = kWG * kWgThreads;
-constexpr int kGroup = 16;                // columns per epilogue group
+constexpr int kGroup = 8;                 // columns per epilogue group (one core-matrix row)
 constexpr int kMaxSmem = 227 * 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
@@ -285,7 +285,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
          const __grid_constant__ TcJobs jobs, const double *zj, float *u, float *dudz,
-         const __grid_constant__ GnArgs gn, int gn_on, int *status) {
+         const __grid_constant__ GnArgs gn, int gn_on, int pts_per_tile, int *status) {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ GnShared gsh;
     __shared__ int s_abort;
@@ -297,7 +297,9 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const int W = F.width, D = F.depth, r = fd.r;
     const int KA = W + 16;                   // K of every tensor-core product
     const int Lp = rows_per_point(MODE, r);
-    const int P = kM / Lp;
+    // points per tile: all 128 rows in value mode; in Jacobian mode the host
+    // may use fewer rows per tile to spread a small point set over more SMs
+    const int P = pts_per_tile;
     const int tiles = (n + P - 1) / P;
     const int tid = threadIdx.x;
     const int wg = tid >> 7;                 // warpgroup: column quarter
@@ -350,6 +352,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         W0v[j] = make_float4(w[0], w[1], w[2], 0.f);
         for (int k = 0; k < r; ++k) W0t[k * ldt + j] = w[3 + k];
     }
+    for (int idx = tid; idx < kM * KA / 8; idx += kThreads)
+        reinterpret_cast<uint4 *>(A)[idx] = make_uint4(0u, 0u, 0u, 0u);
     const int T = r * (r + 1) / 2, stride = T + r + 1;
     bool ok = true;
     bool weights_ready = false;
@@ -366,7 +370,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const int slot = row & (Lp - 1);
     const int lp = row / Lp;
     const bool value_row = slot == 0;
-    const bool live_row = slot < 1 + r;      // rows past 1 + r of a point are padding
+    const bool live_row = slot < 1 + r && lp < P;   // padding rows stay zero
+    const bool live_warp = (row & ~31) < P * Lp;     // warps with no tile row skip the epilogue
     const int vlane = (row & 31) & ~(Lp - 1);
 
     for (int it = 0; it < n_iter; ++it) {
@@ -394,7 +399,7 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 x2 = X[2 * ld + p];
             }
             const float *w0t = W0t + (live_row && !value_row ? (slot - 1) * ldt : 0);
-            for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
+            for (int cc = cbeg; live_warp && cc < cbeg + cw; cc += kGroup) {
                 float v[kGroup];
 #pragma unroll
                 for (int i = 0; i < kGroup; ++i) {
@@ -408,9 +413,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 }
                 activate_group<MODE>(v, value_row, vlane);
                 store_a8(A, row, cc, v);
-                store_a8(A, row, cc + 8, v + 8);
             }
-            if (wg == 0) {
+            if (wg == 0 && live_warp) {
                 // bias columns of the A operand: 1, 1 on value rows, 0 elsewhere
                 float ones[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 ones[0] = ones[1] = value_row ? 1.f : 0.f;
@@ -454,21 +458,19 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                 }
                 tc_fence_after();
                 if (!out_layer) {
-                    for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
+                    for (int cc = cbeg; live_warp && cc < cbeg + cw; cc += kGroup) {
                         float v[kGroup];
                         tmem_ld8(tlane + cc, v);
-                        tmem_ld8(tlane + cc + 8, v + 8);
                         tmem_wait_ld();
                         activate_group<MODE>(v, value_row, vlane);
                         store_a8(A, row, cc, v);
-                        store_a8(A, row, cc + 8, v + 8);
                     }
                     tc_fence_before();
                     fence_proxy_async();
                     __syncthreads();
                 } else {
                     bool bad = false;
-                    if (wg == 0) {
+                    if (wg == 0 && live_warp) {
                         float v[16];
                         tmem_ld8(tlane, v);
                         tmem_ld8(tlane + 8, v + 8);
@@ -631,8 +633,22 @@ size_t tc_smem_bytes(int r, int width, int depth) {
     return (size_t)L.total;
 }
 
+// Jacobian mode: points per tile.  A full tile holds 128 / L points; for
+// small point sets fewer points per tile (whole warps of rows) spread the work
+// over more SMs, which shortens the latency of a Gauss-Newton iteration.
+int jac_points_per_tile(const FieldsDev &fd, int n) {
+    const int Lp = rows_per_point(1, fd.r);
+    const int pmax = kM / Lp;
+    const int per_warp = 32 / Lp > 0 ? 32 / Lp : 1;      // points per 32 rows
+    int P = (n + sm_count() - 1) / sm_count();
+    P = (P + per_warp - 1) / per_warp * per_warp;
+    if (P > pmax) P = pmax;
+    if (P < 1) P = 1;
+    return P;
+}
+
 int jac_grid_size_tc(const FieldsDev &fd, int n) {
-    const int P = kM / rows_per_point(1, fd.r);
+    const int P = jac_points_per_tile(fd, n);
     const int tiles = (n + P - 1) / P;
     return tiles < sm_count() ? tiles : sm_count();
 }
@@ -657,7 +673,7 @@ cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld,
     GnArgs none{};
     dim3 grid(per_job, njobs);
     k_mlp_tc<0><<<grid, kThreads, sm, s>>>(fd, X, n, ld, tj, nullptr, nullptr, nullptr, none, 0,
-                                           status);
+                                           kM, status);
     return cudaGetLastError();
 }
 
@@ -685,7 +701,8 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = gn_on ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_mlp_tc<1>, fd, X, n, ld, tj, z, u, dudz, g, gn_on, status);
+    const int P = jac_points_per_tile(fd, n);
+    return cudaLaunchKernelEx(&cfg, k_mlp_tc<1>, fd, X, n, ld, tj, z, u, dudz, g, gn_on, P, status);
 }
 
 }  // namespace nsf

@@ -21,22 +21,21 @@ namespace nsf {
 
 // 1 / sqrt(d) for d > 0 in float64: Newton-Raphson on f(y) = y^-2 - d,
 // y <- y (3 - d y^2) / 2, from the float32 reciprocal square root (relative
-// error ~1e-7); one step gives ~1e-14 (quadratic convergence), the second the
-// float64 rounding.  Values outside the float32 range start from the float64
-// library square root instead.
+// error ~1e-7).  One step squares the error (~1e-14, far below what the
+// Gauss-Newton step needs).  Values outside the float32 range start from the
+// float64 library square root instead.
 __device__ __forceinline__ double rsqrt_newton(double d) {
     const float df = (float)d;
     double y;
     if (df > 1e-30f && df < 1e30f) y = (double)rsqrtf(df);
     else y = 1.0 / sqrt(d);
-    y = y * fma(-0.5 * d * y, y, 1.5);
-    y = y * fma(-0.5 * d * y, y, 1.5);
-    return y;
+    const double hd = -0.5 * d;
+    return y * fma(hd * y, y, 1.5);
 }
 
 struct GnShared {
     double sum[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
-    double red[512];
+    double red[1024];
     double A[kMaxR * kMaxR];
     double y[kMaxR];
     double inv[kMaxR];
@@ -52,7 +51,7 @@ __host__ __device__ __forceinline__ const double *gn_z_in(const GnArgs &g, int i
 // Called by every thread of every CTA after the CTA wrote its partials of
 // iteration `it`.  The last CTA to arrive solves the system and writes the new
 // z; the function returns true in that CTA only, after the new z is written.
-// Other CTAs return false at once.  blockDim.x must be <= 512.
+// Other CTAs return false at once.  blockDim.x must be <= 1024.
 __device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *status,
                                            GnShared &sh) {
     const int tid = threadIdx.x;
@@ -95,48 +94,57 @@ __device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *
     for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.red[T + k];
     __syncthreads();
 
-    // Right-looking Cholesky A = L L^T (L in the lower triangle of A).
-    for (int j = 0; j < r; ++j) {
-        if (tid == 0) {
-            const double d = sh.A[j * r + j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                sh.singular = 1;
-            } else {
-                const double rs = rsqrt_newton(d);
-                sh.inv[j] = rs;
-                sh.A[j * r + j] = d * rs;
+    // Right-looking Cholesky A = L L^T (L in the lower triangle of A) and the
+    // two triangular solves, by warp 0: lane i owns row i, so the steps need
+    // only warp-level synchronisation (r <= 16 <= 32 lanes).
+    if (tid < 32) {
+        const int lane = tid;
+        int singular = 0;
+        for (int j = 0; j < r; ++j) {
+            if (lane == 0) {
+                const double d = sh.A[j * r + j];
+                if (!(d > 0.0) || !isfinite(d)) {
+                    sh.singular = 1;
+                } else {
+                    const double rs = rsqrt_newton(d);
+                    sh.inv[j] = rs;
+                    sh.A[j * r + j] = d * rs;
+                }
             }
+            __syncwarp();
+            if (sh.singular) {
+                singular = 1;
+                break;
+            }
+            const int i = lane;
+            if (i > j && i < r) sh.A[i * r + j] *= sh.inv[j];
+            __syncwarp();
+            if (i > j && i < r) {
+                const double lij = sh.A[i * r + j];
+                for (int k = j + 1; k <= i; ++k)
+                    sh.A[i * r + k] = fma(-lij, sh.A[k * r + j], sh.A[i * r + k]);
+            }
+            __syncwarp();
         }
-        __syncthreads();
-        if (sh.singular) break;
-        for (int i = j + 1 + tid; i < r; i += nthreads) sh.A[i * r + j] *= sh.inv[j];
-        __syncthreads();
-        const int m = r - j - 1;
-        for (int idx = tid; idx < m * m; idx += nthreads) {
-            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
-            if (k <= i) sh.A[i * r + k] = fma(-sh.A[i * r + j], sh.A[k * r + j], sh.A[i * r + k]);
+        if (!singular) {
+            double yi = lane < r ? sh.y[lane] : 0.0;      // -b
+            for (int k = 0; k < r; ++k) {                 // L y = -b
+                const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
+                if (lane == k) yi = yk;
+                else if (lane > k && lane < r) yi = fma(-sh.A[lane * r + k], yk, yi);
+            }
+            for (int k = r - 1; k >= 0; --k) {            // L^T dz = y
+                const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
+                if (lane == k) yi = yk;
+                else if (lane < k) yi = fma(-sh.A[k * r + lane], yk, yi);
+            }
+            if (lane < r) sh.y[lane] = yi;
+        } else if (lane == 0) {
+            set_status(status, NSF_ERR_SINGULAR);
         }
-        __syncthreads();
     }
+    __syncthreads();
     const bool singular = sh.singular != 0;
-    if (!singular) {
-        for (int k = 0; k < r; ++k) {                  // L y = -b
-            if (tid == 0) sh.y[k] *= sh.inv[k];
-            __syncthreads();
-            for (int i = k + 1 + tid; i < r; i += nthreads)
-                sh.y[i] = fma(-sh.A[i * r + k], sh.y[k], sh.y[i]);
-            __syncthreads();
-        }
-        for (int k = r - 1; k >= 0; --k) {             // L^T dz = y
-            if (tid == 0) sh.y[k] *= sh.inv[k];
-            __syncthreads();
-            for (int i = tid; i < k; i += nthreads)
-                sh.y[i] = fma(-sh.A[k * r + i], sh.y[k], sh.y[i]);
-            __syncthreads();
-        }
-    } else if (tid == 0) {
-        set_status(status, NSF_ERR_SINGULAR);
-    }
 
     const bool fin = it == g.iters - 1;
     const double *zin = gn_z_in(g, it);
