@@ -118,7 +118,7 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
 
 struct LatentLayout {
     GridLayout grid;
-    size_t u[2], tau, C, dnext, partials, zgn, gnctl;
+    size_t u[2], tau, C, dnext, partials, zgn, gsum, gnctl;
     size_t total;
 };
 
@@ -136,13 +136,14 @@ LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc) {
                                                  : jac_grid_size_simt(f->dev, sc->n_S);
     L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
     L.zgn = c.take(NSF_MAX_R * 8);
+    L.gsum = c.take((size_t)gn_partial_stride(NSF_MAX_R) * 8);
     L.gnctl = c.take(64);
     L.total = c.off;
     return L;
 }
 
 struct ProjectLayout {
-    size_t target, u, partials, zgn, gnctl, total;
+    size_t target, u, partials, zgn, gsum, gnctl, total;
 };
 
 ProjectLayout project_layout(const nsf_fields *f, int n_S) {
@@ -154,6 +155,7 @@ ProjectLayout project_layout(const nsf_fields *f, int n_S) {
                                                  : jac_grid_size_simt(f->dev, n_S);
     L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
     L.zgn = c.take(NSF_MAX_R * 8);
+    L.gsum = c.take((size_t)gn_partial_stride(NSF_MAX_R) * 8);
     L.gnctl = c.take(64);
     L.total = c.off;
     return L;
@@ -513,6 +515,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
             gn.z_prev_out = d_z_prev;
             gn.z_taps = (last && taps) ? taps->z_iter : nullptr;
             gn.partials = partials;
+            gn.gsum = reinterpret_cast<double *>(base + L.gsum);
             gn.counter = gn_counter;
             gn.flag = gn_counter + 4;
             gn.damping = opts->damping;
@@ -562,6 +565,7 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
         gn.z_prev_out = nullptr;
         gn.z_taps = d_z_iter;
         gn.partials = partials;
+        gn.gsum = reinterpret_cast<double *>(base + L.gsum);
         gn.counter = counter;
         gn.flag = counter + 4;
         gn.damping = opts->damping;

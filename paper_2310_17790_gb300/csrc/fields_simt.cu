@@ -191,6 +191,7 @@ k_jacobian(const __grid_constant__ FieldsDev fd, const float *__restrict__ X,
     __shared__ GnShared gsh;
     __shared__ float RES[kJacRows][3];
     __shared__ float JS[kJacRows][3][kMaxR];
+    __shared__ double PART[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
     const FieldDev &F = fd.f[NSF_FIELD_G];
     const int r = fd.r, S = 1 + r, ppc = kJacRows / S;
     const int W = F.width;
@@ -246,9 +247,10 @@ k_jacobian(const __grid_constant__ FieldsDev fd, const float *__restrict__ X,
                 for (int a = 0; a < 3; ++a)
                     s = fma((double)RES[lp][a], (double)RES[lp][a], s);
         }
-        gn.partials[(size_t)blockIdx.x * stride + e] = s;
+        PART[e] = s;
     }
-    gn_arrive_and_solve(gn, r, it, status, gsh);
+    __syncthreads();
+    gn_arrive_and_solve(gn, r, it, status, gsh, PART);
 }
 
 }  // namespace

@@ -562,9 +562,8 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
             // Gauss-Newton iteration `it`: publish this CTA's partials; the last
             // CTA to arrive solves and releases the others (grid barrier of a
             // cooperative launch; every wait is bounded).
-            for (int e = tid; e < stride; e += kThreads)
-                gn.partials[(size_t)blockIdx.x * stride + e] = part[e];
-            const bool last = gn_arrive_and_solve(gn, r, it, status, gsh);
+            __syncthreads();
+            const bool last = gn_arrive_and_solve(gn, r, it, status, gsh, part);
             if (it + 1 < n_iter) {
                 if (last) {
                     if (tid == 0) atomicExch(gn.flag, it + 1);

@@ -6,13 +6,10 @@
 //   [0, T)            sum_p J_p^T J_p, upper triangle (i <= j), T = r (r + 1) / 2
 //   [T, T + r)        sum_p J_p^T res_p
 //   [T + r]           sum_p |res_p|^2
-// The system (A + damping I) dz = -b is solved by a column-parallel Cholesky
-// factorisation and two triangular solves; z_new = z + dz.  Dependent float64
-// operations are slow on this part, so every step keeps the chain short: the
-// CTA reduction is a tree, each pivot costs one reciprocal square root
-// (float32 estimate + Newton steps) and no division is used.  A non-positive
-// or non-finite pivot sets NSF_ERR_SINGULAR and leaves z unchanged for that
-// iteration.
+// CTAs add their partial sums into one float64 accumulator with atomics; the
+// last CTA to arrive solves (A + damping I) dz = -b (see gn_solve_warp) and
+// sets z_new = z + dz.  A non-positive or non-finite pivot sets
+// NSF_ERR_SINGULAR and leaves z unchanged for that iteration.
 #pragma once
 
 #include "device_common.cuh"
@@ -35,7 +32,6 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 
 struct GnShared {
     double sum[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
-    double red[1024];
     double A[kMaxR * kMaxR];
     double y[kMaxR];
     double inv[kMaxR];
@@ -48,17 +44,64 @@ __host__ __device__ __forceinline__ const double *gn_z_in(const GnArgs &g, int i
     return it == 0 ? g.z_start : g.z_buf;
 }
 
-// Called by every thread of every CTA after the CTA wrote its partials of
-// iteration `it`.  The last CTA to arrive solves the system and writes the new
-// z; the function returns true in that CTA only, after the new z is written.
-// Other CTAs return false at once.  blockDim.x must be <= 1024.
+// float64 solve of A x = y (A: r x r SPD in sh.A, right-hand side in sh.y) by
+// warp 0, lane i owning row i: Cholesky factorisation A = L L^T and the two
+// triangular solves, with warp-level synchronisation only.  Each pivot costs
+// one reciprocal square root (float32 estimate + one Newton step) and no
+// division is used; dependent float64 operations are slow on this part, so
+// the chain is kept to a few operations per column.  Writes x to sh.y;
+// returns 1 if A is not positive definite.
+__device__ inline int gn_solve_warp(GnShared &sh, int r) {
+    const int lane = threadIdx.x & 31;
+    int singular = 0;
+    for (int j = 0; j < r; ++j) {
+        const double d = sh.A[j * r + j];
+        if (!(d > 0.0) || !isfinite(d)) { singular = 1; break; }
+        const double rs = rsqrt_newton(d);
+        if (lane == 0) {
+            sh.inv[j] = rs;
+            sh.A[j * r + j] = d * rs;
+        }
+        if (lane > j && lane < r) sh.A[lane * r + j] *= rs;
+        __syncwarp();
+        if (lane > j && lane < r) {
+            const double lij = sh.A[lane * r + j];
+            for (int k = j + 1; k <= lane; ++k)
+                sh.A[lane * r + k] = fma(-lij, sh.A[k * r + j], sh.A[lane * r + k]);
+        }
+        __syncwarp();
+    }
+    if (singular) return 1;
+    double yi = lane < r ? sh.y[lane] : 0.0;
+    for (int k = 0; k < r; ++k) {                         // L u = y
+        const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
+        if (lane == k) yi = yk;
+        else if (lane > k && lane < r) yi = fma(-sh.A[lane * r + k], yk, yi);
+    }
+    for (int k = r - 1; k >= 0; --k) {                    // L^T x = u
+        const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
+        if (lane == k) yi = yk;
+        else if (lane < k) yi = fma(-sh.A[k * r + lane], yk, yi);
+    }
+    if (lane < r) sh.y[lane] = yi;
+    __syncwarp();
+    return 0;
+}
+
+// Called by every thread of every CTA with the CTA's float64 partial sums of
+// iteration `it` in `part` (shared memory, gn_partial_stride(r) values).  The
+// partials are added into g.gsum with float64 atomics; the last CTA to arrive
+// reads the sums, clears them, solves the system and writes the new z.  The
+// function returns true in that CTA only, after the new z is written; other
+// CTAs return false at once.
 __device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *status,
-                                           GnShared &sh) {
+                                           GnShared &sh, const double *part) {
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
     const int T = r * (r + 1) / 2;
     const int stride = T + r + 1;
     const int nblk = (int)gridDim.x;
+    for (int e = tid; e < stride; e += nthreads) atomicAdd(&g.gsum[e], part[e]);
     __threadfence();
     __syncthreads();
     if (tid == 0) {
@@ -69,78 +112,23 @@ __device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *
     __syncthreads();
     if (!sh.is_last) return false;
     __threadfence();
-
-    // Tree reduction over CTAs: thread t sums CTAs c, c + C, ... of entry
-    // e = t % stride (c = t / stride), then the C values of each entry are
-    // combined pairwise in a fixed order (deterministic).
-    const int C = nthreads / stride;
-    const int e_t = tid % stride, c_t = tid / stride;
-    if (c_t < C) {
-        double s = 0.0;
-        for (int b = c_t; b < nblk; b += C) s += __ldcg(&g.partials[(size_t)b * stride + e_t]);
-        sh.red[c_t * stride + e_t] = s;
+    for (int e = tid; e < stride; e += nthreads) {
+        sh.sum[e] = __ldcg(&g.gsum[e]);
+        g.gsum[e] = 0.0;                   // ready for the next iteration / launch
     }
     __syncthreads();
-    for (int half = 1; half < C; half <<= 1) {
-        if (c_t < C && (c_t % (2 * half)) == 0 && c_t + half < C)
-            sh.red[c_t * stride + e_t] += sh.red[(c_t + half) * stride + e_t];
-        __syncthreads();
-    }
     for (int idx = tid; idx < r * r; idx += nthreads) {
         int i = idx / r, j = idx - i * r;
         int e = i <= j ? tri_index(i, j, r) : tri_index(j, i, r);
-        sh.A[idx] = sh.red[e] + (i == j ? g.damping : 0.0);
+        sh.A[idx] = sh.sum[e] + (i == j ? g.damping : 0.0);
     }
-    for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.red[T + k];
+    for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.sum[T + k];
     __syncthreads();
-
-    // Right-looking Cholesky A = L L^T (L in the lower triangle of A) and the
-    // two triangular solves, by warp 0: lane i owns row i, so the steps need
-    // only warp-level synchronisation (r <= 16 <= 32 lanes).
     if (tid < 32) {
-        const int lane = tid;
-        int singular = 0;
-        for (int j = 0; j < r; ++j) {
-            if (lane == 0) {
-                const double d = sh.A[j * r + j];
-                if (!(d > 0.0) || !isfinite(d)) {
-                    sh.singular = 1;
-                } else {
-                    const double rs = rsqrt_newton(d);
-                    sh.inv[j] = rs;
-                    sh.A[j * r + j] = d * rs;
-                }
-            }
-            __syncwarp();
-            if (sh.singular) {
-                singular = 1;
-                break;
-            }
-            const int i = lane;
-            if (i > j && i < r) sh.A[i * r + j] *= sh.inv[j];
-            __syncwarp();
-            if (i > j && i < r) {
-                const double lij = sh.A[i * r + j];
-                for (int k = j + 1; k <= i; ++k)
-                    sh.A[i * r + k] = fma(-lij, sh.A[k * r + j], sh.A[i * r + k]);
-            }
-            __syncwarp();
-        }
-        if (!singular) {
-            double yi = lane < r ? sh.y[lane] : 0.0;      // -b
-            for (int k = 0; k < r; ++k) {                 // L y = -b
-                const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
-                if (lane == k) yi = yk;
-                else if (lane > k && lane < r) yi = fma(-sh.A[lane * r + k], yk, yi);
-            }
-            for (int k = r - 1; k >= 0; --k) {            // L^T dz = y
-                const double yk = __shfl_sync(0xffffffffu, yi, k) * sh.inv[k];
-                if (lane == k) yi = yk;
-                else if (lane < k) yi = fma(-sh.A[k * r + lane], yk, yi);
-            }
-            if (lane < r) sh.y[lane] = yi;
-        } else if (lane == 0) {
-            set_status(status, NSF_ERR_SINGULAR);
+        const int sing = gn_solve_warp(sh, r);
+        if (tid == 0) {
+            sh.singular = sing;
+            if (sing) set_status(status, NSF_ERR_SINGULAR);
         }
     }
     __syncthreads();

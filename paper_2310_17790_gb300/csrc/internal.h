@@ -105,7 +105,8 @@ struct GnArgs {
     double *z_out;            // z after the last iteration (may alias z_start)
     double *z_prev_out;       // if non-null: receives z_start after the last iteration
     double *z_taps;           // [iters][r] optional copy of z after every iteration
-    double *partials;         // [grid][gn_partial_stride(r)]
+    double *partials;         // [grid][gn_partial_stride(r)] (unused; kept for layout)
+    double *gsum;             // [gn_partial_stride(r)] float64 sums, zero before and after
     int *counter;             // arrival counter, zero before and after
     int *flag;                // iteration release flag (persistent kernel), zero before and after
     double damping;
