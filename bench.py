@@ -237,12 +237,19 @@ def run_gpu(args, rank, world, local):
         roof = {"kernel": dom_name, "bound": "hbm", "achieved": None,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None}
 
+    traffic = load_traffic(KERNEL_OF_STAGE.get(dom_name))
+    roof["traffic"] = traffic
+    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    throughput = run_throughput(args, nsf, fs, dev, peaks, peak_src) if args.precision == "bf16" else None
+
     # e2e: through the public API with host buffers, copies inside the timed region
     e2e = run_e2e(args, nsf, sc, F, gd, dev)
 
     full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
 
-    launches_per_step = 1 + 3 + 1 + 1 + 1 + sc.gn_iters
+    # kernels per step: fields 1, bin 3, P2G 1, grid 1, G2P 1, Gauss-Newton 1
+    # (all iterations in one cooperative launch on the BF16 path)
+    launches_per_step = 8 if args.precision == "bf16" else 7 + sc.gn_iters
     out = {
         "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -254,12 +261,69 @@ def run_gpu(args, rank, world, local):
                    "parallelism": f"replicas{world}", "graph": "one CUDA graph per step"},
         "stages_ms": {names[i]: float(st_ms[i]) for i in range(nst)},
         "roofline": roof,
+        "mlp_throughput": throughput,
         "e2e": e2e,
         "full_order": full,
         "gpu_launches": launches_per_step * K,
         "status": status,
     }
     return out, clocks
+
+
+# The library's kernel that implements each latent stage.
+KERNEL_OF_STAGE = {"inference": "k_mlp_tc<0>", "gauss_newton": "k_mlp_tc<1>",
+                   "p2g": "k_p2g_latent", "grid": "k_grid_update", "g2p": "k_g2p_latent"}
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch of `kernel` on this workload, from the ncu summary
+    in profiles/ (None if absent)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if kernel is None or not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = [x.strip() for x in line.strip().strip("|").split("|")]
+        if len(f) >= 2 and f[0] == kernel:
+            try:
+                return float(f[1].replace(",", ""))
+            except ValueError:
+                return None
+    return None
+
+
+def run_throughput(args, nsf, fs, dev, peaks, peak_src):
+    """The inference kernel (g, h, l) on a throughput-sized point set (one
+    launch, 2^20 points), timed with CUDA events: what the tensor-core MLP
+    kernel sustains when the work is large enough to fill the GPU."""
+    import torch
+    n = 1 << 20
+    rng = np.random.Generator(np.random.PCG64(77))
+    X = torch.from_numpy(rng.uniform(0.3, 0.7, size=(3, n)).astype(np.float32)).to(dev)
+    z = torch.tensor(rng.normal(0, 0.1, size=fs.r), dtype=torch.float64, device=dev)
+    F = nsf.Fields.from_spec(fs)
+    x = torch.empty(3, n, device=dev)
+    tau = torch.empty(6, n, device=dev)
+    Cm = torch.empty(9, n, device=dev)
+    for _ in range(3):
+        nsf.nsf_eval_fields(F, X, z, x=x, tau6=tau, C9=Cm)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        nsf.nsf_eval_fields(F, X, z, x=x, tau6=tau, C9=Cm)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    macs = [mlp_macs(fs.r, fs.width[i], fs.depth[i], od) for i, od in enumerate((3, 6, 9))]
+    flops = 2.0 * n * sum(macs)
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops"]
+    return {"kernel": "k_mlp_tc<0>", "points": n, "ms": ms, "achieved": achieved,
+            "unit": "TFLOP/s", "peak": peak, "frac": achieved / peak,
+            "peak_source": f"bf16 dense burst, {peak_src}",
+            "note": "fields g, h, l on 2^20 points; the latent step's own launches are latency-bound"}
 
 
 def run_e2e(args, nsf, sc, F, gd, dev):
