@@ -246,6 +246,8 @@ def run_gpu(args, rank, world, local):
     e2e = run_e2e(args, nsf, sc, F, gd, dev)
 
     full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
+    full_plastic = run_full(args, nsf, full_config2(model="von_mises", steps=args.steps), dev,
+                            flush)
 
     # kernels per step: fields 1, bin 3, P2G 1, grid 1, G2P 1, Gauss-Newton 1
     # (all iterations in one cooperative launch on the BF16 path)
@@ -264,6 +266,7 @@ def run_gpu(args, rank, world, local):
         "mlp_throughput": throughput,
         "e2e": e2e,
         "full_order": full,
+        "full_order_plastic": full_plastic,
         "gpu_launches": launches_per_step * K,
         "status": status,
     }

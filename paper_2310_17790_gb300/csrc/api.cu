@@ -594,7 +594,11 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         !(P->mass > 0.f) || !(P->vol0 > 0.f) || !(mat->E > 0.f) || !(mat->nu > -1.f) ||
         !(mat->nu < 0.5f))
         return NSF_ERR_INVALID_ARG;
-    if (mat->model != NSF_NEO_HOOKEAN) return NSF_ERR_UNSUPPORTED;
+    if (mat->model < NSF_NEO_HOOKEAN || mat->model > NSF_DRUCKER_PRAGER) return NSF_ERR_INVALID_ARG;
+    if (mat->model == NSF_VON_MISES && !(mat->yield_stress > 0.f)) return NSF_ERR_INVALID_ARG;
+    if (mat->model == NSF_DRUCKER_PRAGER &&
+        !(mat->friction_deg > 0.f && mat->friction_deg < 90.f))
+        return NSF_ERR_INVALID_ARG;
     if (nsteps == 0) return NSF_OK;
     FullLayout L = full_layout(grid, P->n);
     if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
@@ -604,6 +608,11 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
     GridParams gp = make_params(grid);
     const float mu = mat->E / (2.f * (1.f + mat->nu));
     const float lam = mat->E * mat->nu / ((1.f + mat->nu) * (1.f - 2.f * mat->nu));
+    // SVD-based models keep the float64 stress of F^E in the workspace: computed
+    // here for the first step, then by every G2P after its return map
+    const bool svd_model = mat->model != NSF_NEO_HOOKEAN;
+    float *tau6 = svd_model ? reinterpret_cast<float *>(base + L.tau) : nullptr;
+    if (svd_model) NSF_CUDA_TRY(launch_stress(P->d_F, tau6, P->n, mat->model, mu, lam, s));
     for (int step = 0; step < nsteps; ++step) {
         const bool last = step == nsteps - 1;
         NSF_CUDA_TRY(launch_bin(g, nullptr, P->d_x, P->n, gp.inv_dx, d_status, s));
@@ -612,7 +621,7 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         pa.v = P->d_v;
         pa.C = P->d_C;
         pa.F = P->d_F;
-        pa.tau6 = nullptr;
+        pa.tau6 = tau6;
         pa.n = P->n;
         pa.mass = P->mass;
         pa.vol0 = P->vol0;
@@ -628,7 +637,7 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         ga.v = P->d_v;
         ga.C = P->d_C;
         ga.F = P->d_F;
-        ga.tau6 = nullptr;
+        ga.tau6 = tau6;
         ga.n = P->n;
         ga.dt = (float)dt;
         ga.model = mat->model;

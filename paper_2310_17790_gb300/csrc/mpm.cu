@@ -13,6 +13,7 @@
 //                  shared-memory tile, then one vector atomic per touched node
 //   k_grid_update  v = p / m + dt g, walls, blade; re-zeroes the accumulators
 //   k_g2p_*        gather of the 27 node velocities per particle
+#include "constitutive.cuh"
 #include "device_common.cuh"
 
 namespace nsf {
@@ -415,6 +416,22 @@ k_g2p_full(GridWs g, GridParams gp, G2pFullArgs a, int *status) {
         for (int j = 0; j < 3; ++j)
             Fn[3 * i + j] = F[3 * i + j] + a.dt * (C[3 * i] * F[j] + C[3 * i + 1] * F[3 + j] +
                                                    C[3 * i + 2] * F[6 + j]);
+    if (a.tau6) {
+        // float64 SVD, return map and stress of F^E for the next step
+        double Fd[9], t6[6];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Fd[c] = (double)Fn[c];
+        return_map_and_stress(a.model, Fd, a.mu, a.lam, a.yield_stress, a.friction_deg, true, t6);
+        bool fin = true;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            Fn[c] = (float)Fd[c];
+            fin &= isfinite(Fn[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.tau6[(size_t)c * n + p] = (float)t6[c];
+        if (!fin) set_status(status, NSF_ERR_NONFINITE);
+    }
     a.x[p] = fmaf(a.dt, v[0], x0);
     a.x[n + p] = fmaf(a.dt, v[1], x1);
     a.x[2 * n + p] = fmaf(a.dt, v[2], x2);
@@ -427,9 +444,28 @@ k_g2p_full(GridWs g, GridParams gp, G2pFullArgs a, int *status) {
     }
 }
 
+// Kirchhoff stress of F (no return map) for the SVD-based models, float64.
+__global__ void __launch_bounds__(256)
+k_stress(const float *__restrict__ F, float *tau6, int n, int model, float mu, float lam) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double Fd[9], t6[6];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Fd[c] = (double)F[(size_t)c * n + p];
+    return_map_and_stress(model, Fd, mu, lam, 0.0, 0.0, false, t6);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tau6[(size_t)c * n + p] = (float)t6[c];
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers ---
+cudaError_t launch_stress(const float *F, float *tau6, int n, int model, float mu, float lam,
+                          cudaStream_t s) {
+    k_stress<<<(n + 255) / 256, 256, 0, s>>>(F, tau6, n, model, mu, lam);
+    return cudaGetLastError();
+}
+
 static int persistent_grid(int work, int per_sm) {
     static int sms = 0;
     if (sms == 0) {

@@ -58,7 +58,9 @@ def _run(nsf, sc, nsteps=1, t0=0.0):
 def _check(sc, out, t0=0.0):
     assert out["status"] == 0
     og = oracle_grid(sc.grid)
-    mat = ocm.Material(sc.material["model"], sc.material["E"], sc.material["nu"])
+    m = sc.material
+    mat = ocm.Material(m["model"], m["E"], m["nu"], m.get("yield_stress", 0.0),
+                       m.get("friction_deg", 30.0))
     x0 = sc.x.astype(np.float64)
     v0 = sc.v.astype(np.float64)
     C0 = sc.C.astype(np.float64).reshape(-1, 3, 3)
@@ -77,7 +79,9 @@ def _check(sc, out, t0=0.0):
     assert rel(out["v"], vp) < TOL
     assert rel(out["C"], Cp.reshape(-1, 9)) < TOL
     Fn = np.einsum("nij,njk->nik", np.eye(3) + sc.dt * Gp, F0)
-    assert rel(out["F"], Fn.reshape(-1, 9)) < TOL
+    Fe = mat.return_map(Fn)
+    assert rel(out["F"], Fe.reshape(-1, 9)) < TOL
+    return Fn, Fe
 
 
 def test_full_step_small_slab_with_blade(nsf):
@@ -109,5 +113,30 @@ def test_full_step_conserves_momentum_on_gpu(nsf):
 def test_full_step_multi_step_stays_in_grid(nsf):
     sc = full_scene(74, lattice=(24, 24, 6), n_grid=64)
     out = _run(nsf, sc, nsteps=20)
+    assert out["status"] == 0
+    assert np.isfinite(out["x"]).all() and np.isfinite(out["F"]).all()
+
+
+@pytest.mark.parametrize("model,extra", [
+    ("fixed_corotated", {}),
+    ("von_mises", {"yield_stress": 2.5e3}),
+    ("drucker_prager", {"friction_deg": 30.0}),
+])
+def test_full_step_svd_models(nsf, model, extra):
+    # float64 SVD, return map and stress on the GPU (App. F) against the oracle
+    sc = _perturb(full_scene(75, lattice=(24, 24, 8), n_grid=64, model=model, **extra), 75,
+                  f=0.03)
+    out = _run(nsf, sc)
+    Fn, Fe = _check(sc, out)
+    if model != "fixed_corotated":
+        # some particles must have been projected for the test to mean anything
+        moved = np.linalg.norm((Fe - Fn).reshape(-1, 9), axis=1) > 1e-6
+        assert moved.mean() > 0.05, moved.mean()
+
+
+def test_full_step_plastic_slab_multi_step(nsf):
+    # the 200k slab with von Mises (yield stress 1e4) and the blade, 10 steps
+    sc = full_scene(76, model="von_mises", yield_stress=1e4)
+    out = _run(nsf, sc, nsteps=10)
     assert out["status"] == 0
     assert np.isfinite(out["x"]).all() and np.isfinite(out["F"]).all()
