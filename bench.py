@@ -249,9 +249,10 @@ def run_gpu(args, rank, world, local):
     full_plastic = run_full(args, nsf, full_config2(model="von_mises", steps=args.steps), dev,
                             flush)
 
-    # kernels per step: fields 1, bin 3, P2G 1, grid 1, G2P 1, Gauss-Newton 1
-    # (all iterations in one cooperative launch on the BF16 path)
-    launches_per_step = 8 if args.precision == "bf16" else 7 + sc.gn_iters
+    # kernels per step: fields 1, MPM 1 (binning, P2G, grid update and G2P in
+    # one cooperative launch), Gauss-Newton 1 (all iterations in one
+    # cooperative launch on the BF16 path)
+    launches_per_step = 3 if args.precision == "bf16" else 2 + sc.gn_iters
     out = {
         "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -275,7 +276,7 @@ def run_gpu(args, rank, world, local):
 
 # The library's kernel that implements each latent stage.
 KERNEL_OF_STAGE = {"inference": "k_mlp_tc<0>", "gauss_newton": "k_mlp_tc<1>",
-                   "p2g": "k_p2g_latent", "grid": "k_grid_update", "g2p": "k_g2p_latent"}
+                   "mpm": "k_mpm_latent"}
 
 
 def load_traffic(kernel):

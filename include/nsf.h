@@ -178,13 +178,11 @@ typedef struct nsf_gn_opts {
  */
 /* Stages of a latent step, for the optional stage events of nsf_latent_taps. */
 enum {
-    NSF_STAGE_INFERENCE = 0,   /* field networks on N (§5.1)                 */
-    NSF_STAGE_BIN = 1,         /* particle binning by grid block             */
-    NSF_STAGE_P2G = 2,         /* P2G with the stress force (§3.3, Eq. 5)    */
-    NSF_STAGE_GRID = 3,        /* grid update                                */
-    NSF_STAGE_G2P = 4,         /* G2P on S                                   */
-    NSF_STAGE_GN = 5,          /* Gauss-Newton inversion (§5.3)              */
-    NSF_LATENT_STAGES = 6
+    NSF_STAGE_INFERENCE = 0,   /* field networks on N (§5.1)                          */
+    NSF_STAGE_MPM = 1,         /* binning, P2G with the stress force (§3.3, Eq. 5),
+                                  grid update and G2P on S: one launch                */
+    NSF_STAGE_GN = 2,          /* Gauss-Newton inversion (§5.3)                       */
+    NSF_LATENT_STAGES = 3
 };
 
 typedef struct nsf_latent_taps {

@@ -27,8 +27,8 @@ NSF_FIELD_G, NSF_FIELD_H, NSF_FIELD_L = 0, 1, 2
 NSF_PREC_FP32, NSF_PREC_BF16 = 0, 1
 NSF_NEO_HOOKEAN, NSF_FIXED_COROTATED, NSF_VON_MISES, NSF_DRUCKER_PRAGER = 0, 1, 2, 3
 NSF_MAX_R, NSF_MAX_WIDTH, NSF_MAX_DEPTH = 16, 256, 8
-NSF_STAGE_NAMES = ("inference", "bin", "p2g", "grid", "g2p", "gauss_newton")
-NSF_LATENT_STAGES = 6
+NSF_STAGE_NAMES = ("inference", "mpm", "gauss_newton")
+NSF_LATENT_STAGES = 3
 NSF_LATENT_REUSE_PREV = 1
 NSF_PROJECT_STATIC_MAX_S = 2048
 NSF_PROJECT_STATIC_BYTES = 1 << 20

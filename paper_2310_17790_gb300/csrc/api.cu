@@ -61,7 +61,7 @@ GridParams make_params(const nsf_grid_desc *g) {
 
 // Grid part of a workspace.
 struct GridLayout {
-    size_t acc, vel, gstamp, cnt, blk_slot, plist, pcount, poff, glist, key, rank, perm, ctl;
+    size_t acc, vel, gstamp, pstamp, plist, glist, ctl;
     int nblocks, max_pblocks, max_gblocks;
 };
 
@@ -76,15 +76,9 @@ GridLayout carve_grid(Carver &c, const nsf_grid_desc *g, int n) {
     L.acc = c.take(nodes * sizeof(float4));
     L.vel = c.take(nodes * sizeof(float4));
     L.gstamp = c.take((size_t)L.nblocks * 4);
-    L.cnt = c.take((size_t)L.nblocks * 4);
-    L.blk_slot = c.take((size_t)L.nblocks * 4);
+    L.pstamp = c.take((size_t)L.nblocks * 4);
     L.plist = c.take((size_t)L.max_pblocks * 4);
-    L.pcount = c.take((size_t)L.max_pblocks * 4);
-    L.poff = c.take((size_t)(L.max_pblocks + 1) * 4);
     L.glist = c.take((size_t)L.max_gblocks * 4);
-    L.key = c.take((size_t)n * 4);
-    L.rank = c.take((size_t)n * 4);
-    L.perm = c.take((size_t)n * 4);
     return L;
 }
 
@@ -100,17 +94,10 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
     w.acc = reinterpret_cast<float4 *>(base + L.acc);
     w.vel = reinterpret_cast<float4 *>(base + L.vel);
     w.gstamp = reinterpret_cast<int *>(base + L.gstamp);
-    w.cnt = reinterpret_cast<int *>(base + L.cnt);
-    w.blk_slot = reinterpret_cast<int *>(base + L.blk_slot);
+    w.pstamp = reinterpret_cast<int *>(base + L.pstamp);
     w.plist = reinterpret_cast<int *>(base + L.plist);
-    w.pcount = reinterpret_cast<int *>(base + L.pcount);
-    w.poff = reinterpret_cast<int *>(base + L.poff);
     w.glist = reinterpret_cast<int *>(base + L.glist);
-    w.key = reinterpret_cast<int *>(base + L.key);
-    w.rank = reinterpret_cast<int *>(base + L.rank);
-    w.perm = reinterpret_cast<int *>(base + L.perm);
     w.ctl = reinterpret_cast<Ctl *>(base + L.ctl);
-    w.max_p = n;
     w.max_pblocks = L.max_pblocks;
     w.max_gblocks = L.max_gblocks;
     return w;
@@ -469,10 +456,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_INFERENCE));
         NSF_CUDA_TRY(run_fields(f->dev, sc->d_X, nN, nN, njobs, jobs, d_status, s));
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_INFERENCE));
-        // 2. MPM step on N (§5.2)
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_BIN));
-        NSF_CUDA_TRY(launch_bin(g, Xoff, u_n, nN, gp.inv_dx, d_status, s));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_BIN));
+        // 2. MPM step on N (§5.2): binning, P2G, grid update and G2P on S
         P2gLatentArgs pa;
         pa.X = Xoff;
         pa.u = u_n;
@@ -484,17 +468,11 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         pa.vol0 = sc->vol0;
         pa.inv_dt = (float)(1.0 / dt);
         pa.dt = (float)dt;
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_P2G));
-        NSF_CUDA_TRY(launch_p2g_latent(g, gp, pa, s));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_P2G));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GRID));
-        NSF_CUDA_TRY(launch_grid_update(g, gp, (float)dt, t0 + step * dt,
-                                        last && taps ? taps->grid_mp : nullptr,
-                                        last && taps ? taps->grid_v : nullptr, s));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_GRID));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_G2P));
-        NSF_CUDA_TRY(launch_g2p_latent(g, gp, Xoff, u_n, nN, nS, (float)dt, dnext, d_status, s));
-        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_G2P));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_MPM));
+        NSF_CUDA_TRY(launch_mpm_latent(g, gp, pa, nS, t0 + step * dt, dnext,
+                                       last && taps ? taps->grid_mp : nullptr,
+                                       last && taps ? taps->grid_v : nullptr, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? taps->ev_end : nullptr, NSF_STAGE_MPM));
         if (last && taps) {
             if (taps->u_n) NSF_CUDA_TRY(cudaMemcpyAsync(taps->u_n, u_n, 12 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
             if (taps->u_prev) NSF_CUDA_TRY(cudaMemcpyAsync(taps->u_prev, u_prev, 12 * (size_t)nN, cudaMemcpyDeviceToDevice, s));
@@ -615,7 +593,6 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
     if (svd_model) NSF_CUDA_TRY(launch_stress(P->d_F, tau6, P->n, mat->model, mu, lam, s));
     for (int step = 0; step < nsteps; ++step) {
         const bool last = step == nsteps - 1;
-        NSF_CUDA_TRY(launch_bin(g, nullptr, P->d_x, P->n, gp.inv_dx, d_status, s));
         P2gFullArgs pa;
         pa.x = P->d_x;
         pa.v = P->d_v;
@@ -628,10 +605,6 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         pa.dt = (float)dt;
         pa.mu = mu;
         pa.lam = lam;
-        NSF_CUDA_TRY(launch_p2g_full(g, gp, pa, s));
-        NSF_CUDA_TRY(launch_grid_update(g, gp, (float)dt, t0 + step * dt,
-                                        last && taps ? taps->grid_mp : nullptr,
-                                        last && taps ? taps->grid_v : nullptr, s));
         G2pFullArgs ga;
         ga.x = P->d_x;
         ga.v = P->d_v;
@@ -645,7 +618,9 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         ga.lam = lam;
         ga.yield_stress = mat->yield_stress;
         ga.friction_deg = mat->friction_deg;
-        NSF_CUDA_TRY(launch_g2p_full(g, gp, ga, d_status, s));
+        NSF_CUDA_TRY(launch_mpm_full(g, gp, pa, ga, t0 + step * dt,
+                                     last && taps ? taps->grid_mp : nullptr,
+                                     last && taps ? taps->grid_v : nullptr, d_status, s));
     }
     return NSF_OK;
 }

@@ -44,12 +44,16 @@ struct FieldsDev {
 
 // ------------------------------------------------------------- workspace ---
 struct Ctl {
-    int epoch;          // incremented once per MPM step (grid-block stamps)
-    int n_p_atomic;     // particle-block counter filled by the binning pass
-    int n_pblocks;      // active particle blocks of the current step
-    int n_gblocks;      // active grid blocks of the current step
-    int gn_counter;     // arrival counter of the fused Gauss-Newton solve
-    int pad[3];
+    int epoch;          // incremented once per MPM step (block stamps)
+    int n_p_atomic;     // active particle blocks of the current step
+    int n_g_atomic;     // active grid blocks of the current step
+    int pad0[29];
+    // grid barrier of the fused MPM kernel; the arrival counter and the
+    // generation word the waiting CTAs poll sit in separate 128-byte lines
+    unsigned bar_count;
+    unsigned pad1[31];
+    unsigned bar_gen;
+    unsigned pad2[31];
 };
 
 // Sparse-in-use, dense-in-address background grid.  Nodes are stored
@@ -61,17 +65,11 @@ struct GridWs {
     float4 *acc;        // (m, p) accumulators; all zero between steps
     float4 *vel;        // (v, m) after the grid update; valid on touched blocks
     int *gstamp;        // epoch stamp of each grid block
-    int *cnt;           // particles per particle block; all zero between steps
-    int *blk_slot;      // particle block -> slot in plist
-    int *plist;         // active particle blocks (slot order)
-    int *pcount;        // particles per slot
-    int *poff;          // first sorted index per slot
-    int *glist;         // active grid blocks
-    int *key;           // particle -> particle block (or -1)
-    int *rank;          // particle -> rank inside its block
-    int *perm;          // sorted index -> particle
+    int *pstamp;        // epoch stamp of each particle block (4^3 cells by stencil base)
+    int *plist;         // active particle blocks of the step
+    int *glist;         // active grid blocks of the step
     Ctl *ctl;
-    int max_p, max_pblocks, max_gblocks;
+    int max_pblocks, max_gblocks;
 };
 
 struct GridParams {
@@ -135,9 +133,9 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
                                const double *z, float *u, float *dudz,
                                const GnArgs *gn, int *status, cudaStream_t s);
 
-// MPM transfer kernels.
-cudaError_t launch_bin(const GridWs &g, const float *X, const float *u, int n,
-                       float inv_dx, int *status, cudaStream_t s);
+// MPM step: one cooperative launch each (bin, P2G, grid update, G2P with
+// grid-wide barriers between the phases).  After a barrier timeout
+// (NSF_ERR_ITER_CAP in *status) the workspace's control block is undefined.
 struct P2gLatentArgs {
     const float *X;       // [3][n] or null (non-residual g: u is the position)
     const float *u;       // [3][n] displacement at z_n
@@ -149,8 +147,6 @@ struct P2gLatentArgs {
     float inv_dt;
     float dt;
 };
-cudaError_t launch_p2g_latent(const GridWs &g, const GridParams &gp,
-                              const P2gLatentArgs &a, cudaStream_t s);
 struct P2gFullArgs {
     const float *x, *v, *C, *F;   // SoA
     const float *tau6;            // [6][n] precomputed stress, or null (neo-Hookean inline)
@@ -158,14 +154,6 @@ struct P2gFullArgs {
     float mass, vol0, dt;
     float mu, lam;
 };
-cudaError_t launch_p2g_full(const GridWs &g, const GridParams &gp,
-                            const P2gFullArgs &a, cudaStream_t s);
-cudaError_t launch_grid_update(const GridWs &g, const GridParams &gp, float dt,
-                               double t, float *tap_mp, float *tap_v,
-                               cudaStream_t s);
-cudaError_t launch_g2p_latent(const GridWs &g, const GridParams &gp,
-                              const float *X, const float *u, int ld, int n_S,
-                              float dt, float *d_next, int *status, cudaStream_t s);
 struct G2pFullArgs {
     float *x, *v, *C, *F;
     float *tau6;                  // [6][n] written for the next step (SVD models) or null
@@ -174,8 +162,12 @@ struct G2pFullArgs {
     int model;
     float mu, lam, yield_stress, friction_deg;
 };
-cudaError_t launch_g2p_full(const GridWs &g, const GridParams &gp,
-                            const G2pFullArgs &a, int *status, cudaStream_t s);
+cudaError_t launch_mpm_latent(const GridWs &g, const GridParams &gp, const P2gLatentArgs &a,
+                              int n_S, double t, float *d_next, float *tap_mp, float *tap_v,
+                              int *status, cudaStream_t s);
+cudaError_t launch_mpm_full(const GridWs &g, const GridParams &gp, const P2gFullArgs &pa,
+                            const G2pFullArgs &ga, double t, float *tap_mp, float *tap_v,
+                            int *status, cudaStream_t s);
 cudaError_t launch_stress(const float *F, float *tau6, int n, int model,
                           float mu, float lam, cudaStream_t s);
 
