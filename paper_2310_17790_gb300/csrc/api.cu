@@ -103,9 +103,23 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
     return w;
 }
 
+// Gauss-Newton control words: the arrival ticket, the grid-barrier word and
+// the two reader counters, each in its own 128-byte line.
+constexpr size_t kGnCtlBytes = 384;
+
+GnArgs gn_args(char *gnctl, double *gsum, double *zgn) {
+    GnArgs g{};
+    g.gsum = gsum;
+    g.z_buf = zgn;
+    g.counter = reinterpret_cast<int *>(gnctl);
+    g.bar = reinterpret_cast<unsigned *>(gnctl + 128);
+    g.readers = reinterpret_cast<int *>(gnctl + 256);
+    return g;
+}
+
 struct LatentLayout {
     GridLayout grid;
-    size_t u[2], tau, C, dnext, partials, zgn, gsum, gnctl;
+    size_t u[2], tau, C, dnext, zgn, gsum, gnctl;
     size_t total;
 };
 
@@ -119,18 +133,15 @@ LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc) {
     L.tau = c.take(6 * n * 4);
     L.C = c.take(9 * n * 4);
     L.dnext = c.take(3 * (size_t)sc->n_S * 4);
-    int grid = f->dev.precision == NSF_PREC_BF16 ? jac_grid_size_tc(f->dev, sc->n_S)
-                                                 : jac_grid_size_simt(f->dev, sc->n_S);
-    L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
     L.zgn = c.take(NSF_MAX_R * 8);
-    L.gsum = c.take((size_t)gn_partial_stride(NSF_MAX_R) * 8);
-    L.gnctl = c.take(64);
+    L.gsum = c.take(2 * (size_t)kGnStrideMax * 8);
+    L.gnctl = c.take(kGnCtlBytes);
     L.total = c.off;
     return L;
 }
 
 struct ProjectLayout {
-    size_t target, u, partials, zgn, gsum, gnctl, total;
+    size_t target, u, zgn, gsum, gnctl, total;
 };
 
 ProjectLayout project_layout(const nsf_fields *f, int n_S) {
@@ -138,12 +149,9 @@ ProjectLayout project_layout(const nsf_fields *f, int n_S) {
     ProjectLayout L;
     L.target = c.take(3 * (size_t)n_S * 4);
     L.u = c.take(3 * (size_t)n_S * 4);
-    int grid = f->dev.precision == NSF_PREC_BF16 ? jac_grid_size_tc(f->dev, n_S)
-                                                 : jac_grid_size_simt(f->dev, n_S);
-    L.partials = c.take((size_t)grid * gn_partial_stride(f->desc.r) * 8);
     L.zgn = c.take(NSF_MAX_R * 8);
-    L.gsum = c.take((size_t)gn_partial_stride(NSF_MAX_R) * 8);
-    L.gnctl = c.take(64);
+    L.gsum = c.take(2 * (size_t)kGnStrideMax * 8);
+    L.gnctl = c.take(kGnCtlBytes);
     L.total = c.off;
     return L;
 }
@@ -427,9 +435,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
     float *tau = reinterpret_cast<float *>(base + L.tau);
     float *C9 = reinterpret_cast<float *>(base + L.C);
     float *dnext = reinterpret_cast<float *>(base + L.dnext);
-    double *partials = reinterpret_cast<double *>(base + L.partials);
     double *zgn = reinterpret_cast<double *>(base + L.zgn);
-    int *gn_counter = reinterpret_cast<int *>(base + L.gnctl);
     const float *Xoff = f->dev.residual_g ? sc->d_X : nullptr;
     // ub[1] holds g(X, z_prev) between calls; step s writes g(X, z_n) to ub[s & 1 ^ 0]
     // and reads g(X, z_{n-1}) from the other buffer.
@@ -483,19 +489,14 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         // 3. network inversion (§5.3), Gauss-Newton from z_n
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GN));
         {
-            GnArgs gn;
+            GnArgs gn = gn_args(base + L.gnctl, reinterpret_cast<double *>(base + L.gsum), zgn);
             gn.target = dnext;
             gn.target_ld = nS;
             gn.iters = opts->iters;
             gn.z_start = d_z;
-            gn.z_buf = zgn;
             gn.z_out = d_z;
             gn.z_prev_out = d_z_prev;
             gn.z_taps = (last && taps) ? taps->z_iter : nullptr;
-            gn.partials = partials;
-            gn.gsum = reinterpret_cast<double *>(base + L.gsum);
-            gn.counter = gn_counter;
-            gn.flag = gn_counter + 4;
             gn.damping = opts->damping;
             NSF_CUDA_TRY(run_jacobian(f->dev, sc->d_X, nS, nN, d_z, nullptr, nullptr, &gn, d_status, s));
         }
@@ -526,26 +527,19 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
     char *base = static_cast<char *>(d_ws);
     float *target = reinterpret_cast<float *>(base + L.target);
     float *u = reinterpret_cast<float *>(base + L.u);
-    double *partials = reinterpret_cast<double *>(base + L.partials);
     double *zgn = reinterpret_cast<double *>(base + L.zgn);
-    int *counter = reinterpret_cast<int *>(base + L.gnctl);
     // residual fields work on displacements: d = x_target - X
     if (f->dev.residual_g) NSF_CUDA_TRY(axpy(target, d_x_target, d_X_S, -1.f, 3 * n_S, s));
     else NSF_CUDA_TRY(cudaMemcpyAsync(target, d_x_target, 12 * (size_t)n_S, cudaMemcpyDeviceToDevice, s));
     {
-        GnArgs gn;
+        GnArgs gn = gn_args(base + L.gnctl, reinterpret_cast<double *>(base + L.gsum), zgn);
         gn.target = target;
         gn.target_ld = n_S;
         gn.iters = opts->iters;
         gn.z_start = d_z_inout;
-        gn.z_buf = zgn;
         gn.z_out = d_z_inout;
         gn.z_prev_out = nullptr;
         gn.z_taps = d_z_iter;
-        gn.partials = partials;
-        gn.gsum = reinterpret_cast<double *>(base + L.gsum);
-        gn.counter = counter;
-        gn.flag = counter + 4;
         gn.damping = opts->damping;
         NSF_CUDA_TRY(run_jacobian(f->dev, d_X_S, n_S, n_S, d_z_inout, nullptr, nullptr, &gn, d_status, s));
     }

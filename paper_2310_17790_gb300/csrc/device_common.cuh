@@ -5,6 +5,16 @@
 
 namespace nsf {
 
+// Bound on every spin-wait of the library's kernels (barriers, mbarriers):
+// a wait that runs out records an error status and returns.
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // First error wins: the status word only moves away from NSF_OK once.
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, NSF_OK, code);
@@ -14,6 +24,36 @@ __device__ __forceinline__ void set_status(int *status, int code) {
 __device__ __forceinline__ float elu(float a) { return a > 0.f ? a : expm1f(a); }
 // Its derivative, from the pre-activation: 1 for a > 0, exp(a) otherwise.
 __device__ __forceinline__ float elu_grad(float a) { return a > 0.f ? 1.f : expf(a); }
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident) on one
+// arrival word that is zero before the launch's first barrier.  CTA 0 adds
+// 2^31 - (gridDim.x - 1), every other CTA adds 1: the low bits count the
+// arrivals and carry into the top bit exactly when the last CTA arrives, after
+// which they are back at zero, so the word is ready for the next barrier with
+// no reset.  Every thread of every CTA calls it.  Returns false after
+// recording NSF_ERR_ITER_CAP if the wait ran out; the word is then undefined.
+__device__ inline bool grid_barrier(unsigned *word, int *status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+        __threadfence();
+        const unsigned old = atomicAdd(word, inc);
+        volatile unsigned *w = word;
+        const unsigned long long t0 = global_ns();
+        while (((*w ^ old) & 0x80000000u) == 0u) {
+            if (global_ns() - t0 > kWaitNs) {
+                set_status(status, NSF_ERR_ITER_CAP);
+                s_ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
 
 // Upper-triangle (i <= j) packed index of an r x r symmetric matrix.
 __host__ __device__ __forceinline__ int tri_index(int i, int j, int r) {

@@ -191,7 +191,7 @@ k_jacobian(const __grid_constant__ FieldsDev fd, const float *__restrict__ X,
     __shared__ GnShared gsh;
     __shared__ float RES[kJacRows][3];
     __shared__ float JS[kJacRows][3][kMaxR];
-    __shared__ double PART[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
+    __shared__ double PART[kGnStrideMax];
     const FieldDev &F = fd.f[NSF_FIELD_G];
     const int r = fd.r, S = 1 + r, ppc = kJacRows / S;
     const int W = F.width;

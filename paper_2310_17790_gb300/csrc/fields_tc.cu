@@ -76,7 +76,6 @@ constexpr int kWgThreads = 128;
 constexpr int kThreads = kWG * kWgThreads;
 constexpr int kGroup = 8;                 // columns per epilogue group (one core-matrix row)
 constexpr int kMaxSmem = 227 * 1024;
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 // Shared-memory carve of one CTA (byte offsets from a 1024-aligned base).
 struct TcLayout {
@@ -95,7 +94,7 @@ __host__ __device__ inline TcLayout tc_layout(int r, int W, int D) {
     L.w0v = o;  o = align_to(o + W * 16, 16);                 // float4 {w_x, w_y, w_z, c0}
     L.w0t = o;  o = align_to(o + r * (W + 1) * 4, 16);        // tangent inputs W0[:, 3 + k]
     L.o3 = o;   o = align_to(o + kM * 3 * 4, 16);
-    L.part = o; o = align_to(o + (kMaxR * (kMaxR + 1) / 2 + kMaxR + 1) * 8, 16);
+    L.part = o; o = align_to(o + (kGnStrideMax) * 8, 16);
     L.pe = o;   o = align_to(o + kThreads * 8, 16);
     L.bars = o; o = align_to(o + 2 * 8, 16);
     L.tmem = o; o = align_to(o + 16, 16);
@@ -108,11 +107,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -138,9 +132,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
 // Bounded wait for the given phase parity; false if it did not complete in time.
 __device__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
     if (mbar_try_wait(bar, phase)) return true;
-    const unsigned long long t0 = now_ns();
+    const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, phase))
-        if (now_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
     return true;
 }
 
@@ -288,7 +282,6 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
          const __grid_constant__ GnArgs gn, int gn_on, int pts_per_tile, int *status) {
     extern __shared__ uint8_t smem_dyn[];
     __shared__ GnShared gsh;
-    __shared__ int s_abort;
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
 
@@ -324,7 +317,6 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const int n_iter = (MODE == 1 && gn_on) ? gn.iters : 1;
 
     if (tid == 0) {
-        s_abort = 0;
         mbar_init(bar_w, 1);
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -374,13 +366,19 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
     const bool live_warp = (row & ~31) < P * Lp;     // warps with no tile row skip the epilogue
     const int vlane = (row & 31) & ~(Lp - 1);
 
+    // Gauss-Newton: every CTA carries z in shared memory from iteration to
+    // iteration (it solves each iteration's system itself)
+    if (MODE == 1 && gn_on && tid < r) gsh.z[tid] = gsh.z0[tid] = __ldcg(&gn.z_start[tid]);
+
     for (int it = 0; it < n_iter; ++it) {
-        const double *z = MODE == 0 ? jobs.job[blockIdx.y].z
-                                    : (gn_on ? gn_z_in(gn, it) : zj);
+        const double *z = MODE == 0 ? jobs.job[blockIdx.y].z : zj;
         __syncthreads();
         for (int j = tid; j < W; j += kThreads) {
             float a = F.b[0][j];
-            for (int k = 0; k < r; ++k) a = fmaf(W0t[k * ldt + j], (float)__ldcg(&z[k]), a);
+            for (int k = 0; k < r; ++k) {
+                const double zk = (MODE == 1 && gn_on) ? gsh.z[k] : __ldcg(&z[k]);
+                a = fmaf(W0t[k * ldt + j], (float)zk, a);
+            }
             W0v[j].w = a;
         }
         if (MODE == 1)
@@ -559,32 +557,10 @@ k_mlp_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         }
 
         if (MODE == 1 && gn_on) {
-            // Gauss-Newton iteration `it`: publish this CTA's partials; the last
-            // CTA to arrive solves and releases the others (grid barrier of a
-            // cooperative launch; every wait is bounded).
+            // Gauss-Newton iteration `it`: all CTAs' partials summed behind a
+            // grid barrier (cooperative launch), then every CTA solves
             __syncthreads();
-            const bool last = gn_arrive_and_solve(gn, r, it, status, gsh, part);
-            if (it + 1 < n_iter) {
-                if (last) {
-                    if (tid == 0) atomicExch(gn.flag, it + 1);
-                } else {
-                    if (tid == 0) {
-                        const unsigned long long t0 = now_ns();
-                        while (atomicAdd(gn.flag, 0) < it + 1) {
-                            if (now_ns() - t0 > kWaitNs) {
-                                set_status(status, NSF_ERR_ITER_CAP);
-                                s_abort = 1;
-                                break;
-                            }
-                        }
-                        __threadfence();
-                    }
-                    __syncthreads();
-                    if (s_abort) goto teardown;
-                }
-            } else if (last && tid == 0) {
-                atomicExch(gn.flag, 0);      // ready for the next launch
-            }
+            if (!gn_allreduce_solve(gn, r, it, status, gsh, part)) goto teardown;
         }
     }
 

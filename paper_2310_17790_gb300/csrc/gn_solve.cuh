@@ -1,15 +1,22 @@
 // Gauss-Newton normal equations of the network inversion (§5.3, Eq. 9), in
-// float64, finished by the last CTA of the Jacobian kernel that produced the
-// per-CTA partial sums of an iteration.
+// float64, from the per-CTA partial sums of the Jacobian kernel.
 //
-// Partial layout per CTA (stride gn_partial_stride(r)):
+// Partial layout (stride gn_partial_stride(r)):
 //   [0, T)            sum_p J_p^T J_p, upper triangle (i <= j), T = r (r + 1) / 2
 //   [T, T + r)        sum_p J_p^T res_p
 //   [T + r]           sum_p |res_p|^2
-// CTAs add their partial sums into one float64 accumulator with atomics; the
-// last CTA to arrive solves (A + damping I) dz = -b (see gn_solve_warp) and
-// sets z_new = z + dz.  A non-positive or non-finite pivot sets
-// NSF_ERR_SINGULAR and leaves z unchanged for that iteration.
+// CTAs add their partial sums into a float64 accumulator with atomics.  The
+// system (A + damping I) dz = -b is solved by gn_solve_warp and z_new = z + dz.
+// A non-positive or non-finite pivot sets NSF_ERR_SINGULAR and leaves z
+// unchanged for that iteration.
+//
+// Two ways to finish an iteration:
+//   gn_arrive_and_solve   the last CTA to arrive solves and writes z to global
+//                         memory (one launch per iteration)
+//   gn_allreduce_solve    a grid barrier, then every CTA reads the sums and
+//                         solves the same system itself, keeping z in shared
+//                         memory (all iterations in one cooperative launch:
+//                         no second broadcast of z through global memory)
 #pragma once
 
 #include "device_common.cuh"
@@ -31,10 +38,12 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 }
 
 struct GnShared {
-    double sum[kMaxR * (kMaxR + 1) / 2 + kMaxR + 1];
+    double sum[kGnStrideMax];
     double A[kMaxR * kMaxR];
     double y[kMaxR];
     double inv[kMaxR];
+    double z[kMaxR];          // gn_allreduce_solve: z of the current iteration
+    double z0[kMaxR];         //   and z at the start of the run
     int singular;
     int is_last;
 };
@@ -88,6 +97,74 @@ __device__ inline int gn_solve_warp(GnShared &sh, int r) {
     return 0;
 }
 
+// Builds A + damping I and y = -b from the sums in sh.sum and solves in
+// warp 0; leaves dz in sh.y and the outcome in sh.singular.
+__device__ inline void gn_build_and_solve(const GnArgs &g, int r, int *status, GnShared &sh) {
+    const int tid = threadIdx.x;
+    const int T = r * (r + 1) / 2;
+    for (int idx = tid; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, j = idx - i * r;
+        const int e = i <= j ? tri_index(i, j, r) : tri_index(j, i, r);
+        sh.A[idx] = sh.sum[e] + (i == j ? g.damping : 0.0);
+    }
+    for (int k = tid; k < r; k += blockDim.x) sh.y[k] = -sh.sum[T + k];
+    __syncthreads();
+    if (tid < 32) {
+        const int sing = gn_solve_warp(sh, r);
+        if (tid == 0) {
+            sh.singular = sing;
+            if (sing) set_status(status, NSF_ERR_SINGULAR);
+        }
+    }
+    __syncthreads();
+}
+
+// Called by every thread of every CTA of a cooperative launch with the CTA's
+// float64 partial sums of iteration `it` in `part` and the iteration's z in
+// sh.z (sh.z0: z at the start of the run).  Sums go to g.gsum[it & 1]; after
+// the grid barrier every CTA reads them, and the last CTA to read clears that
+// buffer (its next use is two iterations on, behind another barrier).  Every
+// CTA then solves the same system and moves sh.z to the next iterate; CTA 0
+// writes the per-iteration taps and, after the last iteration, z_out and
+// z_prev_out.  Returns false if the barrier wait ran out.
+__device__ inline bool gn_allreduce_solve(const GnArgs &g, int r, int it, int *status,
+                                          GnShared &sh, const double *part) {
+    const int tid = threadIdx.x;
+    const int stride = r * (r + 1) / 2 + r + 1;
+    const int buf = it & 1;
+    double *gsum = g.gsum + (size_t)buf * kGnStrideMax;
+    for (int e = tid; e < stride; e += blockDim.x) atomicAdd(&gsum[e], part[e]);
+    if (!grid_barrier(g.bar, status)) return false;
+    for (int e = tid; e < stride; e += blockDim.x) sh.sum[e] = __ldcg(&gsum[e]);
+    __syncthreads();
+    if (tid == 0) sh.is_last = atomicAdd(&g.readers[buf], 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (sh.is_last) {
+        for (int e = tid; e < stride; e += blockDim.x) gsum[e] = 0.0;
+        if (tid == 0) g.readers[buf] = 0;
+    }
+    gn_build_and_solve(g, r, status, sh);
+    const bool fin = it == g.iters - 1;
+    for (int k = tid; k < r; k += blockDim.x) {
+        const double z0 = sh.z[k];
+        double zn = sh.singular ? z0 : z0 + sh.y[k];
+        if (!isfinite(zn)) {
+            set_status(status, NSF_ERR_NONFINITE);
+            zn = z0;
+        }
+        sh.z[k] = zn;
+        if (blockIdx.x == 0) {
+            if (g.z_taps) g.z_taps[(size_t)it * r + k] = zn;
+            if (fin) {
+                if (g.z_prev_out) g.z_prev_out[k] = sh.z0[k];
+                g.z_out[k] = zn;
+            }
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // Called by every thread of every CTA with the CTA's float64 partial sums of
 // iteration `it` in `part` (shared memory, gn_partial_stride(r) values).  The
 // partials are added into g.gsum with float64 atomics; the last CTA to arrive
@@ -117,21 +194,7 @@ __device__ inline bool gn_arrive_and_solve(const GnArgs &g, int r, int it, int *
         g.gsum[e] = 0.0;                   // ready for the next iteration / launch
     }
     __syncthreads();
-    for (int idx = tid; idx < r * r; idx += nthreads) {
-        int i = idx / r, j = idx - i * r;
-        int e = i <= j ? tri_index(i, j, r) : tri_index(j, i, r);
-        sh.A[idx] = sh.sum[e] + (i == j ? g.damping : 0.0);
-    }
-    for (int k = tid; k < r; k += nthreads) sh.y[k] = -sh.sum[T + k];
-    __syncthreads();
-    if (tid < 32) {
-        const int sing = gn_solve_warp(sh, r);
-        if (tid == 0) {
-            sh.singular = sing;
-            if (sing) set_status(status, NSF_ERR_SINGULAR);
-        }
-    }
-    __syncthreads();
+    gn_build_and_solve(g, r, status, sh);
     const bool singular = sh.singular != 0;
 
     const bool fin = it == g.iters - 1;

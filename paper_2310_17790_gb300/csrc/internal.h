@@ -10,6 +10,9 @@
 namespace nsf {
 
 constexpr int kMaxR = NSF_MAX_R;
+// float64 partial sums of one Gauss-Newton iteration (J^T J upper triangle,
+// J^T res, |res|^2) for the largest latent dimension
+constexpr int kGnStrideMax = kMaxR * (kMaxR + 1) / 2 + kMaxR + 1;
 constexpr int kMaxWidth = NSF_MAX_WIDTH;
 constexpr int kMaxDepth = NSF_MAX_DEPTH;
 constexpr int kOutDim[3] = {3, 6, 9};
@@ -48,12 +51,10 @@ struct Ctl {
     int n_p_atomic;     // active particle blocks of the current step
     int n_g_atomic;     // active grid blocks of the current step
     int pad0[29];
-    // grid barrier of the fused MPM kernel; the arrival counter and the
-    // generation word the waiting CTAs poll sit in separate 128-byte lines
-    unsigned bar_count;
+    // arrival word of the fused MPM kernel's grid barrier, alone in its
+    // 128-byte line
+    unsigned bar;
     unsigned pad1[31];
-    unsigned bar_gen;
-    unsigned pad2[31];
 };
 
 // Sparse-in-use, dense-in-address background grid.  Nodes are stored
@@ -99,14 +100,14 @@ struct GnArgs {
     int target_ld;
     int iters;                // Gauss-Newton iterations of the run
     const double *z_start;    // z at the start of the run (iteration 0 input)
-    double *z_buf;            // z between iterations (workspace)
+    double *z_buf;            // z between iterations (one launch per iteration)
     double *z_out;            // z after the last iteration (may alias z_start)
     double *z_prev_out;       // if non-null: receives z_start after the last iteration
     double *z_taps;           // [iters][r] optional copy of z after every iteration
-    double *partials;         // [grid][gn_partial_stride(r)] (unused; kept for layout)
-    double *gsum;             // [gn_partial_stride(r)] float64 sums, zero before and after
-    int *counter;             // arrival counter, zero before and after
-    int *flag;                // iteration release flag (persistent kernel), zero before and after
+    double *gsum;             // [2][kGnStrideMax] float64 sums, zero before and after
+    int *counter;             // arrival ticket (one launch per iteration), zero before and after
+    unsigned *bar;            // grid-barrier arrival word (all iterations in one launch)
+    int *readers;             // [2] readers of gsum[0], gsum[1]; zero before and after
     double damping;
 };
 int gn_partial_stride(int r);

@@ -29,43 +29,7 @@ namespace nsf {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on a barrier wait
 
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Grid-wide barrier of a cooperative launch: arrival counter + generation.
-// Returns false (and records NSF_ERR_ITER_CAP) if the wait timed out.
-__device__ bool grid_sync(Ctl *ctl, int *status) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        s_ok = 1;
-        volatile unsigned *gen = &ctl->bar_gen;
-        const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
-            ctl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = now_ns();
-            while (*gen == g0) {
-                if (now_ns() - t0 > kWaitNs) {
-                    set_status(status, NSF_ERR_ITER_CAP);
-                    s_ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 __device__ __forceinline__ bool cta0_thread0() { return blockIdx.x == 0 && threadIdx.x == 0; }
 
@@ -415,9 +379,9 @@ __device__ bool p2g_and_grid(const GridWs &g, const GridParams &gp, const Args &
                              int epoch, float *tap_mp, float *tap_v, int *status) {
     const float stress_k = -a.dt * a.vol0 * 4.f * gp.inv_dx * gp.inv_dx;
     phase_p2g(g, gp, a, stress_k, epoch, status);
-    if (!grid_sync(g.ctl, status)) return false;
+    if (!grid_barrier(&g.ctl->bar, status)) return false;
     phase_activate(g, __ldcg(&g.ctl->n_p_atomic), epoch);
-    if (!grid_sync(g.ctl, status)) return false;
+    if (!grid_barrier(&g.ctl->bar, status)) return false;
     if (cta0_thread0()) g.ctl->n_p_atomic = 0;          // every CTA has read it
     phase_grid(g, gp, a.dt, t, tap_mp, tap_v);
     return true;
@@ -428,7 +392,7 @@ k_mpm_latent(GridWs g, GridParams gp, P2gLatentArgs a, int n_S, double t, float 
              float *tap_mp, float *tap_v, int *status) {
     const int epoch = __ldcg(&g.ctl->epoch) + 1;
     if (!p2g_and_grid(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
-    if (!grid_sync(g.ctl, status)) return;
+    if (!grid_barrier(&g.ctl->bar, status)) return;
     phase_g2p_latent(g, gp, a.X, a.u, a.n, n_S, a.dt, d_next, status);
     if (cta0_thread0()) {
         g.ctl->n_g_atomic = 0;                            // read by the grid phase only
