@@ -103,23 +103,40 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
     return w;
 }
 
-// Gauss-Newton control words: the arrival ticket, the grid-barrier word and
-// the two reader counters, each in its own 128-byte line.
-constexpr size_t kGnCtlBytes = 384;
+// Gauss-Newton scratch of a workspace: z between iterations and the float64
+// sums (one launch per iteration, FP32 path), the per-CTA float-float slots
+// (cooperative tensor-core path) and the control words (arrival ticket and
+// grid-barrier word, each in its own 128-byte line).
+struct GnLayout {
+    size_t zgn, gsum, slots, ctl;
+};
 
-GnArgs gn_args(char *gnctl, double *gsum, double *zgn) {
+GnLayout carve_gn(Carver &c, const nsf_fields *f, int n_S) {
+    GnLayout L;
+    L.zgn = c.take(NSF_MAX_R * 8);
+    L.gsum = c.take((size_t)kGnStrideMax * 8);
+    size_t slots = 0;
+    if (f->dev.precision == NSF_PREC_BF16)
+        slots = 2 * (size_t)jac_grid_size_tc(f->dev, n_S) * gn_partial_stride(f->desc.r) * 8;
+    L.slots = c.take(slots);
+    L.ctl = c.take(256);
+    return L;
+}
+
+GnArgs gn_args(char *base, const GnLayout &L) {
     GnArgs g{};
-    g.gsum = gsum;
-    g.z_buf = zgn;
-    g.counter = reinterpret_cast<int *>(gnctl);
-    g.bar = reinterpret_cast<unsigned *>(gnctl + 128);
-    g.readers = reinterpret_cast<int *>(gnctl + 256);
+    g.z_buf = reinterpret_cast<double *>(base + L.zgn);
+    g.gsum = reinterpret_cast<double *>(base + L.gsum);
+    g.slots = reinterpret_cast<float2 *>(base + L.slots);
+    g.counter = reinterpret_cast<int *>(base + L.ctl);
+    g.bar = reinterpret_cast<unsigned *>(base + L.ctl + 128);
     return g;
 }
 
 struct LatentLayout {
     GridLayout grid;
-    size_t u[2], tau, C, dnext, zgn, gsum, gnctl;
+    size_t u[2], tau, C, dnext;
+    GnLayout gn;
     size_t total;
 };
 
@@ -133,15 +150,15 @@ LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc) {
     L.tau = c.take(6 * n * 4);
     L.C = c.take(9 * n * 4);
     L.dnext = c.take(3 * (size_t)sc->n_S * 4);
-    L.zgn = c.take(NSF_MAX_R * 8);
-    L.gsum = c.take(2 * (size_t)kGnStrideMax * 8);
-    L.gnctl = c.take(kGnCtlBytes);
+    L.gn = carve_gn(c, f, sc->n_S);
     L.total = c.off;
     return L;
 }
 
 struct ProjectLayout {
-    size_t target, u, zgn, gsum, gnctl, total;
+    size_t target, u;
+    GnLayout gn;
+    size_t total;
 };
 
 ProjectLayout project_layout(const nsf_fields *f, int n_S) {
@@ -149,9 +166,7 @@ ProjectLayout project_layout(const nsf_fields *f, int n_S) {
     ProjectLayout L;
     L.target = c.take(3 * (size_t)n_S * 4);
     L.u = c.take(3 * (size_t)n_S * 4);
-    L.zgn = c.take(NSF_MAX_R * 8);
-    L.gsum = c.take(2 * (size_t)kGnStrideMax * 8);
-    L.gnctl = c.take(kGnCtlBytes);
+    L.gn = carve_gn(c, f, n_S);
     L.total = c.off;
     return L;
 }
@@ -238,8 +253,7 @@ bool valid_gn(const nsf_gn_opts *o) {
 // shared memory a field needs on the tensor-core path (0: does not fit).
 namespace nsf {
 size_t tc_layer_elems(int rows_pad, int k);
-void tc_pack_layer(const float *W, const float *b, int rows, int rows_pad, int k,
-                   __nv_bfloat16 *dst);
+void tc_pack_layer(const float *W, int rows, int rows_pad, int k, __nv_bfloat16 *dst);
 size_t tc_smem_bytes(int r, int width, int depth);
 }
 
@@ -308,7 +322,7 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 if (bf16) {
                     size_t o2 = hbuf.size();
                     hbuf.resize(o2 + tc_layer_elems(16, W));
-                    tc_pack_layer(Wm.data(), src + pos, od, 16, W, hbuf.data() + o2);
+                    tc_pack_layer(Wm.data(), od, 16, W, hbuf.data() + o2);
                 }
             } else {
                 std::vector<float> Wt((size_t)W * W);
@@ -318,7 +332,7 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
                 if (bf16) {
                     size_t o2 = hbuf.size();
                     hbuf.resize(o2 + tc_layer_elems(W, W));
-                    tc_pack_layer(Wm.data(), src + pos, W, W, W, hbuf.data() + o2);
+                    tc_pack_layer(Wm.data(), W, W, W, hbuf.data() + o2);
                 }
             }
             for (int q = 0; q < o; ++q)
@@ -435,7 +449,6 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
     float *tau = reinterpret_cast<float *>(base + L.tau);
     float *C9 = reinterpret_cast<float *>(base + L.C);
     float *dnext = reinterpret_cast<float *>(base + L.dnext);
-    double *zgn = reinterpret_cast<double *>(base + L.zgn);
     const float *Xoff = f->dev.residual_g ? sc->d_X : nullptr;
     // ub[1] holds g(X, z_prev) between calls; step s writes g(X, z_n) to ub[s & 1 ^ 0]
     // and reads g(X, z_{n-1}) from the other buffer.
@@ -489,7 +502,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         // 3. network inversion (§5.3), Gauss-Newton from z_n
         NSF_CUDA_TRY(ev(tev, tev ? taps->ev_begin : nullptr, NSF_STAGE_GN));
         {
-            GnArgs gn = gn_args(base + L.gnctl, reinterpret_cast<double *>(base + L.gsum), zgn);
+            GnArgs gn = gn_args(base, L.gn);
             gn.target = dnext;
             gn.target_ld = nS;
             gn.iters = opts->iters;
@@ -527,12 +540,11 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
     char *base = static_cast<char *>(d_ws);
     float *target = reinterpret_cast<float *>(base + L.target);
     float *u = reinterpret_cast<float *>(base + L.u);
-    double *zgn = reinterpret_cast<double *>(base + L.zgn);
     // residual fields work on displacements: d = x_target - X
     if (f->dev.residual_g) NSF_CUDA_TRY(axpy(target, d_x_target, d_X_S, -1.f, 3 * n_S, s));
     else NSF_CUDA_TRY(cudaMemcpyAsync(target, d_x_target, 12 * (size_t)n_S, cudaMemcpyDeviceToDevice, s));
     {
-        GnArgs gn = gn_args(base + L.gnctl, reinterpret_cast<double *>(base + L.gsum), zgn);
+        GnArgs gn = gn_args(base, L.gn);
         gn.target = target;
         gn.target_ld = n_S;
         gn.iters = opts->iters;

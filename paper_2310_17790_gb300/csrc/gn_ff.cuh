@@ -1,0 +1,200 @@
+// Gauss-Newton iterations of the network inversion (§5.3, Eq. 9) inside the
+// cooperative tensor-core Jacobian kernel, in float-float arithmetic (ff.cuh).
+//
+// One iteration, after the CTA's tiles have produced residuals res_p and
+// Jacobian columns J_p (in the O3 rows of the tile):
+//   1. per CTA: partial sums over its points of the entries
+//        [0, T)       J^T J, upper triangle (i <= j), T = r (r + 1) / 2
+//        [T, T + r)   J^T res
+//        [T + r]      |res|^2
+//      each product exact (two_prod), sums in float-float
+//   2. each CTA stores its partials in its own column of a per-iteration-parity
+//      slot array [entry][CTA] (plain stores: no atomics, nothing to clear)
+//   3. grid barrier
+//   4. every CTA adds all CTAs' slots in the same fixed order (so all CTAs
+//      hold bit-identical sums) and solves
+//        (J^T J + damping I) dz = -J^T res
+//      by Gauss-Jordan elimination without pivoting (the matrix is symmetric
+//      positive definite for damping > 0; a non-positive or non-finite pivot
+//      is reported as NSF_ERR_SINGULAR and leaves z unchanged)
+//   5. z <- z + dz in every CTA; CTA 0 writes the taps and the final z.
+// The slot parity alternates: a CTA that has finished iteration it + 1 writes
+// the other parity while slower CTAs may still read iteration it's slots, and
+// it can only come back to this parity after the barrier of iteration it + 1,
+// which every reader passes after reading.
+#pragma once
+
+#include "device_common.cuh"
+#include "ff.cuh"
+
+namespace nsf {
+
+struct GnFF {
+    ff part[kGnStrideMax];          // this CTA's sums over its tiles
+    ff sum[kGnStrideMax];           // sums over all CTAs
+    ff M[kMaxR * (kMaxR + 1)];      // [A + damping I | -b], row-major, r + 1 columns
+    ff z[kMaxR];                    // current iterate
+    double z0[kMaxR];               // z at the start of the run
+    ff damping;
+    int singular;
+};
+
+// CTAs of a cooperative Gauss-Newton launch are at most one per SM; a lane
+// adds the slots of CTAs lane, lane + 32, ...
+constexpr int kGnMaxSlotsPerLane = 5;
+constexpr int kGnMaxCtas = 32 * kGnMaxSlotsPerLane;
+
+__device__ __forceinline__ int gn_stride(int r) { return r * (r + 1) / 2 + r + 1; }
+
+// (i, j) of entry e < T of the packed upper triangle.
+__device__ __forceinline__ void gn_tri_pair(int e, int r, int &i, int &j) {
+    int ii = 0, off = 0;
+    while (e >= off + (r - ii)) {
+        off += r - ii;
+        ++ii;
+    }
+    i = ii;
+    j = ii + (e - off);
+}
+
+__device__ __forceinline__ ff ff_dot3(const float *a, const float *b) {
+    ff s = ff_prod(a[0], b[0]);
+    s = ff_add(s, ff_prod(a[1], b[1]));
+    return ff_add(s, ff_prod(a[2], b[2]));
+}
+
+// Start of a run: z from global memory, CTA sums cleared.
+__device__ inline void gn_ff_begin(const GnArgs &g, int r, GnFF &sh) {
+    const int tid = threadIdx.x;
+    if (tid < r) {
+        const double z = __ldcg(&g.z_start[tid]);
+        sh.z0[tid] = z;
+        sh.z[tid] = ff_from_double(z);
+    }
+    if (tid == 0) sh.damping = ff_from_double(g.damping);
+    for (int e = tid; e < gn_stride(r); e += blockDim.x) sh.part[e] = ff{0.f, 0.f};
+}
+
+// Step 1 for one tile of P points: point q's residual is O3 row q, its
+// Jacobian column k O3 row 32 + k P + q (three values per row); npts points
+// are live.  Every thread calls.
+__device__ inline void gn_ff_tile_partials(const float *O3, int P, int npts, int r, GnFF &sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int T = r * (r + 1) / 2, S = gn_stride(r);
+    for (int e = warp; e < S; e += nwarps) {
+        int i = -1, j = -1;
+        if (e < T) gn_tri_pair(e, r, i, j);
+        ff acc{0.f, 0.f};
+        for (int q = lane; q < npts; q += 32) {
+            const float *res = O3 + q * 3;
+            if (e < T) acc = ff_add(acc, ff_dot3(O3 + (32 + i * P + q) * 3, O3 + (32 + j * P + q) * 3));
+            else if (e < T + r) acc = ff_add(acc, ff_dot3(O3 + (32 + (e - T) * P + q) * 3, res));
+            else acc = ff_add(acc, ff_dot3(res, res));
+        }
+        acc = npts <= 16 ? ff_half_warp_sum(acc) : ff_warp_sum(acc);
+        if (lane == 0) sh.part[e] = ff_add(sh.part[e], acc);
+    }
+}
+
+// Gauss-Jordan on the augmented r x (r + 1) system in sh.M by warp 0; leaves
+// dz_i = M[i][r] / M[i][i] in sh.M[i][r] and sh.singular set on failure.
+// (A variant holding each row in a lane's registers and broadcasting the
+// pivot row by shuffles measured slower.)
+__device__ inline void gn_ff_solve_warp(int r, GnFF &sh) {
+    const int lane = threadIdx.x & 31;
+    const int C = r + 1;
+    int singular = 0;
+    for (int k = 0; k < r; ++k) {
+        const ff piv = sh.M[k * C + k];
+        if (!(piv.hi > 0.f) || !ff_isfinite(piv)) {
+            singular = 1;
+            break;
+        }
+        const ff inv = ff_rcp(piv);
+        // rows i != k, columns j > k: M[i][j] -= M[i][k] / M[k][k] * M[k][j]
+        const int ncol = C - 1 - k;
+        for (int idx = lane; idx < (r - 1) * ncol; idx += 32) {
+            int i = idx / ncol;
+            const int j = k + 1 + (idx - i * ncol);
+            i += i >= k ? 1 : 0;
+            const ff m = ff_mul(sh.M[i * C + k], inv);
+            sh.M[i * C + j] = ff_sub(sh.M[i * C + j], ff_mul(m, sh.M[k * C + j]));
+        }
+        __syncwarp();
+    }
+    if (!singular && lane < r)
+        sh.M[lane * C + r] = ff_mul(sh.M[lane * C + r], ff_rcp(sh.M[lane * C + lane]));
+    if (lane == 0) sh.singular = singular;
+    __syncwarp();
+}
+
+// Steps 2-5.  Every thread of every CTA calls; returns false if the barrier
+// wait ran out.
+__device__ inline bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, int *status,
+                                              GnFF &sh) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int T = r * (r + 1) / 2, S = gn_stride(r), C = r + 1;
+    const int nblk = gridDim.x;
+    float2 *slots = g.slots + (size_t)(it & 1) * nblk * S;
+    __syncthreads();
+    // entry-major: the CTAs' values of one entry are contiguous, so the
+    // reads below are coalesced
+    for (int e = tid; e < S; e += blockDim.x)
+        __stcg(&slots[(size_t)e * nblk + blockIdx.x], make_float2(sh.part[e].hi, sh.part[e].lo));
+    if (!grid_barrier(g.bar, status)) return false;
+    // all loads of a lane first (one memory round trip), then the sums
+    for (int e = warp; e < S; e += nwarps) {
+        float2 v[kGnMaxSlotsPerLane];
+#pragma unroll
+        for (int k = 0; k < kGnMaxSlotsPerLane; ++k) {
+            const int b = lane + 32 * k;
+            v[k] = b < nblk ? __ldcg(&slots[(size_t)e * nblk + b]) : make_float2(0.f, 0.f);
+        }
+        ff acc{v[0].x, v[0].y};
+#pragma unroll
+        for (int k = 1; k < kGnMaxSlotsPerLane; ++k) acc = ff_add(acc, ff{v[k].x, v[k].y});
+        acc = ff_warp_sum(acc);
+        if (lane == 0) sh.sum[e] = acc;
+    }
+    __syncthreads();
+    const ff damp = sh.damping;
+    for (int idx = tid; idx < r * C; idx += blockDim.x) {
+        const int i = idx / C, j = idx - i * C;
+        ff v;
+        if (j == r) {
+            v = ff_neg(sh.sum[T + i]);
+        } else {
+            v = sh.sum[i <= j ? tri_index(i, j, r) : tri_index(j, i, r)];
+            if (i == j) v = ff_add(v, damp);
+        }
+        sh.M[idx] = v;
+    }
+    for (int e = tid; e < S; e += blockDim.x) sh.part[e] = ff{0.f, 0.f};
+    __syncthreads();
+    if (tid < 32) gn_ff_solve_warp(r, sh);
+    __syncthreads();
+    const bool singular = sh.singular != 0;
+    if (singular && tid == 0) set_status(status, NSF_ERR_SINGULAR);
+    const bool fin = it == g.iters - 1;
+    if (tid < r) {
+        const ff z0 = sh.z[tid];
+        ff zn = singular ? z0 : ff_add(z0, sh.M[tid * C + r]);
+        if (!ff_isfinite(zn)) {
+            set_status(status, NSF_ERR_NONFINITE);
+            zn = z0;
+        }
+        sh.z[tid] = zn;
+        if (blockIdx.x == 0) {
+            const double zd = ff_to_double(zn);
+            if (g.z_taps) g.z_taps[(size_t)it * r + tid] = zd;
+            if (fin) {
+                if (g.z_prev_out) g.z_prev_out[tid] = sh.z0[tid];
+                g.z_out[tid] = zd;
+            }
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+}  // namespace nsf

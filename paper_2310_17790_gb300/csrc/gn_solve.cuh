@@ -10,13 +10,10 @@
 // A non-positive or non-finite pivot sets NSF_ERR_SINGULAR and leaves z
 // unchanged for that iteration.
 //
-// Two ways to finish an iteration:
-//   gn_arrive_and_solve   the last CTA to arrive solves and writes z to global
-//                         memory (one launch per iteration)
-//   gn_allreduce_solve    a grid barrier, then every CTA reads the sums and
-//                         solves the same system itself, keeping z in shared
-//                         memory (all iterations in one cooperative launch:
-//                         no second broadcast of z through global memory)
+// This file serves the one-launch-per-iteration path of the FP32 Jacobian
+// kernel: the last CTA to arrive solves and writes z to global memory.  The
+// cooperative tensor-core kernel runs all iterations in one launch with the
+// float-float variant in gn_ff.cuh.
 #pragma once
 
 #include "device_common.cuh"
@@ -42,8 +39,6 @@ struct GnShared {
     double A[kMaxR * kMaxR];
     double y[kMaxR];
     double inv[kMaxR];
-    double z[kMaxR];          // gn_allreduce_solve: z of the current iteration
-    double z0[kMaxR];         //   and z at the start of the run
     int singular;
     int is_last;
 };
@@ -117,52 +112,6 @@ __device__ inline void gn_build_and_solve(const GnArgs &g, int r, int *status, G
         }
     }
     __syncthreads();
-}
-
-// Called by every thread of every CTA of a cooperative launch with the CTA's
-// float64 partial sums of iteration `it` in `part` and the iteration's z in
-// sh.z (sh.z0: z at the start of the run).  Sums go to g.gsum[it & 1]; after
-// the grid barrier every CTA reads them, and the last CTA to read clears that
-// buffer (its next use is two iterations on, behind another barrier).  Every
-// CTA then solves the same system and moves sh.z to the next iterate; CTA 0
-// writes the per-iteration taps and, after the last iteration, z_out and
-// z_prev_out.  Returns false if the barrier wait ran out.
-__device__ inline bool gn_allreduce_solve(const GnArgs &g, int r, int it, int *status,
-                                          GnShared &sh, const double *part) {
-    const int tid = threadIdx.x;
-    const int stride = r * (r + 1) / 2 + r + 1;
-    const int buf = it & 1;
-    double *gsum = g.gsum + (size_t)buf * kGnStrideMax;
-    for (int e = tid; e < stride; e += blockDim.x) atomicAdd(&gsum[e], part[e]);
-    if (!grid_barrier(g.bar, status)) return false;
-    for (int e = tid; e < stride; e += blockDim.x) sh.sum[e] = __ldcg(&gsum[e]);
-    __syncthreads();
-    if (tid == 0) sh.is_last = atomicAdd(&g.readers[buf], 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (sh.is_last) {
-        for (int e = tid; e < stride; e += blockDim.x) gsum[e] = 0.0;
-        if (tid == 0) g.readers[buf] = 0;
-    }
-    gn_build_and_solve(g, r, status, sh);
-    const bool fin = it == g.iters - 1;
-    for (int k = tid; k < r; k += blockDim.x) {
-        const double z0 = sh.z[k];
-        double zn = sh.singular ? z0 : z0 + sh.y[k];
-        if (!isfinite(zn)) {
-            set_status(status, NSF_ERR_NONFINITE);
-            zn = z0;
-        }
-        sh.z[k] = zn;
-        if (blockIdx.x == 0) {
-            if (g.z_taps) g.z_taps[(size_t)it * r + k] = zn;
-            if (fin) {
-                if (g.z_prev_out) g.z_prev_out[k] = sh.z0[k];
-                g.z_out[k] = zn;
-            }
-        }
-    }
-    __syncthreads();
-    return true;
 }
 
 // Called by every thread of every CTA with the CTA's float64 partial sums of

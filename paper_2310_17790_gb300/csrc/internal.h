@@ -107,7 +107,7 @@ struct GnArgs {
     double *gsum;             // [2][kGnStrideMax] float64 sums, zero before and after
     int *counter;             // arrival ticket (one launch per iteration), zero before and after
     unsigned *bar;            // grid-barrier arrival word (all iterations in one launch)
-    int *readers;             // [2] readers of gsum[0], gsum[1]; zero before and after
+    float2 *slots;            // [2][gn_partial_stride(r)][grid] per-CTA float-float sums
     double damping;
 };
 int gn_partial_stride(int r);
