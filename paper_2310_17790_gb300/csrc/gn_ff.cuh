@@ -44,6 +44,11 @@ struct GnFF {
 constexpr int kGnMaxSlotsPerLane = 5;
 constexpr int kGnMaxCtas = 32 * kGnMaxSlotsPerLane;
 
+// The CTA's Gauss-Newton state.  A namespace-scope shared variable, so that
+// the out-of-line helpers below address it as shared memory (a reference
+// passed to them would be a generic pointer).
+static __shared__ GnFF g_gn;
+
 __device__ __forceinline__ int gn_stride(int r) { return r * (r + 1) / 2 + r + 1; }
 
 // (i, j) of entry e < T of the packed upper triangle.
@@ -64,7 +69,8 @@ __device__ __forceinline__ ff ff_dot3(const float *a, const float *b) {
 }
 
 // Start of a run: z from global memory, CTA sums cleared.
-__device__ inline void gn_ff_begin(const GnArgs &g, int r, GnFF &sh) {
+__device__ inline void gn_ff_begin(const GnArgs &g, int r) {
+    GnFF &sh = g_gn;
     const int tid = threadIdx.x;
     if (tid < r) {
         const double z = __ldcg(&g.z_start[tid]);
@@ -75,10 +81,11 @@ __device__ inline void gn_ff_begin(const GnArgs &g, int r, GnFF &sh) {
     for (int e = tid; e < gn_stride(r); e += blockDim.x) sh.part[e] = ff{0.f, 0.f};
 }
 
-// Step 1 for one tile of P points: point q's residual is O3 row q, its
-// Jacobian column k O3 row 32 + k P + q (three values per row); npts points
-// are live.  Every thread calls.
-__device__ inline void gn_ff_tile_partials(const float *O3, int P, int npts, int r, GnFF &sh) {
+// Step 1 for one tile: point q's residual is O3 row q L, its Jacobian column
+// k O3 row q L + 1 + k (three values per row); npts points are live.  Every
+// thread calls.
+__device__ __noinline__ void gn_ff_tile_partials(const float *O3, int L, int npts, int r) {
+    GnFF &sh = g_gn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int T = r * (r + 1) / 2, S = gn_stride(r);
     for (int e = warp; e < S; e += nwarps) {
@@ -86,9 +93,9 @@ __device__ inline void gn_ff_tile_partials(const float *O3, int P, int npts, int
         if (e < T) gn_tri_pair(e, r, i, j);
         ff acc{0.f, 0.f};
         for (int q = lane; q < npts; q += 32) {
-            const float *res = O3 + q * 3;
-            if (e < T) acc = ff_add(acc, ff_dot3(O3 + (32 + i * P + q) * 3, O3 + (32 + j * P + q) * 3));
-            else if (e < T + r) acc = ff_add(acc, ff_dot3(O3 + (32 + (e - T) * P + q) * 3, res));
+            const float *res = O3 + q * L * 3;
+            if (e < T) acc = ff_add(acc, ff_dot3(res + (1 + i) * 3, res + (1 + j) * 3));
+            else if (e < T + r) acc = ff_add(acc, ff_dot3(res + (1 + e - T) * 3, res));
             else acc = ff_add(acc, ff_dot3(res, res));
         }
         acc = npts <= 16 ? ff_half_warp_sum(acc) : ff_warp_sum(acc);
@@ -98,29 +105,58 @@ __device__ inline void gn_ff_tile_partials(const float *O3, int P, int npts, int
 
 // Gauss-Jordan on the augmented r x (r + 1) system in sh.M by warp 0; leaves
 // dz_i = M[i][r] / M[i][i] in sh.M[i][r] and sh.singular set on failure.
-// (A variant holding each row in a lane's registers and broadcasting the
-// pivot row by shuffles measured slower.)
-__device__ inline void gn_ff_solve_warp(int r, GnFF &sh) {
+// Step k subtracts (M[i][k] / M[k][k]) times row k from every row i != k, in
+// the columns j > k.  For r <= 7 lane = (row i = lane % 8, column slot lane / 8)
+// and each lane updates columns k + 1 + slot and k + 5 + slot, independent of
+// each other; larger r loop over the entries.  (Keeping each row in one lane's
+// registers and broadcasting the pivot row by shuffles measured slower.)
+__device__ __noinline__ void gn_ff_solve_warp(int r) {
+    GnFF &sh = g_gn;
     const int lane = threadIdx.x & 31;
     const int C = r + 1;
     int singular = 0;
-    for (int k = 0; k < r; ++k) {
-        const ff piv = sh.M[k * C + k];
-        if (!(piv.hi > 0.f) || !ff_isfinite(piv)) {
-            singular = 1;
-            break;
+    if (r <= 7) {
+        const int i = lane & 7, cs = lane >> 3;
+        for (int k = 0; k < r; ++k) {
+            const ff piv = sh.M[k * C + k];
+            if (!(piv.hi > 0.f) || !ff_isfinite(piv)) {
+                singular = 1;
+                break;
+            }
+            const int j0 = k + 1 + cs, j1 = j0 + 4;
+            const bool act = i < r && i != k;
+            ff m{0.f, 0.f}, a0{0.f, 0.f}, a1{0.f, 0.f}, p0{0.f, 0.f}, p1{0.f, 0.f};
+            if (act) {
+                m = sh.M[i * C + k];
+                if (j0 < C) { a0 = sh.M[i * C + j0]; p0 = sh.M[k * C + j0]; }
+                if (j1 < C) { a1 = sh.M[i * C + j1]; p1 = sh.M[k * C + j1]; }
+            }
+            __syncwarp();
+            if (act) {
+                m = ff_mul(m, ff_rcp(piv));
+                if (j0 < C) sh.M[i * C + j0] = ff_sub(a0, ff_mul(m, p0));
+                if (j1 < C) sh.M[i * C + j1] = ff_sub(a1, ff_mul(m, p1));
+            }
+            __syncwarp();
         }
-        const ff inv = ff_rcp(piv);
-        // rows i != k, columns j > k: M[i][j] -= M[i][k] / M[k][k] * M[k][j]
-        const int ncol = C - 1 - k;
-        for (int idx = lane; idx < (r - 1) * ncol; idx += 32) {
-            int i = idx / ncol;
-            const int j = k + 1 + (idx - i * ncol);
-            i += i >= k ? 1 : 0;
-            const ff m = ff_mul(sh.M[i * C + k], inv);
-            sh.M[i * C + j] = ff_sub(sh.M[i * C + j], ff_mul(m, sh.M[k * C + j]));
+    } else {
+        for (int k = 0; k < r; ++k) {
+            const ff piv = sh.M[k * C + k];
+            if (!(piv.hi > 0.f) || !ff_isfinite(piv)) {
+                singular = 1;
+                break;
+            }
+            const ff inv = ff_rcp(piv);
+            const int ncol = C - 1 - k;
+            for (int idx = lane; idx < (r - 1) * ncol; idx += 32) {
+                int i = idx / ncol;
+                const int j = k + 1 + (idx - i * ncol);
+                i += i >= k ? 1 : 0;
+                const ff m = ff_mul(sh.M[i * C + k], inv);
+                sh.M[i * C + j] = ff_sub(sh.M[i * C + j], ff_mul(m, sh.M[k * C + j]));
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
     if (!singular && lane < r)
         sh.M[lane * C + r] = ff_mul(sh.M[lane * C + r], ff_rcp(sh.M[lane * C + lane]));
@@ -130,8 +166,8 @@ __device__ inline void gn_ff_solve_warp(int r, GnFF &sh) {
 
 // Steps 2-5.  Every thread of every CTA calls; returns false if the barrier
 // wait ran out.
-__device__ inline bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, int *status,
-                                              GnFF &sh) {
+__device__ __noinline__ bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, int *status) {
+    GnFF &sh = g_gn;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int T = r * (r + 1) / 2, S = gn_stride(r), C = r + 1;
     const int nblk = gridDim.x;
@@ -171,7 +207,7 @@ __device__ inline bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, in
     }
     for (int e = tid; e < S; e += blockDim.x) sh.part[e] = ff{0.f, 0.f};
     __syncthreads();
-    if (tid < 32) gn_ff_solve_warp(r, sh);
+    if (tid < 32) gn_ff_solve_warp(r);
     __syncthreads();
     const bool singular = sh.singular != 0;
     if (singular && tid == 0) set_status(status, NSF_ERR_SINGULAR);

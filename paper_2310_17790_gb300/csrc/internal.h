@@ -23,10 +23,10 @@ constexpr int kOutDim[3] = {3, 6, 9};
 //   Wt[l] for hidden layers l = 1 .. depth-1: transposed, [in = width][out = width],
 //   Wout [out_dim][width] row-major, b[l] biases of layer l (l = 0 .. depth).
 // BF16 layout (tensor-core path): one contiguous blob per field holding the
-// hidden matrices l = 1 .. depth-1 and the output matrix (zero-padded to 16
-// rows) as bf16 in the K-major no-swizzle core-matrix order of tcgen05.mma
-// (see fields_tc.cu); it is copied verbatim into shared memory.  W0 and the
-// biases stay FP32 (W0 holding bf16-rounded values).
+// hidden matrices l = 1 .. depth-1 ([out][in]) and the output matrix
+// (zero-padded to 16 rows) as bf16, K-major with the 128-byte swizzle of
+// tcgen05.mma operands (tc_common.cuh); it is copied verbatim into shared
+// memory.  W0 and the biases stay FP32 (W0 holding bf16-rounded values).
 struct FieldDev {
     int width, depth, out_dim;
     const float *W0;
@@ -123,7 +123,8 @@ cudaError_t launch_jacobian_simt(const FieldsDev &fd, const float *X, int n, int
                                  const double *z, float *u, float *dudz,
                                  const GnArgs *gn, int it, int *status, cudaStream_t s);
 
-// Tensor-core BF16 path (fields_tc.cu).
+// Tensor-core BF16 path: value evaluation (fields_tc.cu), Jacobian and
+// Gauss-Newton (jacobian_tc.cu).
 int jac_grid_size_tc(const FieldsDev &fd, int n);
 cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld,
                              int njobs, const FieldJob *jobs, int *status,
@@ -134,8 +135,8 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
                                const double *z, float *u, float *dudz,
                                const GnArgs *gn, int *status, cudaStream_t s);
 
-// MPM step: one cooperative launch each (bin, P2G, grid update, G2P with
-// grid-wide barriers between the phases).  After a barrier timeout
+// MPM step: one cooperative launch each (P2G, block activation, grid update
+// and, for the latent step, G2P, with grid-wide barriers between the phases).  After a barrier timeout
 // (NSF_ERR_ITER_CAP in *status) the workspace's control block is undefined.
 struct P2gLatentArgs {
     const float *X;       // [3][n] or null (non-residual g: u is the position)

@@ -1,0 +1,419 @@
+// Jacobian of the deformation field g (forward mode) and the Gauss-Newton
+// network inversion on the tcgen05 tensor cores (paper §5.3, Eq. 9; App. E:
+// ELU MLP on [X; z]), BF16 operands with FP32 accumulation.
+//
+// Transposed products: the MMA rows are a layer's output neurons and its
+// columns are the tile's point slots.  Each point owns L consecutive columns
+// (L the smallest power of two >= 1 + r): slot 0 carries the value, slot 1 + k
+// the tangent along latent component k (slots beyond r stay zero).  The
+// accumulator D = W_l [h | t_1 .. t_r] then sits in tensor memory with lane =
+// neuron and column = point slot, so the thread that owns neuron j holds a
+// point's pre-activation and all of its tangents in its own registers, and
+// ELU'(a_value) scales the tangents with no exchange between threads.  The
+// thread writes its neuron's row of the next layer's B operand (MN-major:
+// point slots contiguous per neuron).
+//
+// CTA: eight warpgroups.  Warp (index % 4) = q reads TMEM lanes 32 q .. 32 q +
+// 31, i.e. neurons 32 q + lane (and 128 + 32 q + lane from a second
+// accumulator for widths above 128); warpgroup w owns columns [w CW,
+// (w + 1) CW), CW = max(8, L), so a tile has N = 8 CW columns and P = N / L
+// points.  The per-layer latency grows with the columns a thread handles, so
+// tiles stay small (8 points for r >= 3) and a point set spreads over many
+// SMs.  Layer 0 (K = 3 + r) runs on the CUDA cores: value slot W0[:, :3] X
+// + (b0 + W0[:, 3:] z), tangent slot k the column W0[:, 3 + k].  The output
+// layer is an MMA with M = 128 whose first out_dim rows are the output
+// weights.
+//
+// Products with M = 128 read 128 weight rows per K atom; for layers with fewer
+// rows (widths below 128, the output layer's 16 rows, the second half of width
+// 192) the extra rows are whatever follows in shared memory: the next layer's
+// weights or the activation operand, which is placed right after the weights
+// and takes at least 16 KB.  Those rows only produce accumulator lanes that no
+// thread reads.
+//
+// Gauss-Newton (gn_on): all iterations in one cooperative launch; after its
+// tiles every CTA combines the float-float normal equations of all CTAs and
+// solves them itself (gn_ff.cuh), keeping z in shared memory.
+#include "gn_ff.cuh"
+#include "tc_common.cuh"
+
+namespace nsf {
+
+using namespace tc;
+
+namespace {
+
+__host__ __device__ inline int jac_slots(int r) {
+    int L = 2;
+    while (L < 1 + r) L <<= 1;
+    return L;
+}
+__host__ __device__ inline int jac_cw(int r) {
+    const int L = jac_slots(r);
+    return L > 8 ? L : 8;
+}
+__host__ __device__ inline int jac_cols(int r) { return kWG * jac_cw(r); }
+__host__ __device__ inline int jac_points(int r) { return jac_cols(r) / jac_slots(r); }
+__host__ __device__ inline int jac_halves(int W) { return (W + 127) / 128; }
+
+// Shared-memory carve of one CTA (byte offsets from a 1024-aligned base).
+struct JacLayout {
+    int blob, b, w0v, w0t, b0, bias, xs, tg, o3, bars, tmem, total;
+};
+
+__host__ __device__ inline JacLayout jac_layout(int r, int W, int D) {
+    JacLayout L;
+    const int N = jac_cols(r), P = jac_points(r);
+    int o = 0;
+    L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + kMaxOut * W * 2, 1024);
+    // activations (MN-major); at least 16 KB, the reach of the padded rows
+    // of an M = 128 product past the end of the weights
+    L.b = o;    o = align_to(o + (W * N * 2 > 16384 ? W * N * 2 : 16384), 1024);
+    L.w0v = o;  o = align_to(o + W * 16, 16);                  // float4 {w_x, w_y, w_z, c0}
+    L.w0t = o;  o = align_to(o + r * W * 4, 16);               // W0[:, 3 + k] as [k][W]
+    L.b0 = o;   o = align_to(o + W * 4, 16);                   // input-layer bias
+    L.bias = o; o = align_to(o + D * W * 4, 16);               // hidden biases, output bias
+    L.xs = o;   o = align_to(o + P * 16, 16);                  // tile positions
+    L.tg = o;   o = align_to(o + P * 16, 16);                  // tile Gauss-Newton targets
+    L.o3 = o;   o = align_to(o + N * 3 * 4, 16);               // outputs per column
+    L.bars = o; o = align_to(o + 2 * 8, 16);
+    L.tmem = o; o = align_to(o + 16, 16);
+    L.total = o + 1024;
+    return L;
+}
+
+// Byte offset of the 16-byte chunk of B holding neuron k, columns n .. n + 7
+// (n % 8 == 0): MN-major, 64-column blocks 1024 bytes apart, 8-neuron blocks
+// sbo = (N / 64) * 1024 bytes apart.
+__device__ __forceinline__ int b_chunk(int k, int n, int sbo) {
+    return (k >> 3) * sbo + (n >> 6) * 1024 + (k & 7) * 128 + ((((n >> 3) & 7) ^ (k & 7)) << 4);
+}
+
+template <int CW>
+__device__ __forceinline__ void store_b_row(uint8_t *B, int k, int n0, int sbo, const float *v) {
+#pragma unroll
+    for (int g = 0; g < CW / 8; ++g)
+        *reinterpret_cast<uint4 *>(B + b_chunk(k, n0 + 8 * g, sbo)) = pack_bf16x8(v + 8 * g);
+}
+
+template <int CW>
+__global__ void __launch_bounds__(kThreads, 1)
+k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
+         const double *zj, float *u, float *dudz, const __grid_constant__ GnArgs gn, int gn_on,
+         int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    __shared__ int s_abort;
+    uint8_t *base = aligned_smem(smem_dyn);
+
+    const FieldDev &F = fd.f[NSF_FIELD_G];
+    const int W = F.width, D = F.depth, r = fd.r;
+    const int L = jac_slots(r);
+    const int lgL = __ffs(L) - 1;
+    constexpr int N = kWG * CW;              // columns (point slots) per tile
+    const int P = N / L;                     // points per tile
+    const int MH = jac_halves(W);            // 128-neuron accumulators
+    const int tiles = (n + P - 1) / P;
+    const int tid = threadIdx.x;
+    const int wg = tid >> 7;
+    const int wq = (tid >> 5) & 3;           // TMEM lane quarter of this warp
+    const int lane = tid & 31;
+    const int n0 = wg * CW;                  // first column of this warpgroup
+    const int sbo_b = (N / 64) * 1024;
+    const JacLayout Lo = jac_layout(r, W, D);
+    uint8_t *blob = base + Lo.blob;
+    uint8_t *B = base + Lo.b;
+    float4 *W0v = reinterpret_cast<float4 *>(base + Lo.w0v);
+    float *W0t = reinterpret_cast<float *>(base + Lo.w0t);
+    float *b0s = reinterpret_cast<float *>(base + Lo.b0);
+    float *bias = reinterpret_cast<float *>(base + Lo.bias);
+    float4 *xs = reinterpret_cast<float4 *>(base + Lo.xs);
+    float4 *tg = reinterpret_cast<float4 *>(base + Lo.tg);
+    float *O3 = reinterpret_cast<float *>(base + Lo.o3);
+    uint64_t *bar_w = reinterpret_cast<uint64_t *>(base + Lo.bars);
+    uint64_t *bar_mma = bar_w + 1;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + Lo.tmem);
+    uint32_t ncols = 32;
+    while ((int)ncols < MH * N) ncols <<= 1;
+    const int n_iter = gn_on ? gn.iters : 1;
+
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(bar_w, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) tmem_alloc(tmem_holder, ncols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (tid == 0) bulk_load(blob, F.tc_blob, (uint32_t)F.tc_blob_bytes, bar_w);
+    const int in0 = 3 + r;
+    for (int j = tid; j < W; j += kThreads) {
+        const float *w = F.W0 + (size_t)j * in0;
+        W0v[j] = make_float4(w[0], w[1], w[2], 0.f);
+        b0s[j] = F.b[0][j];
+        for (int k = 0; k < r; ++k) W0t[k * W + j] = w[3 + k];
+    }
+    for (int l = 1; l <= D; ++l) {
+        const int o = l == D ? F.out_dim : W;
+        for (int j = tid; j < o; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
+    }
+    // positions (and Gauss-Newton targets) of this CTA's first tile; a
+    // Gauss-Newton run revisits the same tile in every iteration
+    auto load_tile = [&](int t0) {
+        if (tid < P) {
+            const int p = t0 + tid;
+            const bool in = p < n;
+            xs[tid] = in ? make_float4(X[p], X[ld + p], X[2 * ld + p], 0.f)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gn_on) {
+                const int tl = gn.target_ld;
+                tg[tid] = in ? make_float4(gn.target[p], gn.target[tl + p], gn.target[2 * tl + p], 0.f)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    load_tile(blockIdx.x * P);
+    if (gn_on) gn_ff_begin(gn, r);
+    bool weights_ready = false;
+    const uint32_t blob_addr = smem_u32(blob);
+    const uint32_t b_addr = smem_u32(B);
+    const uint32_t idesc_h = idesc_bf16(kM, N, true);
+    const uint32_t tq = tmem + ((uint32_t)(wq * 32) << 16);
+    uint32_t phase = 0;
+
+    for (int it = 0; it < n_iter; ++it) {
+        __syncthreads();
+        // z-part of the input layer folded into its bias: c0 = b0 + W0[:, 3:] z
+        for (int j = tid; j < W; j += kThreads) {
+            float a = b0s[j];
+            for (int k = 0; k < r; ++k) {
+                const float zk = gn_on ? g_gn.z[k].hi : (float)__ldcg(&zj[k]);
+                a = fmaf(W0t[k * W + j], zk, a);
+            }
+            W0v[j].w = a;
+        }
+        __syncthreads();
+
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+            const int p0 = tile * P;
+            if (tile != (int)blockIdx.x) {
+                __syncthreads();
+                load_tile(p0);
+                __syncthreads();
+            }
+            // ---- layer 0 on the CUDA cores: this thread's neurons, its columns
+            for (int h = 0; h < MH; ++h) {
+                const int j = h * 128 + wq * 32 + lane;
+                if (j < W) {
+                    const float4 w = W0v[j];
+                    float v[CW];
+                    float g = 0.f;
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) {
+                        const int s = c & (L - 1);
+                        if (s == 0) {
+                            const float4 x = xs[(n0 + c) >> lgL];
+                            v[c] = elu_fast(fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w))), g);
+                        } else {
+                            v[c] = s <= r ? g * W0t[(s - 1) * W + j] : 0.f;
+                        }
+                    }
+                    store_b_row<CW>(B, j, n0, sbo_b, v);
+                }
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (!weights_ready) {
+                if (!__syncthreads_and(mbar_wait(bar_w, 0))) {
+                    if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+                    mbar_wait(bar_w, 0);      // bounded: let the copy land before leaving
+                    goto teardown;
+                }
+                weights_ready = true;
+            }
+
+            // ---- hidden layers, then the output layer (l == D)
+            for (int l = 1; l <= D; ++l) {
+                const bool out_layer = l == D;
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t aoff = (uint32_t)((l - 1) * W * W * 2);
+                    const int arows = out_layer ? kMaxOut : W;
+                    const int halves = out_layer ? 1 : MH;
+                    for (int h = 0; h < halves; ++h) {
+                        for (int ks = 0; ks < W / 16; ++ks) {
+                            const uint32_t koff = (uint32_t)((ks & 3) * 32);
+                            const uint32_t atom = (uint32_t)(ks >> 2);
+                            const uint64_t ad = sw128_desc(blob_addr + aoff + atom * (arows * 128) +
+                                                           (uint32_t)h * 16384u + koff);
+                            const uint64_t bd = sw128_desc(b_addr + (uint32_t)(2 * ks * sbo_b),
+                                                           1024u, (uint32_t)sbo_b);
+                            mma_bf16(tmem + (uint32_t)(h * N), ad, bd, idesc_h, ks > 0 ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(bar_mma);
+                    // the issuing thread alone waits; the rest sleep at the barrier
+                    if (!mbar_wait(bar_mma, phase)) s_abort = 1;
+                    tc_fence_before();
+                }
+                phase ^= 1u;
+                __syncthreads();
+                tc_fence_after();
+                if (s_abort) goto mma_timeout;
+                if (!out_layer) {
+                    const float *bl = bias + (l - 1) * W;
+                    for (int h = 0; h < MH; ++h) {
+                        const int j = h * 128 + wq * 32 + lane;
+                        if (j < W) {                 // uniform per warp: W % 64 == 0
+                            float v[CW];
+#pragma unroll
+                            for (int g8 = 0; g8 < CW / 8; ++g8)
+                                tmem_ld8(tq + (uint32_t)(h * N + n0 + 8 * g8), v + 8 * g8);
+                            tmem_wait_ld();
+                            const float b = bl[j];
+                            float g = 0.f;
+#pragma unroll
+                            for (int c = 0; c < CW; ++c) {
+                                const int s = c & (L - 1);
+                                if (s == 0) v[c] = elu_fast(v[c] + b, g);
+                                else v[c] = s <= r ? g * v[c] : 0.f;
+                            }
+                            store_b_row<CW>(B, j, n0, sbo_b, v);
+                        }
+                    }
+                    tc_fence_before();
+                    fence_proxy_async();
+                    __syncthreads();
+                } else {
+                    bool bad = false;
+                    if (wq == 0) {
+                        float v[CW];
+#pragma unroll
+                        for (int g8 = 0; g8 < CW / 8; ++g8) tmem_ld8(tq + (uint32_t)(n0 + 8 * g8), v + 8 * g8);
+                        tmem_wait_ld();
+                        if (lane < 3) {
+                            const int a = lane;
+                            const float sc = F.scale[a], sh = F.shift[a];
+                            const float bo = bias[(D - 1) * W + a];
+#pragma unroll
+                            for (int c = 0; c < CW; ++c) {
+                                const int col = n0 + c;
+                                const int s = col & (L - 1);
+                                const int p = p0 + (col >> lgL);
+                                const bool valid = p < n && s <= r;
+                                float y = s == 0 ? fmaf(sc, v[c] + bo, sh) : sc * v[c];
+                                if (valid) bad |= !isfinite(y);
+                                if (valid && s == 0) {
+                                    if (u) u[(size_t)a * ld + p] = y;
+                                    if (gn_on) {
+                                        const float4 t = tg[col >> lgL];
+                                        y -= a == 0 ? t.x : (a == 1 ? t.y : t.z);
+                                    }
+                                }
+                                if (valid && s > 0 && dudz) dudz[(size_t)(a * r + s - 1) * ld + p] = y;
+                                O3[col * 3 + a] = valid ? y : 0.f;
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    if (bad) set_status(status, NSF_ERR_NONFINITE);
+                    __syncthreads();
+                    if (gn_on) {
+                        // this tile's share of the normal equations
+                        gn_ff_tile_partials(O3, L, max(0, min(P, n - p0)), r);
+                        __syncthreads();
+                    }
+                }
+            }
+        }
+
+        if (gn_on) {
+            // Gauss-Newton iteration `it`: all CTAs' partials summed behind a
+            // grid barrier (cooperative launch), then every CTA solves
+            __syncthreads();
+            if (!gn_ff_finish_iteration(gn, r, it, status)) goto teardown;
+        }
+    }
+    goto teardown;
+
+mma_timeout:
+    if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+    // bounded: let the outstanding MMA finish before the memory is released
+    mbar_wait(bar_mma, phase ^ 1u);
+
+teardown:
+    // a CTA must not leave while its weight copy may still be landing
+    if (!weights_ready) mbar_wait(bar_w, 0);
+    __syncthreads();
+    if (tid < 32) {
+        tc_fence_after();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+}  // namespace
+
+size_t jac_tc_smem_bytes(int r, int width, int depth) {
+    const JacLayout L = jac_layout(r, width, depth);
+    if (jac_halves(width) * jac_cols(r) > 512) return 0;        // tensor memory columns
+    if ((size_t)L.total + sizeof(GnFF) + 64 > (size_t)kMaxSmem) return 0;
+    return (size_t)L.total;
+}
+
+// Points per tile of the Jacobian kernel: every tile holds as many points as
+// its columns allow; the latency of a layer does not depend on how many
+// columns are live, so fuller tiles only mean fewer CTAs to combine in each
+// Gauss-Newton iteration.
+int jac_points_per_tile(const FieldsDev &fd, int n) {
+    (void)n;
+    return jac_points(fd.r);
+}
+
+int jac_grid_size_tc(const FieldsDev &fd, int n) {
+    const int P = jac_points_per_tile(fd, n);
+    const int tiles = (n + P - 1) / P;
+    const int cap = sm_count() < kGnMaxCtas ? sm_count() : kGnMaxCtas;
+    return tiles < cap ? tiles : cap;
+}
+
+cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int ld,
+                               const double *z, float *u, float *dudz, const GnArgs *gn,
+                               int *status, cudaStream_t s) {
+    const FieldDev &F = fd.f[NSF_FIELD_G];
+    const size_t sm = jac_tc_smem_bytes(fd.r, F.width, F.depth);
+    if (sm == 0) return cudaErrorInvalidValue;
+    GnArgs g{};
+    if (gn) g = *gn;
+    const int gn_on = gn ? 1 : 0;
+    const int grid = jac_grid_size_tc(fd, n);
+    // A Gauss-Newton run waits between iterations on a grid barrier, so all
+    // CTAs must be co-resident: cooperative launch (one CTA per SM).
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = gn_on ? 1 : 0;
+    if (jac_cw(fd.r) == 8) {
+        static bool done = false;
+        set_max_dynamic_smem(k_jac_tc<8>, done);
+        return cudaLaunchKernelEx(&cfg, k_jac_tc<8>, fd, X, n, ld, z, u, dudz, g, gn_on, status);
+    }
+    if (jac_cw(fd.r) == 16) {
+        static bool done = false;
+        set_max_dynamic_smem(k_jac_tc<16>, done);
+        return cudaLaunchKernelEx(&cfg, k_jac_tc<16>, fd, X, n, ld, z, u, dudz, g, gn_on, status);
+    }
+    static bool done = false;
+    set_max_dynamic_smem(k_jac_tc<32>, done);
+    return cudaLaunchKernelEx(&cfg, k_jac_tc<32>, fd, X, n, ld, z, u, dudz, g, gn_on, status);
+}
+
+}  // namespace nsf

@@ -1,0 +1,225 @@
+// Shared pieces of the tcgen05 tensor-core kernels (BF16 field evaluation in
+// fields_tc.cu, Jacobian and Gauss-Newton in jacobian_tc.cu): PTX wrappers for
+// mbarriers, bulk copies, tensor memory and tcgen05.mma, the shared-memory
+// operand descriptors, and the BF16-path activation.
+//
+// Operand layouts use the 128-byte swizzle.
+//   K-major (rows of K contiguous): a K-atom is 64 bf16 columns; row n's 128
+//   bytes sit at (n / 8) * 1024 + (n % 8) * 128 in the atom and its 16-byte
+//   chunk c at chunk position c ^ (n % 8); 8-row groups are 1024 bytes apart.
+//   MN-major (rows of MN contiguous, one row per k): an atom is 8 k-rows of
+//   64 bf16 MN-elements (1024 bytes), chunk c of k-row kr at position
+//   c ^ kr; atoms are tiled along MN (leading byte offset) and along K in
+//   8-row steps (stride byte offset).
+// Every atom starts on a 1024-byte boundary.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "device_common.cuh"
+
+namespace nsf {
+namespace tc {
+
+constexpr int kM = 128;                   // tile rows (TMEM lanes)
+constexpr int kWG = 8;                    // warpgroups per CTA
+constexpr int kWgThreads = 128;
+constexpr int kThreads = kWG * kWgThreads;
+constexpr int kGroup = 8;                 // bf16 values per 16-byte chunk
+constexpr int kMaxSmem = 227 * 1024;
+constexpr int kMaxOut = 16;               // output rows of the last layer (out_dim padded)
+
+__host__ __device__ inline int align_to(int v, int a) { return (v + a - 1) / a * a; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 1024-byte aligned base inside the dynamic shared array, by pointer
+// arithmetic on the shared array itself (an integer round trip would hide the
+// address space and turn every shared access into a generic one).
+__device__ __forceinline__ uint8_t *aligned_smem(uint8_t *dyn) {
+    return dyn + ((1024u - (smem_u32(dyn) & 1023u)) & 1023u);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the given phase parity; false if it did not complete in time.
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t phase) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, phase))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One bulk copy of `bytes` (a multiple of 16) in 32 KB pieces, all completing
+// on `bar` (which expects the whole transaction count).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    mbar_expect_tx(bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += 32768u) {
+        const uint32_t len = bytes - off < 32768u ? bytes - off : 32768u;
+        bulk_g2s(static_cast<uint8_t *>(dst) + off, static_cast<const uint8_t *>(src) + off, len,
+                 bar);
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(holder)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor with the 128-byte swizzle.  K-major: the
+// stride byte offset is the 1024-byte step between 8-row groups and the
+// leading byte offset is not used (16).  MN-major: lbo = step between
+// 64-element MN blocks, sbo = step between 8-row K blocks.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo = 16,
+                                               uint32_t sbo = 1024) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;          // descriptor version of the tcgen05 family
+    d |= (uint64_t)2 << 61;          // swizzle mode: 128 bytes
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D; A K-major, B
+// K-major or (b_mn) MN-major.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N, bool b_mn = false) {
+    return (1u << 4)                 // D format F32
+           | (1u << 7)               // A format BF16
+           | (1u << 10)              // B format BF16
+           | ((b_mn ? 1u : 0u) << 16)
+           | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 8 consecutive 32-bit columns of this warp's 32 TMEM lanes (one per thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint4 pack_bf16x8(const float *h) {
+    return make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                      pack_bf16x2(h[6], h[7]));
+}
+
+// ELU on the BF16 path: one exponential per element (the result is rounded to
+// bf16 right after, so exp(a) - 1 is as good as expm1 here); grad = ELU'(a).
+__device__ __forceinline__ float elu_fast(float a, float &grad) {
+    const float e = __expf(fminf(a, 0.f));
+    grad = a > 0.f ? 1.f : e;
+    return a > 0.f ? a : e - 1.f;
+}
+
+// Byte offset of element (n, k) of a K-major, 128-byte-swizzled operand whose
+// K-atoms hold rows_pad rows.
+__host__ __device__ inline size_t sw128_kmajor_offset(int n, int k, int rows_pad) {
+    const int atom = k / 64, kk = k % 64, chunk = kk / 8;
+    return (size_t)atom * rows_pad * 128 + (size_t)(n / 8) * 1024 + (n % 8) * 128 +
+           ((chunk ^ (n % 8)) * 16) + (kk % 8) * 2;
+}
+
+inline int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// Dynamic shared memory limit of a kernel: the opt-in maximum minus its
+// static shared memory; set once per kernel, before any stream capture.
+template <class K>
+inline void set_max_dynamic_smem(K kernel, bool &done) {
+    if (done) return;
+    cudaFuncAttributes fa;
+    int stat = 0;
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - stat);
+    done = true;
+}
+
+}  // namespace tc
+}  // namespace nsf
