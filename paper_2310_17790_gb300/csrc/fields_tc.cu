@@ -3,21 +3,27 @@
 // particles; App. E, fields are ELU MLPs on [X; z]).  The Jacobian and the
 // Gauss-Newton iterations run in jacobian_tc.cu.
 //
-// One CTA = eight warpgroups (1024 threads) on a 128-point tile; point i is
-// tile row i and TMEM lane i, which only the warps with (warp index % 4) ==
-// i / 32 can read.  Warpgroup w owns the column eighth [w W / 8, (w + 1) W / 8)
-// of every layer.  Per tile:
+// A CTA holds one field's weights resident in shared memory (one bulk copy on
+// an mbarrier with a transaction count) and runs up to two tile groups of 256
+// threads (two warpgroups) side by side.  Each group owns a 128-point tile at
+// a time, its own activation operand in shared memory and its own FP32
+// accumulator in tensor memory; point i of the tile is tile row i and TMEM
+// lane i, which only the warps with (warp index % 4) == i / 32 can read, and
+// warpgroup h of the group owns the column half [h W / 2, (h + 1) W / 2).
+// Per tile:
 //   layer 0 (K = 3 + r)  on the CUDA cores in FP32, written as bf16 into the
-//                        shared-memory A operand;
+//                        group's shared-memory A operand;
 //   hidden layers        tcgen05.mma M = 128, N = width, K = width (16 per
-//                        instruction), FP32 accumulator in tensor memory; the
-//                        epilogue reads it with tcgen05.ld, adds the FP32 bias,
-//                        applies ELU, rounds to bf16 and rewrites A in place;
+//                        instruction) issued by the group's first thread; the
+//                        epilogue reads the accumulator with tcgen05.ld, adds
+//                        the FP32 bias, applies ELU (packed f32x2 arithmetic,
+//                        one special-function exp per element), rounds to
+//                        bf16 and rewrites A in place;
 //   output layer         the same MMA with N = 16 (out_dim padded with zero
 //                        rows), bias added when the outputs are read.
-// All weights of the CTA's field stay resident in shared memory (one bulk copy
-// per CTA on an mbarrier with a transaction count); persistent CTAs loop over
-// tiles.  Every wait on an mbarrier is bounded by time: on expiry the kernel
+// The groups synchronise on their own named barriers, so while one group runs
+// an epilogue on the CUDA cores the tensor core works on the other group's
+// layer.  Every wait on an mbarrier is bounded by time: on expiry the kernel
 // records NSF_ERR_ITER_CAP, waits (bounded) for its outstanding operations,
 // frees its tensor memory and returns.
 //
@@ -45,33 +51,33 @@ size_t jac_tc_smem_bytes(int r, int width, int depth);   // jacobian_tc.cu
 
 namespace {
 
+constexpr int kMaxGroups = 2;
+// Warpgroups per tile group: each owns W / kWgPerGroup columns of every layer.
+#ifndef NSF_VALUE_WG_PER_GROUP
+#define NSF_VALUE_WG_PER_GROUP 2
+#endif
+constexpr int kWgPerGroup = NSF_VALUE_WG_PER_GROUP;
+constexpr int kGroupThreads = kWgPerGroup * kWgThreads;
+
+// Tensor-memory columns of one group: the FP32 accumulator (W columns) and,
+// after it at column W, the bf16 activation operand (W / 2 columns).
+__host__ __device__ inline int tmem_region(int W) { return W <= 64 ? 128 : (W <= 128 ? 256 : 512); }
+
 // Shared-memory carve of one CTA (byte offsets from a 1024-aligned base).
 struct TcLayout {
-    int a, blob, w0v, bias, bars, tmem, total;
+    int blob, w0v, bias, bars, tmem, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int W, int D) {
     TcLayout L;
     int o = 0;
-    L.a = o;    o = align_to(o + kM * W * 2, 1024);
     L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + kMaxOut * W * 2, 1024);
-    L.w0v = o;  o = align_to(o + W * 16, 16);                 // float4 {w_x, w_y, w_z, c0}
+    L.w0v = o;  o = align_to(o + W * 16, 16);                 // input layer, column pairs
     L.bias = o; o = align_to(o + D * W * 4, 16);              // hidden biases, then output bias
-    L.bars = o; o = align_to(o + 2 * 8, 16);
+    L.bars = o; o = align_to(o + (2 + kMaxGroups) * 8, 16);   // weights, go, MMA per group
     L.tmem = o; o = align_to(o + 16, 16);
     L.total = o + 1024;   // room to align the dynamic base to 1024 bytes
     return L;
-}
-
-// Byte offset of the 16-byte chunk holding columns c .. c + 7 (c % 8 == 0) of
-// row m in the 128-row A tile.
-__device__ __forceinline__ int a_chunk(int m, int c) {
-    return (c >> 6) * (kM * 128) + (m >> 3) * 1024 + (m & 7) * 128 +
-           ((((c >> 3) & 7) ^ (m & 7)) << 4);
-}
-
-__device__ __forceinline__ void store_a8(uint8_t *A, int m, int c, const float *h) {
-    *reinterpret_cast<uint4 *>(A + a_chunk(m, c)) = pack_bf16x8(h);
 }
 
 struct TcJobs {
@@ -79,38 +85,76 @@ struct TcJobs {
     FieldJob job[4];
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
+// C FP32 values (C = 16 or 32) -> C / 2 packed bf16 pairs (round to nearest
+// even), stored to C / 2 consecutive tensor-memory columns.
+template <int C>
+__device__ __forceinline__ void store_act(uint32_t taddr, const float *v) {
+    uint32_t q[C / 2];
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) q[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+    if constexpr (C == 32) tmem_st16(taddr, q);
+    else tmem_st8(taddr, q);
+}
+
+// C accumulator columns of this warp's lanes (C = 16 or 32).
+template <int C>
+__device__ __forceinline__ void load_acc(uint32_t taddr, float *v) {
+    tmem_ld16(taddr, v);
+    if constexpr (C == 32) tmem_ld16(taddr + 16, v + 16);
+}
+
+// ELU(v + bias) in place over C values.
+template <int C>
+__device__ __forceinline__ void bias_elu(float *v, const float *bl) {
+#pragma unroll
+    for (int i = 0; i < C; i += 4) {
+        const float4 b = *reinterpret_cast<const float4 *>(bl + i);
+        const float2 h0 = elu2(make_float2(v[i], v[i + 1]), make_float2(b.x, b.y));
+        const float2 h1 = elu2(make_float2(v[i + 2], v[i + 3]), make_float2(b.z, b.w));
+        v[i] = h0.x;
+        v[i + 1] = h0.y;
+        v[i + 2] = h1.x;
+        v[i + 3] = h1.y;
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMaxGroups * kGroupThreads, 1)
 k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
-            const __grid_constant__ TcJobs jobs, int *status) {
+            const __grid_constant__ TcJobs jobs, int ng, int *status) {
     extern __shared__ uint8_t smem_dyn[];
-    __shared__ int s_abort;
+    __shared__ int s_ok[kMaxGroups];
     uint8_t *base = aligned_smem(smem_dyn);
 
     const FieldJob &job = jobs.job[blockIdx.y];
     const FieldDev &F = fd.f[job.field];
-    const int W = F.width, D = F.depth, r = fd.r;
+    const int D = F.depth, r = fd.r;
     const int tiles = (n + kM - 1) / kM;
     const int tid = threadIdx.x;
-    const int wg = tid >> 7;                 // warpgroup: column eighth
-    const int row = tid & (kM - 1);          // tile row == TMEM lane
+    const int grp = tid / kGroupThreads;     // tile group
+    const int gt = tid % kGroupThreads;      // thread within the group
+    const int row = gt & (kM - 1);           // tile row == TMEM lane
     const int wq = row >> 5;                 // lane quarter of this warp
-    const int cw = W / kWG;                  // columns per warpgroup (multiple of 8)
-    const int cbeg = wg * cw;
+    constexpr int cw = W / kWgPerGroup;      // columns per warpgroup (multiple of 16)
+    constexpr int kC = cw < 32 ? cw : 32;    // columns per chunk of the epilogue
+    const int cbeg = (gt >> 7) * cw;
+    const int bar_id = 1 + grp;              // the group's named barrier
     const TcLayout L = tc_layout(W, D);
-    uint8_t *A = base + L.a;
     uint8_t *blob = base + L.blob;
-    float4 *W0v = reinterpret_cast<float4 *>(base + L.w0v); // [W] {W0[j][0..2], c0[j]}
+    // input layer by column pairs (j, j + 1): {w_x j, w_x j+1, w_y j, w_y j+1},
+    // {w_z j, w_z j+1, c0 j, c0 j+1}, so a pair's values load as register pairs
+    float4 *W0v = reinterpret_cast<float4 *>(base + L.w0v);
     float *bias = reinterpret_cast<float *>(base + L.bias);  // [D][W]
     uint64_t *bar_w = reinterpret_cast<uint64_t *>(base + L.bars);
-    uint64_t *bar_mma = bar_w + 1;
+    uint64_t *bar_go = bar_w + 1;            // group 0 has issued its first MMA
+    uint64_t *bar_mma = bar_w + 2 + grp;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + L.tmem);
-    uint32_t ncols = 32;
-    while ((int)ncols < W) ncols <<= 1;
+    const uint32_t ncols = (uint32_t)(ng * tmem_region(W));
 
     if (tid == 0) {
-        s_abort = 0;
         mbar_init(bar_w, 1);
-        mbar_init(bar_mma, 1);
+        mbar_init(bar_go, 1);
+        for (int g = 0; g < ng; ++g) mbar_init(bar_w + 2 + g, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < 32) tmem_alloc(tmem_holder, ncols);
@@ -118,120 +162,152 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
+    const uint32_t acc = tmem + (uint32_t)(grp * tmem_region(W));   // FP32 accumulator
+    const uint32_t act = acc + (uint32_t)W;                          // bf16 activations
 
     // weights: one bulk copy, landing while the CTA prepares the input layer
     if (tid == 0) bulk_load(blob, F.tc_blob, (uint32_t)F.tc_blob_bytes, bar_w);
     const int in0 = 3 + r;
-    for (int j = tid; j < W; j += kThreads) {
+    for (int j = tid; j < W; j += blockDim.x) {
         // z-part of the input layer folded into its bias: c0 = b0 + W0[:, 3:] z
         const float *w = F.W0 + (size_t)j * in0;
         float c0 = F.b[0][j];
         for (int k = 0; k < r; ++k) c0 = fmaf(w[3 + k], (float)__ldcg(&job.z[k]), c0);
-        W0v[j] = make_float4(w[0], w[1], w[2], c0);
+        float *pr = reinterpret_cast<float *>(W0v + 2 * (j >> 1)) + (j & 1);
+        pr[0] = w[0];
+        pr[2] = w[1];
+        pr[4] = w[2];
+        pr[6] = c0;
     }
     for (int l = 1; l <= D; ++l) {
         const int o = l == D ? F.out_dim : W;
-        for (int j = tid; j < o; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
+        for (int j = tid; j < o; j += blockDim.x) bias[(l - 1) * W + j] = F.b[l][j];
     }
-    bool weights_ready = false;
-    const uint32_t a_addr = smem_u32(A);
-    const uint32_t b_addr = smem_u32(blob);
-    const uint32_t idesc_h = idesc_bf16(kM, W);
-    const uint32_t idesc_o = idesc_bf16(kM, kMaxOut);
-    const uint32_t tlane = tmem + ((uint32_t)(wq * 32) << 16);
-    uint32_t phase = 0;
     __syncthreads();
+    if (!__syncthreads_and(mbar_wait(bar_w, 0))) {
+        if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+        mbar_wait(bar_w, 0);      // bounded: let the copy land before leaving
+        goto teardown;
+    }
 
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int p = tile * kM + row;
-        const bool valid = p < n;
-        // ---- layer 0 on the CUDA cores
-        float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-        if (valid) {
-            x0 = X[p];
-            x1 = X[ld + p];
-            x2 = X[2 * ld + p];
-        }
-        for (int cc = cbeg; cc < cbeg + cw; cc += kGroup) {
-            float v[kGroup];
-#pragma unroll
-            for (int i = 0; i < kGroup; ++i) {
-                const float4 w = W0v[cc + i];
-                float g;
-                v[i] = elu_fast(fmaf(w.x, x0, fmaf(w.y, x1, fmaf(w.z, x2, w.w))), g);
-            }
-            store_a8(A, row, cc, v);
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (!weights_ready) {
-            if (!__syncthreads_and(mbar_wait(bar_w, 0))) {
-                if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
-                mbar_wait(bar_w, 0);      // bounded: let the copy land before leaving
-                goto teardown;
-            }
-            weights_ready = true;
-        }
+    {
+        const uint32_t b_addr = smem_u32(blob);
+        const uint32_t idesc_h = idesc_bf16(kM, W);
+        const uint32_t idesc_o = idesc_bf16(kM, kMaxOut);
+        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+        const uint32_t acc_l = acc + lane_off;                 // this warp's accumulator lanes
+        const uint32_t act_l = act + lane_off + (uint32_t)(cbeg / 2);   // its activation columns
+        uint32_t phase = 0;
+        bool go_sent = false;
 
-        // ---- hidden layers, then the output layer (l == D)
-        for (int l = 1; l <= D; ++l) {
-            const bool out_layer = l == D;
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t boff = (uint32_t)((l - 1) * W * W * 2);
-                const int nrows = out_layer ? kMaxOut : W;
-                const uint32_t idesc = out_layer ? idesc_o : idesc_h;
-                for (int ks = 0; ks < W / 16; ++ks) {
-                    const uint32_t koff = (uint32_t)((ks & 3) * 32);
-                    const uint32_t atom = (uint32_t)(ks >> 2);
-                    mma_bf16(tmem, sw128_desc(a_addr + atom * (kM * 128) + koff),
-                             sw128_desc(b_addr + boff + atom * (nrows * 128) + koff), idesc,
-                             ks > 0 ? 1u : 0u);
+        for (int j = grp;; j += ng) {
+            const int tile = blockIdx.x + j * gridDim.x;
+            if (tile >= tiles) break;
+            if (grp == 1 && j == 1) {
+                // Group 1 starts once group 0 has handed its first layer to the
+                // tensor core, so that from then on each group's epilogue runs
+                // while the tensor core works on the other group's product
+                // (started together, both would run their epilogues at the
+                // same time and leave the tensor core idle meanwhile).
+                if (gt == 0) s_ok[1] = mbar_wait(bar_go, 0) ? 1 : 0;
+                named_sync(bar_id, kGroupThreads);
+                if (!s_ok[1]) {
+                    if (gt == 0) set_status(status, NSF_ERR_ITER_CAP);
+                    break;
                 }
-                mma_commit(bar_mma);
-                // the issuing thread alone waits (polling by every thread would
-                // take issue slots from the others); the rest sleep at the barrier
-                if (!mbar_wait(bar_mma, phase)) s_abort = 1;
-                tc_fence_before();
             }
-            phase ^= 1u;
-            __syncthreads();
-            tc_fence_after();
-            if (s_abort) goto mma_timeout;
-            if (!out_layer) {
-                const float *bl = bias + (l - 1) * W;
-                for (int cc = cbeg; cc < cbeg + cw; cc += 2 * kGroup) {
-                    const bool two = cc + kGroup < cbeg + cw;
-                    float v[kGroup], w[kGroup];
-                    tmem_ld8(tlane + cc, v);
-                    if (two) tmem_ld8(tlane + cc + kGroup, w);
+            const int p = tile * kM + row;
+            const bool valid = p < n;
+            // ---- layer 0 on the CUDA cores, into the activation operand
+            float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+            if (valid) {
+                x0 = X[p];
+                x1 = X[ld + p];
+                x2 = X[2 * ld + p];
+            }
+            const float2 xx0 = make_float2(x0, x0), xx1 = make_float2(x1, x1),
+                         xx2 = make_float2(x2, x2);
+#pragma unroll
+            for (int c0 = 0; c0 < cw; c0 += kC) {
+                const int cc = cbeg + c0;
+                float v[kC];
+#pragma unroll
+                for (int i = 0; i < kC; i += 2) {
+                    const float4 wa = W0v[cc + i], wb = W0v[cc + i + 1];
+                    const float2 pre = __ffma2_rn(
+                        make_float2(wa.x, wa.y), xx0,
+                        __ffma2_rn(make_float2(wa.z, wa.w), xx1,
+                                   __ffma2_rn(make_float2(wb.x, wb.y), xx2,
+                                              make_float2(wb.z, wb.w))));
+                    const float2 h = elu2(pre, make_float2(0.f, 0.f));
+                    v[i] = h.x;
+                    v[i + 1] = h.y;
+                }
+                store_act<kC>(act_l + (uint32_t)(c0 / 2), v);
+            }
+
+            // ---- hidden layers, then the output layer (l == D)
+            for (int l = 1; l <= D; ++l) {
+                const bool out_layer = l == D;
+                tmem_wait_st();               // this thread's activation stores landed
+                tc_fence_before();            // and its accumulator reads are done
+                named_sync(bar_id, kGroupThreads);
+                if (gt == 0) {
+                    tc_fence_after();
+                    const uint32_t boff = (uint32_t)((l - 1) * W * W * 2);
+                    const int nrows = out_layer ? kMaxOut : W;
+                    const uint32_t idesc = out_layer ? idesc_o : idesc_h;
+#pragma unroll
+                    for (int ks = 0; ks < W / 16; ++ks) {
+                        const uint32_t koff = (uint32_t)((ks & 3) * 32);
+                        const uint32_t atom = (uint32_t)(ks >> 2);
+                        mma_bf16_ts(acc, act + (uint32_t)(8 * ks),
+                                    sw128_desc(b_addr + boff + atom * (nrows * 128) + koff),
+                                    idesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(bar_mma);
+                    if (grp == 0 && !go_sent) {
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                         smem_u32(bar_go))
+                                     : "memory");
+                        go_sent = true;
+                    }
+                    // the issuing thread alone waits; the rest of the group
+                    // sleeps at the barrier while the other group computes
+                    s_ok[grp] = mbar_wait(bar_mma, phase) ? 1 : 0;
+                    tc_fence_before();
+                }
+                phase ^= 1u;
+                named_sync(bar_id, kGroupThreads);
+                tc_fence_after();
+                if (!s_ok[grp]) goto mma_timeout;
+                if (!out_layer) {
+                    // chunk k + 1's accumulator load is in flight while chunk
+                    // k is computed and stored
+                    const float *bl = bias + (l - 1) * W + cbeg;
+                    float v[kC], w[kC];
+                    load_acc<kC>(acc_l + (uint32_t)cbeg, v);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < kGroup; ++i) {
-                        float g;
-                        v[i] = elu_fast(v[i] + bl[cc + i], g);
+                    for (int c0 = 0; c0 < cw; c0 += 2 * kC) {
+                        const bool more = c0 + kC < cw;
+                        if (more) load_acc<kC>(acc_l + (uint32_t)(cbeg + c0 + kC), w);
+                        bias_elu<kC>(v, bl + c0);
+                        store_act<kC>(act_l + (uint32_t)(c0 / 2), v);
+                        if (!more) break;
+                        tmem_wait_ld();
+                        if (c0 + 2 * kC < cw) load_acc<kC>(acc_l + (uint32_t)(cbeg + c0 + 2 * kC), v);
+                        bias_elu<kC>(w, bl + c0 + kC);
+                        store_act<kC>(act_l + (uint32_t)((c0 + kC) / 2), w);
+                        if (c0 + 2 * kC < cw) tmem_wait_ld();
                     }
-                    store_a8(A, row, cc, v);
-                    if (two) {
-#pragma unroll
-                        for (int i = 0; i < kGroup; ++i) {
-                            float g;
-                            w[i] = elu_fast(w[i] + bl[cc + kGroup + i], g);
-                        }
-                        store_a8(A, row, cc + kGroup, w);
-                    }
-                }
-                tc_fence_before();
-                fence_proxy_async();
-                __syncthreads();
-            } else {
-                bool bad = false;
-                if (wg == 0) {
+                } else if (gt < kM) {
+                    // outputs: the first warpgroup reads the 16 output columns
                     float v[16];
-                    tmem_ld8(tlane, v);
-                    tmem_ld8(tlane + 8, v + 8);
+                    tmem_ld16(acc_l, v);
                     tmem_wait_ld();
                     const float *bo = bias + (D - 1) * W;
+                    bool bad = false;
                     if (valid) {
 #pragma unroll
                         for (int o = 0; o < 9; ++o) {
@@ -242,23 +318,23 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
                             }
                         }
                     }
+                    if (bad) set_status(status, NSF_ERR_NONFINITE);
                 }
-                tc_fence_before();
-                if (bad) set_status(status, NSF_ERR_NONFINITE);
-                __syncthreads();
             }
         }
-    }
-    goto teardown;
+        goto teardown;
 
-mma_timeout:
-    if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
-    // bounded: let the outstanding MMA finish before the memory is released
-    mbar_wait(bar_mma, phase ^ 1u);
+    mma_timeout:
+        if (gt == 0) {
+            set_status(status, NSF_ERR_ITER_CAP);
+            // bounded: let the outstanding MMA finish before the memory is released
+            mbar_wait(bar_mma, phase ^ 1u);
+        }
+    }
 
 teardown:
-    // a CTA must not leave while its weight copy may still be landing
-    if (!weights_ready) mbar_wait(bar_w, 0);
+    tmem_wait_st();
+    tc_fence_before();
     __syncthreads();
     if (tid < 32) {
         tc_fence_after();
@@ -266,10 +342,15 @@ teardown:
     }
 }
 
+// Tile groups a CTA runs for this field size (two where both groups' tensor
+// memory fits), 0 if the weights do not fit in shared memory.
+int value_groups(int width, int depth) {
+    if ((size_t)tc_layout(width, depth).total + 64 > (size_t)kMaxSmem) return 0;
+    return 2 * tmem_region(width) <= 512 ? 2 : 1;
+}
+
 size_t value_smem_bytes(int width, int depth) {
-    TcLayout L = tc_layout(width, depth);
-    if ((size_t)L.total + 64 > (size_t)kMaxSmem) return 0;
-    return (size_t)L.total;
+    return value_groups(width, depth) ? (size_t)tc_layout(width, depth).total : 0;
 }
 
 }  // namespace
@@ -284,27 +365,56 @@ size_t tc_smem_bytes(int r, int width, int depth) {
     return v > j ? v : j;
 }
 
-cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld, int njobs,
-                             const FieldJob *jobs, int *status, cudaStream_t s) {
-    TcJobs tj;
-    tj.njobs = njobs;
+namespace {
+
+template <int W>
+cudaError_t launch_fields_tc_w(const FieldsDev &fd, const float *X, int n, int ld,
+                               const TcJobs &tj, int *status, cudaStream_t s) {
+    int ng = kMaxGroups;
     size_t sm = 0;
-    for (int i = 0; i < njobs; ++i) {
-        tj.job[i] = jobs[i];
-        const FieldDev &F = fd.f[jobs[i].field];
-        const size_t b = value_smem_bytes(F.width, F.depth);
-        if (b == 0) return cudaErrorInvalidValue;
+    for (int i = 0; i < tj.njobs; ++i) {
+        const int g = value_groups(W, fd.f[tj.job[i].field].depth);
+        if (g == 0) return cudaErrorInvalidValue;
+        ng = g < ng ? g : ng;
+    }
+    for (int i = 0; i < tj.njobs; ++i) {
+        const size_t b = (size_t)tc_layout(W, fd.f[tj.job[i].field].depth).total;
         sm = b > sm ? b : sm;
     }
     static bool attr_done = false;
-    set_max_dynamic_smem(k_fields_tc, attr_done);
+    set_max_dynamic_smem(k_fields_tc<W>, attr_done);
     const int tiles = (n + kM - 1) / kM;
-    int per_job = sm_count() / njobs;
+    int per_job = sm_count() / tj.njobs;
     if (per_job < 1) per_job = 1;
     if (per_job > tiles) per_job = tiles;
-    dim3 grid(per_job, njobs);
-    k_fields_tc<<<grid, kThreads, sm, s>>>(fd, X, n, ld, tj, status);
+    dim3 grid(per_job, tj.njobs);
+    k_fields_tc<W><<<grid, ng * kGroupThreads, sm, s>>>(fd, X, n, ld, tj, ng, status);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// One launch per distinct field width among the jobs (the kernel is
+// specialised on the width so that its column loops unroll completely).
+cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld, int njobs,
+                             const FieldJob *jobs, int *status, cudaStream_t s) {
+    static const int widths[] = {64, 128, 192, 256};
+    for (int w : widths) {
+        TcJobs tj;
+        tj.njobs = 0;
+        for (int i = 0; i < njobs; ++i)
+            if (fd.f[jobs[i].field].width == w) tj.job[tj.njobs++] = jobs[i];
+        if (tj.njobs == 0) continue;
+        cudaError_t e = cudaSuccess;
+        switch (w) {
+            case 64: e = launch_fields_tc_w<64>(fd, X, n, ld, tj, status, s); break;
+            case 128: e = launch_fields_tc_w<128>(fd, X, n, ld, tj, status, s); break;
+            case 192: e = launch_fields_tc_w<192>(fd, X, n, ld, tj, status, s); break;
+            default: e = launch_fields_tc_w<256>(fd, X, n, ld, tj, status, s); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace nsf
