@@ -283,6 +283,71 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
                               double *d_z_iter, float *d_residual,
                               int *d_status, void *stream);
 
+/*
+ * Batched latent stepping: many independent reduced-order scenes advanced
+ * together, each step as a few launches for the whole batch (field inference
+ * per field width, one MPM launch, one Gauss-Newton launch) instead of three
+ * launches per scene.  Each scene is stepped exactly as nsf_latent_step steps it
+ * (paper §5.1-§5.3).  Scenes may differ in fields (r, width, depth), particle
+ * counts, grids and dt; their fields must be NSF_PREC_BF16 (the tensor-core
+ * path; others give NSF_ERR_UNSUPPORTED) and at most NSF_MAX_BATCH scenes.
+ *
+ * An item names a scene, its fields and its caller-owned latent codes:
+ * d_z [r] holds z_n on entry and z_{n+nsteps} on return, d_z_prev [r] z_{n-1}
+ * and z_{n+nsteps-1}, as in nsf_latent_step.
+ */
+#define NSF_MAX_BATCH 1024
+typedef struct nsf_latent_batch_item {
+    const nsf_fields *fields;
+    nsf_latent_scene scene;
+    double dt;
+    double *d_z;
+    double *d_z_prev;
+} nsf_latent_batch_item;
+
+typedef struct nsf_latent_batch nsf_latent_batch;   /* opaque plan */
+
+/* Workspace bytes a batch of these items needs (the items' pointers are not
+ * read; only sizes, fields and grids). */
+nsf_status nsf_latent_batch_workspace_size(int n_items, const nsf_latent_batch_item *items,
+                                           size_t *bytes);
+
+/*
+ * Plans a batch: validates the items, lays the per-scene buffers out in the
+ * caller's workspace (zero-filled before the first step, kept by the library in
+ * that reusable state), splits the field evaluations into work lists of
+ * 128-point tiles balanced over the SMs, and assigns each scene's Gauss-Newton
+ * run a group of CTAs sized by its cost (large scenes get several dedicated
+ * CTAs that combine their sums behind a per-scene barrier, small ones share
+ * CTAs in longest-first order).  Allocates and uploads the plan's device
+ * tables (synchronously, on the current device): the only allocating batch
+ * call.  The items' fields, positions, latent codes and the workspace must
+ * outlive the plan.  *out is set only on NSF_OK.
+ */
+nsf_status nsf_latent_batch_create(int n_items, const nsf_latent_batch_item *items,
+                                   const nsf_gn_opts *opts, void *d_workspace,
+                                   size_t workspace_bytes, nsf_latent_batch **out);
+void nsf_latent_batch_destroy(nsf_latent_batch *batch);
+
+/* Optional stage events of nsf_latent_step_batched (cudaEvent_t handles or
+ * NULL), recorded around each stage's launches of the last step. */
+typedef struct nsf_batch_events {
+    void *ev_begin[NSF_LATENT_STAGES];
+    void *ev_end[NSF_LATENT_STAGES];
+} nsf_batch_events;
+
+/*
+ * nsteps latent steps of every scene of the batch (the steps of
+ * nsf_latent_step).  t0 is the time at the start of the first step.  flags:
+ * NSF_LATENT_REUSE_PREV as in nsf_latent_step (the workspace holds every
+ * scene's g(X, z_prev) from the previous call on this plan).  Device-detected
+ * errors of any scene go to the one status word *d_status.  Enqueues on
+ * `stream` only; capturable in a CUDA graph.  events may be NULL.
+ */
+nsf_status nsf_latent_step_batched(const nsf_latent_batch *batch, double t0, int nsteps,
+                                   unsigned int flags, int *d_status,
+                                   const nsf_batch_events *events, void *stream);
+
 /* Constitutive models of the full-order step (paper App. F; neo-Hookean is the
  * textbook tau = mu (F F^T - I) + lambda ln(J) I).  The two plastic models use
  * the Hencky (StVK, App. F.2) stress of F^E and return-map F in float64. */

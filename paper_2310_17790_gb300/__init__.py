@@ -184,6 +184,40 @@ def nsf_project_static(fields, X_S, x_target, z, opts, status, z_iter=None, resi
           "nsf_project_static")
 
 
+def batch_items(entries):
+    """entries: sequence of (Fields, X [3, n_N] tensor, n_S, mass, vol0, grid_desc, dt,
+    z [r] float64 tensor, z_prev [r] float64 tensor) -> ctypes array of
+    nsf_latent_batch_item."""
+    arr = (N.nsf_latent_batch_item * len(entries))()
+    for i, (F, X, n_S, mass, vol0, grid, dt, z, zp) in enumerate(entries):
+        arr[i].fields = F.handle
+        arr[i].scene = latent_scene(X, n_S, mass, vol0, grid)
+        arr[i].dt = float(dt)
+        arr[i].d_z = _ptr(z)
+        arr[i].d_z_prev = _ptr(zp)
+    return arr
+
+
+def nsf_latent_batch_workspace_size(items):
+    b = C.c_size_t()
+    check(N.lib.nsf_latent_batch_workspace_size(len(items), items, C.byref(b)),
+          "nsf_latent_batch_workspace_size")
+    return b.value
+
+
+def nsf_latent_batch_create(items, opts, workspace):
+    h = C.c_void_p()
+    check(N.lib.nsf_latent_batch_create(len(items), items, C.byref(opts), _ptr(workspace),
+                                        workspace.numel(), C.byref(h)), "nsf_latent_batch_create")
+    return h
+
+
+def nsf_latent_step_batched(batch, t0, nsteps, status, events=None, stream=None, flags=0):
+    check(N.lib.nsf_latent_step_batched(batch, float(t0), int(nsteps), int(flags), _ptr(status),
+                                        C.byref(events) if events is not None else None,
+                                        _stream(stream)), "nsf_latent_step_batched")
+
+
 def nsf_full_workspace_size(grid, n):
     b = C.c_size_t()
     check(N.lib.nsf_full_workspace_size(C.byref(grid), int(n), C.byref(b)),
@@ -240,6 +274,39 @@ class LatentStepper:
 
     def read_status(self):
         return int(self.status.item())
+
+
+class LatentBatch:
+    """Plan, workspace and status word of a batch of latent scenes stepped
+    together (nsf_latent_step_batched).  entries as in batch_items; the
+    tensors must stay alive with the batch."""
+
+    def __init__(self, entries, iters=5, damping=1e-6):
+        torch = _torch()
+        self.entries = list(entries)
+        self.items = batch_items(self.entries)
+        dev = self.entries[0][1].device
+        self.ws = _zeros_u8(nsf_latent_batch_workspace_size(self.items), dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.handle = nsf_latent_batch_create(self.items, gn_opts(iters, damping), self.ws)
+
+    def step(self, t0=0.0, nsteps=1, events=None, stream=None, reuse_prev=False):
+        nsf_latent_step_batched(self.handle, t0, nsteps, self.status, events, stream,
+                                N.NSF_LATENT_REUSE_PREV if reuse_prev else 0)
+
+    def read_status(self):
+        return int(self.status.item())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib.nsf_latent_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FullStepper:

@@ -32,6 +32,7 @@ NSF_LATENT_STAGES = 3
 NSF_LATENT_REUSE_PREV = 1
 NSF_PROJECT_STATIC_MAX_S = 2048
 NSF_PROJECT_STATIC_BYTES = 1 << 20
+NSF_MAX_BATCH = 1024
 
 
 class nsf_fields_desc(C.Structure):
@@ -60,6 +61,16 @@ class nsf_latent_taps(C.Structure):
                 ("C9", C.c_void_p), ("grid_mp", C.c_void_p), ("grid_v", C.c_void_p),
                 ("u_next_S", C.c_void_p), ("z_iter", C.c_void_p),
                 ("ev_begin", C.c_void_p * NSF_LATENT_STAGES),
+                ("ev_end", C.c_void_p * NSF_LATENT_STAGES)]
+
+
+class nsf_latent_batch_item(C.Structure):
+    _fields_ = [("fields", C.c_void_p), ("scene", nsf_latent_scene), ("dt", C.c_double),
+                ("d_z", C.c_void_p), ("d_z_prev", C.c_void_p)]
+
+
+class nsf_batch_events(C.Structure):
+    _fields_ = [("ev_begin", C.c_void_p * NSF_LATENT_STAGES),
                 ("ev_end", C.c_void_p * NSF_LATENT_STAGES)]
 
 
@@ -96,6 +107,11 @@ SIGNATURES = [
     ("nsf_project_workspace_size", _ST, [_P, _I, C.POINTER(_S)]),
     ("nsf_project", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _S, _P, _P]),
     ("nsf_project_static", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _P]),
+    ("nsf_latent_batch_workspace_size", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(_S)]),
+    ("nsf_latent_batch_create", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(nsf_gn_opts),
+                                      _P, _S, C.POINTER(_P)]),
+    ("nsf_latent_batch_destroy", None, [_P]),
+    ("nsf_latent_step_batched", _ST, [_P, _D, _I, C.c_uint, _P, C.POINTER(nsf_batch_events), _P]),
     ("nsf_full_workspace_size", _ST, [C.POINTER(nsf_grid_desc), _I, C.POINTER(_S)]),
     ("nsf_full_step", _ST, [C.POINTER(nsf_grid_desc), C.POINTER(nsf_material),
                             C.POINTER(nsf_particles), _D, _D, _I, _P, _S, _P,

@@ -1,11 +1,13 @@
 // Host side of the libnsf C ABI (include/nsf.h): argument validation, weight
 // packing, workspace layout and the launch sequence of each call.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "device_common.cuh"
+#include "tc_common.cuh"
 
 using namespace nsf;
 
@@ -627,6 +629,477 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
         NSF_CUDA_TRY(launch_mpm_full(g, gp, pa, ga, t0 + step * dt,
                                      last && taps ? taps->grid_mp : nullptr,
                                      last && taps ? taps->grid_v : nullptr, d_status, s));
+    }
+    return NSF_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ batches ===
+// Batched latent stepping (nsf_latent_step_batched): host-side plan.
+namespace nsf {
+size_t jac_tc_smem_bytes(int r, int width, int depth);
+}
+
+namespace {
+
+// u[1] <- u[0] for every scene (flat index over the scenes' 3 n_N values).
+__global__ void k_batch_keep_prev(const BatchSceneDev *scenes, const int *n_off, int ns) {
+    const int total = 3 * n_off[ns];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int lo = 0, hi = ns;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (3 * n_off[mid] <= q) lo = mid;
+            else hi = mid;
+        }
+        const BatchSceneDev &sc = scenes[lo];
+        const int i = q - 3 * n_off[lo];
+        sc.u[1][i] = sc.u[0][i];
+    }
+}
+
+bool valid_batch_item(const nsf_latent_batch_item &it) {
+    const nsf_latent_scene *sc = &it.scene;
+    return it.fields && it.d_z && it.d_z_prev && sc->d_X && sc->n_N >= 1 && sc->n_S >= 1 &&
+           sc->n_S <= sc->n_N && valid_grid(&sc->grid) && it.dt > 0.0 && std::isfinite(it.dt) &&
+           sc->mass > 0.f && sc->vol0 > 0.f;
+}
+
+// Per-scene layouts inside the batch workspace, after a 256-byte control block
+// (the MPM launch's grid-barrier word).
+struct BatchLayout {
+    std::vector<size_t> base;
+    std::vector<LatentLayout> scene;
+    size_t total;
+};
+
+BatchLayout batch_layout(int n, const nsf_latent_batch_item *items) {
+    BatchLayout B;
+    size_t off = align_up(256);
+    for (int i = 0; i < n; ++i) {
+        LatentLayout L = latent_layout(items[i].fields, &items[i].scene);
+        B.base.push_back(off);
+        B.scene.push_back(L);
+        off = align_up(off + L.total);
+    }
+    B.total = off;
+    return B;
+}
+
+// Work lists of one field width: jobs cut into runs of tiles so that every
+// CTA gets about the same cost (tiles x depth), in job order.
+struct WidthPlan {
+    int W = 0, maxD = 1, nctas = 0;
+    std::vector<FieldBatchItem> items;
+    std::vector<int> cta_item;     // nctas + 1 offsets
+};
+
+WidthPlan plan_width(int W, int n, const nsf_latent_batch_item *items, bool with_prev, int sms) {
+    WidthPlan P;
+    P.W = W;
+    struct Job { int scene, field, zsel, tiles, depth; };
+    std::vector<Job> jobs;
+    double total = 0.0;
+    for (int s = 0; s < n; ++s) {
+        const nsf_fields_desc &d = items[s].fields->desc;
+        const int tiles = (items[s].scene.n_N + 127) / 128;
+        for (int f = 0; f < 3; ++f) {
+            if (d.width[f] != W) continue;
+            P.maxD = d.depth[f] > P.maxD ? d.depth[f] : P.maxD;
+            jobs.push_back({s, f, 0, tiles, d.depth[f]});
+            total += (double)tiles * d.depth[f];
+            if (f == NSF_FIELD_G && with_prev) {
+                jobs.push_back({s, f, 1, tiles, d.depth[f]});
+                total += (double)tiles * d.depth[f];
+            }
+        }
+    }
+    long long all_tiles = 0;
+    for (const Job &j : jobs) all_tiles += j.tiles;
+    if (all_tiles == 0) return P;
+    P.nctas = (int)(all_tiles < sms ? all_tiles : sms);
+    const double target = total / P.nctas;
+    std::vector<std::vector<FieldBatchItem>> per(P.nctas);
+    double cum = 0.0;
+    for (const Job &j : jobs) {
+        int t = 0;
+        while (t < j.tiles) {
+            int cta = (int)((cum + 0.5 * j.depth) / target);
+            if (cta >= P.nctas) cta = P.nctas - 1;
+            // extend the run while the tiles fall to the same CTA
+            int t1 = t + 1;
+            double c = cum + j.depth;
+            while (t1 < j.tiles) {
+                int c2 = (int)((c + 0.5 * j.depth) / target);
+                if (c2 >= P.nctas) c2 = P.nctas - 1;
+                if (c2 != cta) break;
+                ++t1;
+                c += j.depth;
+            }
+            per[cta].push_back({j.scene, j.field, j.zsel, t, t1});
+            cum = c;
+            t = t1;
+        }
+    }
+    P.cta_item.push_back(0);
+    for (int c = 0; c < P.nctas; ++c) {
+        for (const FieldBatchItem &it : per[c]) P.items.push_back(it);
+        P.cta_item.push_back((int)P.items.size());
+    }
+    return P;
+}
+
+// Gauss-Newton CTA schedule: scenes whose cost is at least two CTAs' share get
+// that many dedicated CTAs (a group that combines its sums behind the scene's
+// barrier); the others are packed whole onto the remaining CTAs, longest
+// first, each onto the least loaded CTA.
+struct GnPlan {
+    std::vector<GnBatchEntry> entries;
+    std::vector<int> cta_entry;
+    int nctas = 0;
+    size_t smem = 0;
+};
+
+int jac_slots_host(int r) {
+    int L = 2;
+    while (L < 1 + r) L <<= 1;
+    return L;
+}
+
+GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
+    GnPlan G;
+    std::vector<double> cost(n);
+    std::vector<int> tiles(n);
+    double total = 0.0;
+    for (int s = 0; s < n; ++s) {
+        const nsf_fields_desc &d = items[s].fields->desc;
+        const int P = jac_points_per_cta_tile(d.r);
+        tiles[s] = (items[s].scene.n_S + P - 1) / P;
+        const double wq = (double)d.width[NSF_FIELD_G] / 64.0;
+        const int L = jac_slots_host(d.r);
+        cost[s] = (double)tiles[s] * d.depth[NSF_FIELD_G] * wq * wq * (L > 8 ? L : 8) / 8.0;
+        total += cost[s];
+        const size_t sm = jac_tc_smem_bytes(d.r, d.width[NSF_FIELD_G], d.depth[NSF_FIELD_G]);
+        G.smem = sm > G.smem ? sm : G.smem;
+    }
+    const int cap = sms < kGnMaxCtas ? sms : kGnMaxCtas;
+    const double share = total / cap;
+    std::vector<int> group(n, 0);
+    int used = 0, nsmall = 0;
+    for (int s = 0; s < n; ++s) {
+        int g = (int)(cost[s] / share);
+        if (g > tiles[s]) g = tiles[s];
+        if (g > cap) g = cap;
+        if (g >= 2) {
+            group[s] = g;
+            used += g;
+        } else {
+            ++nsmall;
+        }
+    }
+    // leave at least one CTA for the small scenes
+    while (used > cap - (nsmall > 0 ? 1 : 0)) {
+        int big = -1;
+        for (int s = 0; s < n; ++s)
+            if (group[s] >= 2 && (big < 0 || group[s] > group[big])) big = s;
+        if (group[big] == 2) {
+            group[big] = 0;
+            used -= 2;
+            ++nsmall;
+        } else {
+            --group[big];
+            --used;
+        }
+    }
+    std::vector<std::vector<GnBatchEntry>> per;
+    for (int s = 0; s < n; ++s)
+        for (int k = 0; k < group[s]; ++k) per.push_back({GnBatchEntry{s, k, group[s]}});
+    int room = cap - used;
+    if (nsmall > 0) {
+        const int m = nsmall < room ? nsmall : room;
+        std::vector<int> order;
+        for (int s = 0; s < n; ++s)
+            if (group[s] < 2) order.push_back(s);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<double> load(m, 0.0);
+        std::vector<std::vector<GnBatchEntry>> small(m);
+        for (int s : order) {
+            int best = 0;
+            for (int c = 1; c < m; ++c)
+                if (load[c] < load[best]) best = c;
+            load[best] += cost[s];
+            small[best].push_back(GnBatchEntry{s, 0, 1});
+        }
+        for (auto &v : small) per.push_back(v);
+    }
+    G.nctas = (int)per.size();
+    G.cta_entry.push_back(0);
+    for (auto &v : per) {
+        for (auto &e : v) G.entries.push_back(e);
+        G.cta_entry.push_back((int)G.entries.size());
+    }
+    return G;
+}
+
+// Device tables of a plan, laid out in one allocation.
+struct TableCarver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        size_t o = align_up(off);
+        off = o + count * sizeof(T);
+        return o;
+    }
+};
+
+}  // namespace
+
+struct nsf_latent_batch {
+    int n;
+    nsf_gn_opts opts;
+    void *d_mem;
+    BatchSceneDev *scenes;
+    int *n_off, *s_off;
+    unsigned *mpm_bar;
+    struct Width {
+        int W, maxD;
+        int nctas[2];                 // [0]: g, h, l per scene; [1]: plus g at z_prev
+        FieldBatchItem *items[2];
+        int *cta_item[2];
+    };
+    std::vector<Width> widths;
+    GnBatchProblem *probs;
+    GnBatchEntry *entries;
+    int *cta_entry;
+    int gn_ctas;
+    size_t gn_smem;
+};
+
+extern "C" {
+
+nsf_status nsf_latent_batch_workspace_size(int n, const nsf_latent_batch_item *items,
+                                           size_t *bytes) {
+    if (n < 1 || n > NSF_MAX_BATCH || !items || !bytes) return NSF_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (!items[i].fields || items[i].scene.n_N < 1 || items[i].scene.n_S < 1 ||
+            items[i].scene.n_S > items[i].scene.n_N || !valid_grid(&items[i].scene.grid))
+            return NSF_ERR_INVALID_ARG;
+    *bytes = batch_layout(n, items).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
+                                   const nsf_gn_opts *opts, void *d_ws, size_t ws_bytes,
+                                   nsf_latent_batch **out) {
+    if (!out || n < 1 || n > NSF_MAX_BATCH || n > kMaxBatchScenes || !items || !valid_gn(opts))
+        return NSF_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!valid_batch_item(items[i])) return NSF_ERR_INVALID_ARG;
+        const nsf_fields_desc &d = items[i].fields->desc;
+        if (d.precision != NSF_PREC_BF16) return NSF_ERR_UNSUPPORTED;
+    }
+    const BatchLayout BL = batch_layout(n, items);
+    if (!d_ws || ws_bytes < BL.total) return NSF_ERR_WORKSPACE;
+    char *ws = static_cast<char *>(d_ws);
+    const int sms = tc::sm_count();
+
+    // distinct fields objects
+    std::vector<const nsf_fields *> fobj;
+    std::vector<int> fidx(n);
+    for (int i = 0; i < n; ++i) {
+        int k = -1;
+        for (size_t j = 0; j < fobj.size(); ++j)
+            if (fobj[j] == items[i].fields) k = (int)j;
+        if (k < 0) {
+            k = (int)fobj.size();
+            fobj.push_back(items[i].fields);
+        }
+        fidx[i] = k;
+    }
+    // work lists
+    std::vector<WidthPlan> wp[2];
+    static const int kWidths[4] = {64, 128, 192, 256};
+    for (int w : kWidths)
+        for (int set = 0; set < 2; ++set) {
+            WidthPlan P = plan_width(w, n, items, set == 1, sms);
+            if (P.nctas > 0) wp[set].push_back(P);
+        }
+    const GnPlan G = plan_gn(n, items, sms);
+
+    // table layout
+    TableCarver tc_;
+    const size_t o_fd = tc_.take<FieldsDev>(fobj.size());
+    const size_t o_sc = tc_.take<BatchSceneDev>(n);
+    const size_t o_no = tc_.take<int>(n + 1), o_so = tc_.take<int>(n + 1);
+    size_t o_items[2][4], o_cta[2][4];
+    for (int set = 0; set < 2; ++set)
+        for (size_t k = 0; k < wp[set].size(); ++k) {
+            o_items[set][k] = tc_.take<FieldBatchItem>(wp[set][k].items.size());
+            o_cta[set][k] = tc_.take<int>(wp[set][k].cta_item.size());
+        }
+    const size_t o_pr = tc_.take<GnBatchProblem>(n);
+    const size_t o_en = tc_.take<GnBatchEntry>(G.entries.size());
+    const size_t o_ce = tc_.take<int>(G.cta_entry.size());
+    const size_t tbytes = align_up(tc_.off);
+    std::vector<char> h(tbytes, 0);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, tbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return NSF_ERR_NO_MEMORY;
+    }
+    char *dm = static_cast<char *>(mem);
+    auto put = [&](size_t off, const void *src, size_t bytes) { std::memcpy(h.data() + off, src, bytes); };
+
+    for (size_t j = 0; j < fobj.size(); ++j) put(o_fd + j * sizeof(FieldsDev), &fobj[j]->dev, sizeof(FieldsDev));
+    std::vector<int> noff(n + 1, 0), soff(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const nsf_latent_batch_item &it = items[i];
+        const LatentLayout &L = BL.scene[i];
+        char *base = ws + BL.base[i];
+        BatchSceneDev sd;
+        std::memset(&sd, 0, sizeof(sd));
+        sd.fd = reinterpret_cast<const FieldsDev *>(dm + o_fd + fidx[i] * sizeof(FieldsDev));
+        sd.X = it.scene.d_X;
+        sd.n_N = it.scene.n_N;
+        sd.n_S = it.scene.n_S;
+        sd.mass = it.scene.mass;
+        sd.vol0 = it.scene.vol0;
+        sd.dt = (float)it.dt;
+        sd.inv_dt = (float)(1.0 / it.dt);
+        sd.residual_g = it.fields->dev.residual_g;
+        sd.u[0] = reinterpret_cast<float *>(base + L.u[0]);
+        sd.u[1] = reinterpret_cast<float *>(base + L.u[1]);
+        sd.tau6 = reinterpret_cast<float *>(base + L.tau);
+        sd.C9 = reinterpret_cast<float *>(base + L.C);
+        sd.dnext = reinterpret_cast<float *>(base + L.dnext);
+        sd.z = it.d_z;
+        sd.z_prev = it.d_z_prev;
+        sd.g = grid_ws(base, L.grid, &it.scene.grid, it.scene.n_N);
+        sd.gp = make_params(&it.scene.grid);
+        put(o_sc + i * sizeof(BatchSceneDev), &sd, sizeof(sd));
+        noff[i + 1] = noff[i] + it.scene.n_N;
+        soff[i + 1] = soff[i] + it.scene.n_S;
+
+        GnBatchProblem pb;
+        std::memset(&pb, 0, sizeof(pb));
+        pb.fd = sd.fd;
+        pb.X = it.scene.d_X;
+        pb.n = it.scene.n_S;
+        pb.ld = it.scene.n_N;
+        pb.gn = gn_args(base, L.gn);
+        pb.gn.target = sd.dnext;
+        pb.gn.target_ld = it.scene.n_S;
+        pb.gn.iters = opts->iters;
+        pb.gn.z_start = it.d_z;
+        pb.gn.z_out = it.d_z;
+        pb.gn.z_prev_out = it.d_z_prev;
+        pb.gn.z_taps = nullptr;
+        pb.gn.damping = opts->damping;
+        put(o_pr + i * sizeof(GnBatchProblem), &pb, sizeof(pb));
+    }
+    if (noff[n] > (1 << 30) / 3) {
+        cudaFree(mem);
+        return NSF_ERR_INVALID_ARG;
+    }
+    put(o_no, noff.data(), (n + 1) * sizeof(int));
+    put(o_so, soff.data(), (n + 1) * sizeof(int));
+    for (int set = 0; set < 2; ++set)
+        for (size_t k = 0; k < wp[set].size(); ++k) {
+            put(o_items[set][k], wp[set][k].items.data(), wp[set][k].items.size() * sizeof(FieldBatchItem));
+            put(o_cta[set][k], wp[set][k].cta_item.data(), wp[set][k].cta_item.size() * sizeof(int));
+        }
+    put(o_en, G.entries.data(), G.entries.size() * sizeof(GnBatchEntry));
+    put(o_ce, G.cta_entry.data(), G.cta_entry.size() * sizeof(int));
+    if (cudaMemcpy(mem, h.data(), tbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(mem);
+        return NSF_ERR_CUDA;
+    }
+    nsf_latent_batch *B = new (std::nothrow) nsf_latent_batch;
+    if (!B) {
+        cudaFree(mem);
+        return NSF_ERR_NO_MEMORY;
+    }
+    B->n = n;
+    B->opts = *opts;
+    B->d_mem = mem;
+    B->scenes = reinterpret_cast<BatchSceneDev *>(dm + o_sc);
+    B->n_off = reinterpret_cast<int *>(dm + o_no);
+    B->s_off = reinterpret_cast<int *>(dm + o_so);
+    B->mpm_bar = reinterpret_cast<unsigned *>(ws);
+    // width classes: the same widths appear in both sets
+    for (size_t k = 0; k < wp[0].size(); ++k) {
+        nsf_latent_batch::Width w;
+        w.W = wp[0][k].W;
+        w.maxD = wp[0][k].maxD;
+        for (int set = 0; set < 2; ++set) {
+            w.nctas[set] = wp[set][k].nctas;
+            w.items[set] = reinterpret_cast<FieldBatchItem *>(dm + o_items[set][k]);
+            w.cta_item[set] = reinterpret_cast<int *>(dm + o_cta[set][k]);
+        }
+        B->widths.push_back(w);
+    }
+    B->probs = reinterpret_cast<GnBatchProblem *>(dm + o_pr);
+    B->entries = reinterpret_cast<GnBatchEntry *>(dm + o_en);
+    B->cta_entry = reinterpret_cast<int *>(dm + o_ce);
+    B->gn_ctas = G.nctas;
+    B->gn_smem = G.smem;
+    *out = B;
+    return NSF_OK;
+}
+
+void nsf_latent_batch_destroy(nsf_latent_batch *b) {
+    if (!b) return;
+    cudaFree(b->d_mem);
+    delete b;
+}
+
+nsf_status nsf_latent_step_batched(const nsf_latent_batch *b, double t0, int nsteps,
+                                   unsigned int flags, int *d_status,
+                                   const nsf_batch_events *events, void *stream) {
+    if (!b || nsteps < 0 || !std::isfinite(t0) || (flags & ~(unsigned)NSF_LATENT_REUSE_PREV))
+        return NSF_ERR_INVALID_ARG;
+    if (nsteps == 0) return NSF_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool reuse = (flags & NSF_LATENT_REUSE_PREV) != 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (events) NSF_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                   : cudaEventRecordDefault;
+    auto ev = [&](bool on, void *const *arr, int stage) -> cudaError_t {
+        if (!on || !arr[stage]) return cudaSuccess;
+        return cudaEventRecordWithFlags(static_cast<cudaEvent_t>(arr[stage]), s, ev_flags);
+    };
+    for (int step = 0; step < nsteps; ++step) {
+        const bool tev = step == nsteps - 1 && events;
+        const int parity = step & 1;
+        const int set = (step == 0 && !reuse) ? 1 : 0;
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_INFERENCE));
+        for (const auto &w : b->widths)
+            NSF_CUDA_TRY(launch_fields_batch(w.W, b->scenes, w.items[set], w.cta_item[set],
+                                             w.nctas[set], parity, w.maxD, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_INFERENCE));
+        MpmBatchArgs ma;
+        ma.scenes = b->scenes;
+        ma.nscenes = b->n;
+        ma.n_off = b->n_off;
+        ma.s_off = b->s_off;
+        ma.parity = parity;
+        ma.t0 = t0;
+        ma.step = step;
+        ma.bar = b->mpm_bar;
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_MPM));
+        NSF_CUDA_TRY(launch_mpm_batch(ma, d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_MPM));
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_GN));
+        NSF_CUDA_TRY(launch_jac_batch(b->probs, b->entries, b->cta_entry, b->gn_ctas, b->gn_smem,
+                                      d_status, s));
+        NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_GN));
+    }
+    // keep every scene's g(X, z_prev) of the returned z_prev in u[1]
+    if (((nsteps - 1) & 1) == 0) {
+        k_batch_keep_prev<<<2 * tc::sm_count(), 256, 0, s>>>(b->scenes, b->n_off, b->n);
+        NSF_CUDA_TRY(cudaGetLastError());
     }
     return NSF_OK;
 }

@@ -32,12 +32,15 @@ __device__ __forceinline__ float elu_grad(float a) { return a > 0.f ? 1.f : expf
 // which they are back at zero, so the word is ready for the next barrier with
 // no reset.  Every thread of every CTA calls it.  Returns false after
 // recording NSF_ERR_ITER_CAP if the wait ran out; the word is then undefined.
-__device__ inline bool grid_barrier(unsigned *word, int *status) {
+//
+// group_barrier is the same over the `size` CTAs of a group that share `word`,
+// the CTA of rank 0 taking the part of CTA 0.
+__device__ inline bool group_barrier(unsigned *word, int rank, int size, int *status) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         s_ok = 1;
-        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+        const unsigned inc = rank == 0 ? 0x80000000u - (unsigned)(size - 1) : 1u;
         __threadfence();
         const unsigned old = atomicAdd(word, inc);
         volatile unsigned *w = word;
@@ -53,6 +56,10 @@ __device__ inline bool grid_barrier(unsigned *word, int *status) {
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ inline bool grid_barrier(unsigned *word, int *status) {
+    return group_barrier(word, (int)blockIdx.x, (int)gridDim.x, status);
 }
 
 // Upper-triangle (i <= j) packed index of an r x r symmetric matrix.

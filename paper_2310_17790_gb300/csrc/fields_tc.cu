@@ -118,18 +118,59 @@ __device__ __forceinline__ void bias_elu(float *v, const float *bl) {
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kMaxGroups * kGroupThreads, 1)
-k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
-            const __grid_constant__ TcJobs jobs, int ng, int *status) {
-    extern __shared__ uint8_t smem_dyn[];
+// One work item of the value kernel: field F at latent code z on the
+// 128-point tiles [tile0, tile1) of the point set X ([3][ld], n points),
+// outputs to out ([out_dim][ld]).
+struct ItemView {
+    const FieldDev *F;
+    int r;
+    const float *X;
+    int n, ld;
+    const double *z;
+    float *out;
+    int tile0, tile1;
+};
+
+// Work items of the single-problem launch: CTA (x, y) runs job y on its
+// contiguous share of the tiles.
+struct SingleSrc {
+    const FieldsDev *fd;
+    const float *X;
+    int n, ld;
+    const TcJobs *jobs;
+    __device__ ItemView item(int) const {
+        const FieldJob &job = jobs->job[blockIdx.y];
+        const int tiles = (n + kM - 1) / kM;
+        const int per = (tiles + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int t0 = (int)blockIdx.x * per;
+        return ItemView{&fd->f[job.field], fd->r, X, n, ld, job.z, job.out, t0,
+                        t0 + per < tiles ? t0 + per : tiles};
+    }
+};
+
+// Work items of a batched launch: CTA c runs items cta_item[c] .. cta_item[c +
+// 1] - 1; a g item writes the step's current displacement buffer (zsel 0, z_n)
+// or the other one (zsel 1, z_{n-1}).
+struct BatchSrc {
+    const BatchSceneDev *scenes;
+    const FieldBatchItem *items;
+    int e0, parity;
+    __device__ ItemView item(int k) const {
+        const FieldBatchItem it = items[e0 + k];
+        const BatchSceneDev &sc = scenes[it.scene];
+        float *out = it.field == NSF_FIELD_G ? sc.u[it.zsel ? parity ^ 1 : parity]
+                     : it.field == NSF_FIELD_H ? sc.tau6 : sc.C9;
+        return ItemView{&sc.fd->f[it.field], sc.fd->r, sc.X, sc.n_N, sc.n_N,
+                        it.zsel ? sc.z_prev : sc.z, out, it.tile0, it.tile1};
+    }
+};
+
+template <int W, class Src>
+__device__ __forceinline__ void fields_body(const Src &src, int nitems, int ng, int maxD,
+                                            uint8_t *smem_dyn, int *status) {
     __shared__ int s_ok[kMaxGroups];
     uint8_t *base = aligned_smem(smem_dyn);
 
-    const FieldJob &job = jobs.job[blockIdx.y];
-    const FieldDev &F = fd.f[job.field];
-    const int D = F.depth, r = fd.r;
-    const int tiles = (n + kM - 1) / kM;
     const int tid = threadIdx.x;
     const int grp = tid / kGroupThreads;     // tile group
     const int gt = tid % kGroupThreads;      // thread within the group
@@ -139,7 +180,7 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
     constexpr int kC = cw < 32 ? cw : 32;    // columns per chunk of the epilogue
     const int cbeg = (gt >> 7) * cw;
     const int bar_id = 1 + grp;              // the group's named barrier
-    const TcLayout L = tc_layout(W, D);
+    const TcLayout L = tc_layout(W, maxD);
     uint8_t *blob = base + L.blob;
     // input layer by column pairs (j, j + 1): {w_x j, w_x j+1, w_y j, w_y j+1},
     // {w_z j, w_z j+1, c0 j, c0 j+1}, so a pair's values load as register pairs
@@ -164,46 +205,56 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
     const uint32_t tmem = *tmem_holder;
     const uint32_t acc = tmem + (uint32_t)(grp * tmem_region(W));   // FP32 accumulator
     const uint32_t act = acc + (uint32_t)W;                          // bf16 activations
+    const uint32_t b_addr = smem_u32(blob);
+    const uint32_t idesc_h = idesc_bf16(kM, W);
+    const uint32_t idesc_o = idesc_bf16(kM, kMaxOut);
+    const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
+    const uint32_t acc_l = acc + lane_off;                           // this warp's lanes
+    const uint32_t act_l = act + lane_off + (uint32_t)(cbeg / 2);    // its activation columns
+    uint32_t phase = 0, phase_w = 0;
+    bool go_sent = false, go_waited = false;
+    bool copy_pending = false;
+    const FieldDev *curF = nullptr;
 
-    // weights: one bulk copy, landing while the CTA prepares the input layer
-    if (tid == 0) bulk_load(blob, F.tc_blob, (uint32_t)F.tc_blob_bytes, bar_w);
-    const int in0 = 3 + r;
-    for (int j = tid; j < W; j += blockDim.x) {
-        // z-part of the input layer folded into its bias: c0 = b0 + W0[:, 3:] z
-        const float *w = F.W0 + (size_t)j * in0;
-        float c0 = F.b[0][j];
-        for (int k = 0; k < r; ++k) c0 = fmaf(w[3 + k], (float)__ldcg(&job.z[k]), c0);
-        float *pr = reinterpret_cast<float *>(W0v + 2 * (j >> 1)) + (j & 1);
-        pr[0] = w[0];
-        pr[2] = w[1];
-        pr[4] = w[2];
-        pr[6] = c0;
-    }
-    for (int l = 1; l <= D; ++l) {
-        const int o = l == D ? F.out_dim : W;
-        for (int j = tid; j < o; j += blockDim.x) bias[(l - 1) * W + j] = F.b[l][j];
-    }
-    __syncthreads();
-    if (!__syncthreads_and(mbar_wait(bar_w, 0))) {
-        if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
-        mbar_wait(bar_w, 0);      // bounded: let the copy land before leaving
-        goto teardown;
-    }
+    for (int it = 0; it < nitems; ++it) {
+        const ItemView I = src.item(it);
+        if (I.tile0 >= I.tile1) continue;
+        const FieldDev &F = *I.F;
+        const int D = F.depth, r = I.r;
+        __syncthreads();                      // the previous item is done with shared memory
+        const bool reload = I.F != curF;
+        // weights: one bulk copy, landing while the CTA prepares the input layer
+        if (reload && tid == 0) bulk_load(blob, F.tc_blob, (uint32_t)F.tc_blob_bytes, bar_w);
+        copy_pending = reload;
+        const int in0 = 3 + r;
+        for (int j = tid; j < W; j += blockDim.x) {
+            // z-part of the input layer folded into its bias: c0 = b0 + W0[:, 3:] z
+            const float *w = F.W0 + (size_t)j * in0;
+            float c0 = F.b[0][j];
+            for (int k = 0; k < r; ++k) c0 = fmaf(w[3 + k], (float)__ldcg(&I.z[k]), c0);
+            float *pr = reinterpret_cast<float *>(W0v + 2 * (j >> 1)) + (j & 1);
+            pr[0] = w[0];
+            pr[2] = w[1];
+            pr[4] = w[2];
+            pr[6] = c0;
+        }
+        for (int l = 1; l <= D; ++l) {
+            const int o = l == D ? F.out_dim : W;
+            for (int j = tid; j < o; j += blockDim.x) bias[(l - 1) * W + j] = F.b[l][j];
+        }
+        __syncthreads();
+        if (reload) {
+            if (!__syncthreads_and(mbar_wait(bar_w, phase_w))) {
+                if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+                goto teardown;
+            }
+            phase_w ^= 1u;
+            copy_pending = false;
+            curF = I.F;
+        }
 
-    {
-        const uint32_t b_addr = smem_u32(blob);
-        const uint32_t idesc_h = idesc_bf16(kM, W);
-        const uint32_t idesc_o = idesc_bf16(kM, kMaxOut);
-        const uint32_t lane_off = (uint32_t)(wq * 32) << 16;
-        const uint32_t acc_l = acc + lane_off;                 // this warp's accumulator lanes
-        const uint32_t act_l = act + lane_off + (uint32_t)(cbeg / 2);   // its activation columns
-        uint32_t phase = 0;
-        bool go_sent = false;
-
-        for (int j = grp;; j += ng) {
-            const int tile = blockIdx.x + j * gridDim.x;
-            if (tile >= tiles) break;
-            if (grp == 1 && j == 1) {
+        for (int tile = I.tile0 + grp; tile < I.tile1; tile += ng) {
+            if (grp == 1 && !go_waited) {
                 // Group 1 starts once group 0 has handed its first layer to the
                 // tensor core, so that from then on each group's epilogue runs
                 // while the tensor core works on the other group's product
@@ -211,19 +262,20 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
                 // same time and leave the tensor core idle meanwhile).
                 if (gt == 0) s_ok[1] = mbar_wait(bar_go, 0) ? 1 : 0;
                 named_sync(bar_id, kGroupThreads);
+                go_waited = true;
                 if (!s_ok[1]) {
                     if (gt == 0) set_status(status, NSF_ERR_ITER_CAP);
-                    break;
+                    goto teardown;
                 }
             }
             const int p = tile * kM + row;
-            const bool valid = p < n;
+            const bool valid = p < I.n;
             // ---- layer 0 on the CUDA cores, into the activation operand
             float x0 = 0.f, x1 = 0.f, x2 = 0.f;
             if (valid) {
-                x0 = X[p];
-                x1 = X[ld + p];
-                x2 = X[2 * ld + p];
+                x0 = I.X[p];
+                x1 = I.X[I.ld + p];
+                x2 = I.X[2 * I.ld + p];
             }
             const float2 xx0 = make_float2(x0, x0), xx1 = make_float2(x1, x1),
                          xx2 = make_float2(x2, x2);
@@ -314,7 +366,7 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
                             if (o < F.out_dim) {
                                 const float y = fmaf(F.scale[o], v[o] + bo[o], F.shift[o]);
                                 bad |= !isfinite(y);
-                                job.out[(size_t)o * ld + p] = y;
+                                I.out[(size_t)o * I.ld + p] = y;
                             }
                         }
                     }
@@ -322,17 +374,19 @@ k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, i
                 }
             }
         }
-        goto teardown;
+    }
+    goto teardown;
 
-    mma_timeout:
-        if (gt == 0) {
-            set_status(status, NSF_ERR_ITER_CAP);
-            // bounded: let the outstanding MMA finish before the memory is released
-            mbar_wait(bar_mma, phase ^ 1u);
-        }
+mma_timeout:
+    if (gt == 0) {
+        set_status(status, NSF_ERR_ITER_CAP);
+        // bounded: let the outstanding MMA finish before the memory is released
+        mbar_wait(bar_mma, phase ^ 1u);
     }
 
 teardown:
+    // a CTA must not leave while a weight copy may still be landing
+    if (copy_pending && tid == 0) mbar_wait(bar_w, phase_w);
     tmem_wait_st();
     tc_fence_before();
     __syncthreads();
@@ -340,6 +394,25 @@ teardown:
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
     }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMaxGroups * kGroupThreads, 1)
+k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
+            const __grid_constant__ TcJobs jobs, int ng, int maxD, int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    const SingleSrc src{&fd, X, n, ld, &jobs};
+    fields_body<W>(src, 1, ng, maxD, smem_dyn, status);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMaxGroups * kGroupThreads, 1)
+k_fields_batch(const BatchSceneDev *__restrict__ scenes, const FieldBatchItem *__restrict__ items,
+               const int *__restrict__ cta_item, int parity, int ng, int maxD, int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    const int e0 = cta_item[blockIdx.x], e1 = cta_item[blockIdx.x + 1];
+    const BatchSrc src{scenes, items, e0, parity};
+    fields_body<W>(src, e1 - e0, ng, maxD, smem_dyn, status);
 }
 
 // Tile groups a CTA runs for this field size (two where both groups' tensor
@@ -388,11 +461,46 @@ cudaError_t launch_fields_tc_w(const FieldsDev &fd, const float *X, int n, int l
     if (per_job < 1) per_job = 1;
     if (per_job > tiles) per_job = tiles;
     dim3 grid(per_job, tj.njobs);
-    k_fields_tc<W><<<grid, ng * kGroupThreads, sm, s>>>(fd, X, n, ld, tj, ng, status);
+    int maxD = 1;
+    for (int i = 0; i < tj.njobs; ++i) {
+        const int d = fd.f[tj.job[i].field].depth;
+        maxD = d > maxD ? d : maxD;
+    }
+    k_fields_tc<W><<<grid, ng * kGroupThreads, sm, s>>>(fd, X, n, ld, tj, ng, maxD, status);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t fields_batch_smem(int W, int maxD) { return (size_t)tc_layout(W, maxD).total; }
+int fields_batch_groups(int W) { return 2 * tmem_region(W) <= 512 ? 2 : 1; }
+
+namespace {
+template <int W>
+cudaError_t launch_batch_w(const BatchSceneDev *scenes, const FieldBatchItem *items,
+                           const int *cta_item, int nctas, int parity, int maxD, int *status,
+                           cudaStream_t s) {
+    static bool attr_done = false;
+    set_max_dynamic_smem(k_fields_batch<W>, attr_done);
+    const int ng = fields_batch_groups(W);
+    k_fields_batch<W><<<nctas, ng * kGroupThreads, tc_layout(W, maxD).total, s>>>(
+        scenes, items, cta_item, parity, ng, maxD, status);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_fields_batch(int W, const BatchSceneDev *scenes, const FieldBatchItem *items,
+                                const int *cta_item, int nctas, int parity, int maxD,
+                                int *status, cudaStream_t s) {
+    if (nctas <= 0) return cudaSuccess;
+    switch (W) {
+        case 64: return launch_batch_w<64>(scenes, items, cta_item, nctas, parity, maxD, status, s);
+        case 128: return launch_batch_w<128>(scenes, items, cta_item, nctas, parity, maxD, status, s);
+        case 192: return launch_batch_w<192>(scenes, items, cta_item, nctas, parity, maxD, status, s);
+        case 256: return launch_batch_w<256>(scenes, items, cta_item, nctas, parity, maxD, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // One launch per distinct field width among the jobs (the kernel is
 // specialised on the width so that its column loops unroll completely).

@@ -39,10 +39,6 @@ struct GnFF {
     int singular;
 };
 
-// CTAs of a cooperative Gauss-Newton launch are at most one per SM; a lane
-// adds the slots of CTAs lane, lane + 32, ...
-constexpr int kGnMaxSlotsPerLane = 5;
-constexpr int kGnMaxCtas = 32 * kGnMaxSlotsPerLane;
 
 // The CTA's Gauss-Newton state.  A namespace-scope shared variable, so that
 // the out-of-line helpers below address it as shared memory (a reference
@@ -166,18 +162,20 @@ __device__ __noinline__ void gn_ff_solve_warp(int r) {
 
 // Steps 2-5.  Every thread of every CTA calls; returns false if the barrier
 // wait ran out.
-__device__ __noinline__ bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, int *status) {
+// The CTA is `rank` of the `nblk` CTAs that share this run (the whole grid for
+// one problem, a CTA group of a batched launch).
+__device__ __noinline__ bool gn_ff_finish_iteration(const GnArgs &g, int r, int it, int rank,
+                                                    int nblk, int *status) {
     GnFF &sh = g_gn;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int T = r * (r + 1) / 2, S = gn_stride(r), C = r + 1;
-    const int nblk = gridDim.x;
     float2 *slots = g.slots + (size_t)(it & 1) * nblk * S;
     __syncthreads();
     // entry-major: the CTAs' values of one entry are contiguous, so the
     // reads below are coalesced
     for (int e = tid; e < S; e += blockDim.x)
-        __stcg(&slots[(size_t)e * nblk + blockIdx.x], make_float2(sh.part[e].hi, sh.part[e].lo));
-    if (!grid_barrier(g.bar, status)) return false;
+        __stcg(&slots[(size_t)e * nblk + rank], make_float2(sh.part[e].hi, sh.part[e].lo));
+    if (!group_barrier(g.bar, rank, nblk, status)) return false;
     // all loads of a lane first (one memory round trip), then the sums
     for (int e = warp; e < S; e += nwarps) {
         float2 v[kGnMaxSlotsPerLane];
@@ -220,7 +218,7 @@ __device__ __noinline__ bool gn_ff_finish_iteration(const GnArgs &g, int r, int 
             zn = z0;
         }
         sh.z[tid] = zn;
-        if (blockIdx.x == 0) {
+        if (rank == 0) {
             const double zd = ff_to_double(zn);
             if (g.z_taps) g.z_taps[(size_t)it * r + tid] = zd;
             if (fin) {

@@ -111,6 +111,10 @@ struct GnArgs {
     double damping;
 };
 int gn_partial_stride(int r);
+// CTAs that combine one Gauss-Newton run on the tensor-core path are at most
+// one per SM; a lane adds the slots of CTAs lane, lane + 32, ...
+constexpr int kGnMaxSlotsPerLane = 5;
+constexpr int kGnMaxCtas = 32 * kGnMaxSlotsPerLane;
 
 // CUDA-core FP32 path (fields_simt.cu).
 int jac_grid_size_simt(const FieldsDev &fd, int n);
@@ -134,6 +138,65 @@ cudaError_t launch_fields_tc(const FieldsDev &fd, const float *X, int n, int ld,
 cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int ld,
                                const double *z, float *u, float *dudz,
                                const GnArgs *gn, int *status, cudaStream_t s);
+
+// ------------------------------------------------------------- batches ---
+// One scene of a batched latent step, in device memory: its fields, reference
+// positions and the per-scene part of the batch workspace.
+struct BatchSceneDev {
+    const FieldsDev *fd;       // device copy of the scene's fields
+    const float *X;            // [3][n_N]
+    int n_N, n_S;
+    float mass, vol0, dt, inv_dt;
+    int residual_g;
+    float *u[2];               // g(X, z) displacement buffers (current / previous)
+    float *tau6, *C9;          // [6][n_N], [9][n_N]
+    float *dnext;              // [3][n_S] Gauss-Newton target
+    double *z, *z_prev;        // caller's latent codes
+    GridWs g;
+    GridParams gp;
+};
+// A field evaluation of a batched step: field `field` of scene `scene` at z_n
+// (zsel 0) or z_{n-1} (zsel 1) on 128-point tiles [tile0, tile1).
+struct FieldBatchItem {
+    int scene, field, zsel, tile0, tile1;
+};
+// Value kernel over a batch: CTA c runs items cta_item[c] .. cta_item[c+1]-1,
+// all of width W (64, 128, 192 or 256).
+cudaError_t launch_fields_batch(int W, const BatchSceneDev *scenes, const FieldBatchItem *items,
+                                const int *cta_item, int nctas, int parity, int maxD,
+                                int *status, cudaStream_t s);
+size_t fields_batch_smem(int W, int maxD);
+int fields_batch_groups(int W);
+
+// MPM part of a batched latent step (mpm.cu): one cooperative launch.
+constexpr int kMaxBatchScenes = 1024;
+struct MpmBatchArgs {
+    const BatchSceneDev *scenes;
+    int nscenes;
+    const int *n_off;          // [nscenes + 1] prefix sums of n_N
+    const int *s_off;          // [nscenes + 1] prefix sums of n_S
+    int parity;                // scenes' u[parity] holds g(X, z_n)
+    double t0;                 // time of the call's first step
+    int step;                  // step index within the call (t = t0 + step dt per scene)
+    unsigned *bar;             // grid-barrier word, zero before the first launch
+};
+cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int *status, cudaStream_t s);
+
+// Batched Gauss-Newton (jacobian_tc.cu): one problem per scene, each run by a
+// group of CTAs of one cooperative launch.
+struct GnBatchProblem {
+    const FieldsDev *fd;       // device copy of the scene's fields
+    const float *X;            // [3][ld] reference positions (first n are the samples)
+    int n, ld;
+    GnArgs gn;                 // target, z, slots (sized for the group), barrier word
+};
+struct GnBatchEntry {
+    int problem, rank, size;
+};
+int jac_points_per_cta_tile(int r);
+cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
+                             const int *cta_entry, int nctas, size_t smem, int *status,
+                             cudaStream_t s);
 
 // MPM step: one cooperative launch each (P2G, block activation, grid update
 // and, for the latent step, G2P, with grid-wide barriers between the phases).  After a barrier timeout

@@ -96,12 +96,13 @@ __device__ __forceinline__ void store_b_row(uint8_t *B, int k, int n0, int sbo, 
         *reinterpret_cast<uint4 *>(B + b_chunk(k, n0 + 8 * g, sbo)) = pack_bf16x8(v + 8 * g);
 }
 
+// One CTA's share of a Jacobian evaluation or Gauss-Newton run: the CTA is
+// `rank` of the `gsize` CTAs that work on this point set (tiles rank, rank +
+// gsize, ...) and, for Gauss-Newton, combine their sums behind gn.bar.
 template <int CW>
-__global__ void __launch_bounds__(kThreads, 1)
-k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
-         const double *zj, float *u, float *dudz, const __grid_constant__ GnArgs gn, int gn_on,
-         int *status) {
-    extern __shared__ uint8_t smem_dyn[];
+__device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n, int ld,
+                         const double *zj, float *u, float *dudz, const GnArgs &gn, int gn_on,
+                         int rank, int gsize, bool last_alloc, uint8_t *smem_dyn, int *status) {
     __shared__ int s_abort;
     uint8_t *base = aligned_smem(smem_dyn);
 
@@ -142,7 +143,7 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < 32) tmem_alloc(tmem_holder, ncols);
+    if (tid < 32) tmem_alloc(tmem_holder, ncols, last_alloc);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -160,8 +161,7 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         const int o = l == D ? F.out_dim : W;
         for (int j = tid; j < o; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
     }
-    // positions (and Gauss-Newton targets) of this CTA's first tile; a
-    // Gauss-Newton run revisits the same tile in every iteration
+    // positions (and Gauss-Newton targets) of a tile of this CTA
     auto load_tile = [&](int t0) {
         if (tid < P) {
             const int p = t0 + tid;
@@ -175,7 +175,8 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
             }
         }
     };
-    load_tile(blockIdx.x * P);
+    load_tile(rank * P);
+    int loaded = rank;                       // the tile whose points xs, tg hold
     if (gn_on) gn_ff_begin(gn, r);
     bool weights_ready = false;
     const uint32_t blob_addr = smem_u32(blob);
@@ -197,12 +198,15 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
         }
         __syncthreads();
 
-        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        for (int tile = rank; tile < tiles; tile += gsize) {
             const int p0 = tile * P;
-            if (tile != (int)blockIdx.x) {
+            if (tile != loaded) {
+                // a CTA with several tiles reloads its first one in every
+                // Gauss-Newton iteration after the first
                 __syncthreads();
                 load_tile(p0);
                 __syncthreads();
+                loaded = tile;
             }
             // ---- layer 0 on the CUDA cores: this thread's neurons, its columns
             for (int h = 0; h < MH; ++h) {
@@ -334,7 +338,7 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
             // Gauss-Newton iteration `it`: all CTAs' partials summed behind a
             // grid barrier (cooperative launch), then every CTA solves
             __syncthreads();
-            if (!gn_ff_finish_iteration(gn, r, it, status)) goto teardown;
+            if (!gn_ff_finish_iteration(gn, r, it, rank, gsize, status)) goto teardown;
         }
     }
     goto teardown;
@@ -351,6 +355,55 @@ teardown:
     if (tid < 32) {
         tc_fence_after();
         tmem_dealloc(tmem, ncols);
+    }
+    if (tid == 0) {
+        // a batched launch runs further problems whose layouts reuse this memory
+        mbar_inval(bar_w);
+        mbar_inval(bar_mma);
+    }
+    // ... and whose weight copy (async proxy) may land where this problem's
+    // threads stored activations: order those stores first
+    fence_proxy_async();
+    __syncthreads();
+}
+
+template <int CW>
+__global__ void __launch_bounds__(kThreads, 1)
+k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
+         const double *zj, float *u, float *dudz, const __grid_constant__ GnArgs gn, int gn_on,
+         int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    jac_body<CW>(fd, X, n, ld, zj, u, dudz, gn, gn_on, (int)blockIdx.x, (int)gridDim.x, true,
+                 smem_dyn, status);
+}
+
+// One Gauss-Newton problem of a batch (out of line, so that each latent-size
+// class keeps its own register allocation).
+template <int CW>
+__device__ __noinline__ void jac_batch_problem(const GnBatchProblem &pb, const GnBatchEntry &en,
+                                               uint8_t *smem_dyn, int *status) {
+    jac_body<CW>(*pb.fd, pb.X, pb.n, pb.ld, nullptr, nullptr, nullptr, pb.gn, 1, en.rank, en.size,
+                 false, smem_dyn, status);
+}
+
+// Batched Gauss-Newton: CTA c runs the problems of its entries
+// cta_entry[c] .. cta_entry[c + 1] - 1 in order; an entry names a problem, the
+// CTA's rank in that problem's CTA group and the group size.  A CTA that
+// shares a problem with others (group size > 1) has no other entry, so the
+// group barriers of different problems never wait on each other.
+__global__ void __launch_bounds__(kThreads, 1)
+k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__restrict__ entries,
+            const int *__restrict__ cta_entry, int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    const int e0 = cta_entry[blockIdx.x], e1 = cta_entry[blockIdx.x + 1];
+    for (int e = e0; e < e1; ++e) {
+        const GnBatchEntry en = entries[e];
+        const GnBatchProblem &pb = probs[en.problem];
+        const int cw = jac_cw(pb.fd->r);
+        if (cw == 8) jac_batch_problem<8>(pb, en, smem_dyn, status);
+        else if (cw == 16) jac_batch_problem<16>(pb, en, smem_dyn, status);
+        else jac_batch_problem<32>(pb, en, smem_dyn, status);
+        __syncthreads();
     }
 }
 
@@ -414,6 +467,27 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
     static bool done = false;
     set_max_dynamic_smem(k_jac_tc<32>, done);
     return cudaLaunchKernelEx(&cfg, k_jac_tc<32>, fd, X, n, ld, z, u, dudz, g, gn_on, status);
+}
+
+int jac_points_per_cta_tile(int r) { return jac_points(r); }
+
+cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
+                             const int *cta_entry, int nctas, size_t smem, int *status,
+                             cudaStream_t s) {
+    if (nctas <= 0) return cudaSuccess;
+    static bool done = false;
+    set_max_dynamic_smem(k_jac_batch, done);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_jac_batch, probs, entries, cta_entry, status);
 }
 
 }  // namespace nsf

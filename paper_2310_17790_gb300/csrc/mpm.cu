@@ -158,40 +158,50 @@ __device__ __forceinline__ float4 node_contribution(const P2gParticle &q, const 
 }
 
 // ---------------------------------------------------------------- P2G ----
+// Particle p's 27 node contributions, added straight into the grid; returns
+// its particle block, or -1 when its stencil leaves the grid (status set).
+template <class Args>
+__device__ __forceinline__ int p2g_particle(const GridWs &g, const GridParams &gp, const Args &a,
+                                            float stress_k, int p, int *status) {
+    P2gParticle q;
+    load_particle(a, stress_k, p, q);
+    const int key = block_key(g, q.x, gp.inv_dx, status);
+    if (key >= 0) {
+        Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
+                  bspline_axis(q.x[2], gp.inv_dx)};
+#pragma unroll
+        for (int ia = 0; ia < 3; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+                for (int ic = 0; ic < 3; ++ic)
+                    atomicAdd(&g.acc[node_addr(g, s.ax.base + ia, s.ay.base + ib, s.az.base + ic)],
+                              node_contribution(q, s, a.mass, gp.dx, ia, ib, ic));
+    }
+    return key;
+}
+
+// One stamp per distinct (scene tag, block) in the warp; the first stamp of
+// this step appends the block to the scene's active list.  Every lane of the
+// warp calls; key < 0 means no particle.
+__device__ __forceinline__ void stamp_block(const GridWs &g, int tag, int key, int epoch) {
+    const unsigned peers = __match_any_sync(0xffffffffu, key < 0 ? -1 : (tag << 16) | key);
+    if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+        if (atomicExch(&g.pstamp[key], epoch) != epoch)
+            g.plist[atomicAdd(&g.ctl->n_p_atomic, 1)] = key;
+    }
+}
+
 template <class Args>
 __device__ void phase_p2g(const GridWs &g, const GridParams &gp, const Args &a,
                                  float stress_k, int epoch, int *status) {
     const int n = a.n;
     const int stride = gridDim.x * blockDim.x;
-    // the loop bound is uniform across each warp (match_any below)
+    // the loop bound is uniform across each warp (match_any in stamp_block)
     for (int base = spread_index() & ~31; base < n; base += stride) {
         const int p = base + (threadIdx.x & 31);
-        int key = -2;                                   // -2: no particle
-        if (p < n) {
-            P2gParticle q;
-            load_particle(a, stress_k, p, q);
-            key = block_key(g, q.x, gp.inv_dx, status);
-            if (key >= 0) {
-                Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
-                          bspline_axis(q.x[2], gp.inv_dx)};
-#pragma unroll
-                for (int ia = 0; ia < 3; ++ia)
-#pragma unroll
-                    for (int ib = 0; ib < 3; ++ib)
-#pragma unroll
-                        for (int ic = 0; ic < 3; ++ic)
-                            atomicAdd(&g.acc[node_addr(g, s.ax.base + ia, s.ay.base + ib,
-                                                       s.az.base + ic)],
-                                      node_contribution(q, s, a.mass, gp.dx, ia, ib, ic));
-            }
-        }
-        // one stamp per distinct block in the warp; the first stamp of this
-        // step appends the block to the active list
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
-            if (atomicExch(&g.pstamp[key], epoch) != epoch)
-                g.plist[atomicAdd(&g.ctl->n_p_atomic, 1)] = key;
-        }
+        const int key = p < n ? p2g_particle(g, gp, a, stress_k, p, status) : -2;
+        stamp_block(g, 0, key, epoch);
     }
 }
 
@@ -211,14 +221,12 @@ __device__ void phase_activate(const GridWs &g, int np, int epoch) {
 }
 
 // --------------------------------------------------------------- grid ----
-__device__ void phase_grid(const GridWs &g, const GridParams &gp, float dt, double t,
-                           float *tap_mp, float *tap_v) {
-    const int ngb = __ldcg(&g.ctl->n_g_atomic);
-    const int per = blockDim.x >> 6;                 // grid blocks per CTA pass
-    const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+// Node l (0 .. 63) of active grid block number idx of the step.
+__device__ __forceinline__ void grid_node(const GridWs &g, const GridParams &gp, float dt,
+                                          double blade_z, int idx, int l, float *tap_mp,
+                                          float *tap_v) {
     const int lx = l >> 4, ly = (l >> 2) & 3, lz = l & 3;
-    const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
-    for (int idx = sub * gridDim.x + blockIdx.x; idx < ngb; idx += gridDim.x * per) {
+    {
         const int gb = __ldcg(&g.glist[idx]);
         const int bz = gb % g.nb2, tt = gb / g.nb2, by = tt % g.nb1, bx = tt / g.nb1;
         const int i = bx * 4 + lx, j = by * 4 + ly, k = bz * 4 + lz;
@@ -254,13 +262,24 @@ __device__ void phase_grid(const GridWs &g, const GridParams &gp, float dt, doub
     }
 }
 
+__device__ void phase_grid(const GridWs &g, const GridParams &gp, float dt, double t,
+                           float *tap_mp, float *tap_v) {
+    const int ngb = __ldcg(&g.ctl->n_g_atomic);
+    const int per = blockDim.x >> 6;                 // grid blocks per CTA pass
+    const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+    const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
+    for (int idx = sub * gridDim.x + blockIdx.x; idx < ngb; idx += gridDim.x * per)
+        grid_node(g, gp, dt, blade_z, idx, l, tap_mp, tap_v);
+}
+
 // ---------------------------------------------------------------- G2P ----
 // Latent G2P on the sample particles (§5.2): only x^{n+1} is needed.  Writes
 // the displacement target d = u_n + dt v_p (x^{n+1} - X for a residual g).
-__device__ void phase_g2p_latent(const GridWs &g, const GridParams &gp, const float *X,
-                                 const float *u, int ld, int n_S, float dt, float *d_next,
-                                 int *status) {
-    for (int p = spread_index(); p < n_S; p += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void g2p_latent_particle(const GridWs &g, const GridParams &gp,
+                                                    const float *X, const float *u, int ld,
+                                                    int n_S, float dt, float *d_next, int p,
+                                                    int *status) {
+    {
         const float u0 = u[p], u1 = u[ld + p], u2 = u[2 * ld + p];
         float x0 = u0, x1 = u1, x2 = u2;
         if (X) { x0 += X[p]; x1 += X[ld + p]; x2 += X[2 * ld + p]; }
@@ -289,6 +308,13 @@ __device__ void phase_g2p_latent(const GridWs &g, const GridParams &gp, const fl
         d_next[n_S + p] = fmaf(dt, vy, u1);
         d_next[2 * n_S + p] = fmaf(dt, vz, u2);
     }
+}
+
+__device__ void phase_g2p_latent(const GridWs &g, const GridParams &gp, const float *X,
+                                 const float *u, int ld, int n_S, float dt, float *d_next,
+                                 int *status) {
+    for (int p = spread_index(); p < n_S; p += gridDim.x * blockDim.x)
+        g2p_latent_particle(g, gp, X, u, ld, n_S, dt, d_next, p, status);
 }
 
 // Full-order G2P (§3.3): v, x, C = (4/dx^2) sum w v_i (x_i - x_p)^T and the
@@ -431,6 +457,145 @@ k_stress(const float *__restrict__ F, float *tau6, int n, int model, float mu, f
     for (int c = 0; c < 6; ++c) tau6[(size_t)c * n + p] = (float)t6[c];
 }
 
+// ------------------------------------------------------------- batches ---
+// Largest s with off[s] <= q (off ascending, off[0] = 0 <= q < off[ns]).
+__device__ __forceinline__ int find_scene(const int *off, int ns, int q) {
+    int lo = 0, hi = ns;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= q) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive prefix sums off[0 .. ns] of v(s), s < ns, over the CTA (ns <=
+// kMaxBatchScenes); every thread calls.
+template <class F>
+__device__ void block_offsets(int ns, int *off, F v) {
+    __shared__ int wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (ns + kThreads - 1) / kThreads;
+    const int s0 = threadIdx.x * per;
+    int loc[kMaxBatchScenes / kThreads];
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < kMaxBatchScenes / kThreads; ++k) {
+        const int sc = s0 + k;
+        loc[k] = (k < per && sc < ns) ? v(sc) : 0;
+        tot += loc[k];
+    }
+    int x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int run = x - tot, all = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+        if (w < warp) run += wsum[w];
+        all += wsum[w];
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxBatchScenes / kThreads; ++k) {
+        const int sc = s0 + k;
+        if (k < per && sc < ns) off[sc] = run;
+        run += loc[k];
+    }
+    if (threadIdx.x == 0) off[ns] = all;
+    __syncthreads();
+}
+
+__device__ __forceinline__ P2gLatentArgs latent_args(const BatchSceneDev &sc, int parity) {
+    P2gLatentArgs a;
+    a.X = sc.residual_g ? sc.X : nullptr;
+    a.u = sc.u[parity];
+    a.u_prev = sc.u[parity ^ 1];
+    a.tau6 = sc.tau6;
+    a.C9 = sc.C9;
+    a.n = sc.n_N;
+    a.mass = sc.mass;
+    a.vol0 = sc.vol0;
+    a.inv_dt = sc.inv_dt;
+    a.dt = sc.dt;
+    return a;
+}
+
+// The MPM part of a batched latent step: every phase runs over all scenes at
+// once (a flat index over the scenes' particles, active particle blocks,
+// active grid blocks and sample particles), with one grid barrier between
+// phases for the whole batch.
+__global__ void __launch_bounds__(kThreads)
+k_mpm_batch(MpmBatchArgs b, int *status) {
+    __shared__ int off[kMaxBatchScenes + 1];
+    const int ns = b.nscenes;
+    const int stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // P2G
+    const int total_N = __ldg(&b.n_off[ns]);
+    for (int base = spread_index() & ~31; base < total_N; base += stride) {
+        const int q = base + lane;
+        int key = -2, sidx = 0;
+        if (q < total_N) sidx = find_scene(b.n_off, ns, q);
+        const BatchSceneDev &sc = b.scenes[sidx];
+        const int epoch = __ldcg(&sc.g.ctl->epoch) + 1;
+        if (q < total_N) {
+            const float stress_k = -sc.dt * sc.vol0 * 4.f * sc.gp.inv_dx * sc.gp.inv_dx;
+            key = p2g_particle(sc.g, sc.gp, latent_args(sc, b.parity), stress_k,
+                               q - __ldg(&b.n_off[sidx]), status);
+        }
+        stamp_block(sc.g, sidx, key, epoch);
+    }
+    if (!grid_barrier(b.bar, status)) return;
+    // block activation
+    block_offsets(ns, off, [&](int sc) { return 8 * __ldcg(&b.scenes[sc].g.ctl->n_p_atomic); });
+    for (int q = spread_index(); q < off[ns]; q += stride) {
+        const int sidx = find_scene(off, ns, q);
+        const GridWs &g = b.scenes[sidx].g;
+        const int epoch = __ldcg(&g.ctl->epoch) + 1;
+        const int k = q - off[sidx];
+        const int key = __ldcg(&g.plist[k >> 3]), d = k & 7;
+        const int bz = key % g.nb2, t = key / g.nb2, by = t % g.nb1, bx = t / g.nb1;
+        const int cx = bx + (d >> 2), cy = by + ((d >> 1) & 1), cz = bz + (d & 1);
+        if (cx >= g.nb0 || cy >= g.nb1 || cz >= g.nb2) continue;
+        const int gb = (cx * g.nb1 + cy) * g.nb2 + cz;
+        if (atomicExch(&g.gstamp[gb], epoch) != epoch) g.glist[atomicAdd(&g.ctl->n_g_atomic, 1)] = gb;
+    }
+    if (!grid_barrier(b.bar, status)) return;
+    if (blockIdx.x == 0)                         // every CTA has read them
+        for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) b.scenes[sc].g.ctl->n_p_atomic = 0;
+    // grid update
+    block_offsets(ns, off, [&](int sc) { return __ldcg(&b.scenes[sc].g.ctl->n_g_atomic); });
+    {
+        const int per = blockDim.x >> 6;
+        const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+        for (int u = sub * gridDim.x + blockIdx.x; u < off[ns]; u += gridDim.x * per) {
+            const int sidx = find_scene(off, ns, u);
+            const BatchSceneDev &sc = b.scenes[sidx];
+            const double t = b.t0 + (double)b.step * (double)sc.dt;
+            const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
+            grid_node(sc.g, sc.gp, sc.dt, blade_z, u - off[sidx], l, nullptr, nullptr);
+        }
+    }
+    if (!grid_barrier(b.bar, status)) return;
+    // G2P on the sample particles
+    const int total_S = __ldg(&b.s_off[ns]);
+    for (int q = spread_index(); q < total_S; q += stride) {
+        const int sidx = find_scene(b.s_off, ns, q);
+        const BatchSceneDev &sc = b.scenes[sidx];
+        g2p_latent_particle(sc.g, sc.gp, sc.residual_g ? sc.X : nullptr, sc.u[b.parity], sc.n_N,
+                            sc.n_S, sc.dt, sc.dnext, q - __ldg(&b.s_off[sidx]), status);
+    }
+    if (blockIdx.x == 0)
+        for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) {
+            Ctl *c = b.scenes[sc].g.ctl;
+            c->n_g_atomic = 0;                   // read by the grid phase only
+            c->epoch = c->epoch + 1;
+        }
+}
+
 template <class K>
 int coop_grid(K kernel) {
     int dev = 0, sms = 0, per = 0;
@@ -471,6 +636,12 @@ cudaError_t launch_mpm_latent(const GridWs &g, const GridParams &gp, const P2gLa
     static const int grid = coop_grid(k_mpm_latent);
     return launch_coop(k_mpm_latent, grid, s, g, gp, a, n_S, t, d_next, tap_mp,
                        tap_v, status);
+}
+
+cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int *status, cudaStream_t s) {
+    if (b.nscenes < 1 || b.nscenes > kMaxBatchScenes) return cudaErrorInvalidValue;
+    static const int grid = coop_grid(k_mpm_batch);
+    return launch_coop(k_mpm_batch, grid, s, b, status);
 }
 
 cudaError_t launch_mpm_full(const GridWs &g, const GridParams &gp, const P2gFullArgs &pa,

@@ -46,7 +46,8 @@ def test_library_exports_every_declared_symbol(native):
 
 def test_ctypes_structs_match_c_layout(native, tmp_path):
     structs = ["nsf_fields_desc", "nsf_grid_desc", "nsf_latent_scene", "nsf_gn_opts",
-               "nsf_latent_taps", "nsf_material", "nsf_particles", "nsf_full_taps"]
+               "nsf_latent_taps", "nsf_material", "nsf_particles", "nsf_full_taps",
+               "nsf_latent_batch_item", "nsf_batch_events"]
     prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "nsf.h"', "int main(void){"]
     for s in structs:
         prog.append(f'printf("{s} %zu\\n", sizeof({s}));')
@@ -100,3 +101,20 @@ def test_host_side_validation_without_gpu(native):
     parts = native.nsf_particles()
     assert lib.nsf_full_step(C.byref(g), C.byref(mat), C.byref(parts), 1e-4, 0.0, 1, None, 0,
                              None, None, None) == native.NSF_ERR_INVALID_ARG
+
+
+def test_batch_validation_without_gpu(native):
+    lib = native.lib
+    size = C.c_size_t()
+    items = (native.nsf_latent_batch_item * 2)()
+    # no fields: rejected
+    assert lib.nsf_latent_batch_workspace_size(2, items, C.byref(size)) == native.NSF_ERR_INVALID_ARG
+    assert lib.nsf_latent_batch_workspace_size(0, items, C.byref(size)) == native.NSF_ERR_INVALID_ARG
+    assert lib.nsf_latent_batch_workspace_size(native.NSF_MAX_BATCH + 1, items,
+                                               C.byref(size)) == native.NSF_ERR_INVALID_ARG
+    opts = native.nsf_gn_opts()
+    opts.iters, opts.damping = 5, 1e-6
+    h = C.c_void_p()
+    assert lib.nsf_latent_batch_create(2, items, C.byref(opts), None, 0,
+                                       C.byref(h)) == native.NSF_ERR_INVALID_ARG
+    assert lib.nsf_latent_step_batched(None, 0.0, 1, 0, None, None, None) == native.NSF_ERR_INVALID_ARG

@@ -1,0 +1,164 @@
+"""GPU parity of the batched latent step (nsf_latent_step_batched).
+
+A batch steps every scene as nsf_latent_step steps it alone (paper §5.1-§5.3):
+the field values of a point do not depend on the tile or CTA that computes
+them, and the only arithmetic differences are the order of the P2G float
+atomics and the split of the Gauss-Newton sums over CTAs.  The single-scene
+step is checked stage by stage against the FP64 oracle in
+test_gpu_latent.py; here each scene of a mixed batch (r, width, depth,
+particle counts, grids and dt all differing) is checked against it:
+
+* the first call's z_prev is the input z exactly;
+* the batched z minimises the single-scene step's Gauss-Newton objective
+  (Eq. 9, on the single step's own target x^{n+1} of the sample particles) as
+  well as the single-scene z does: within 2 % of the objective decrease plus
+  1e-3 of the starting objective (the BF16 resolution of the fields);
+* |z_batch - z_single| <= 5e-2 max(1, |z|_inf).  With BF16 fields two
+  single-scene runs of the same step already differ by up to ~1e-2 in z: the
+  atomics' rounding differences (~1e-10 in x^{n+1}) are amplified along
+  weakly determined latent directions, and the fitted positions differ by
+  ~1e-3 dx, the size of one step's displacement.
+
+also with the scenes in another order, over a second call that reuses the
+cached g(X, z_prev), and for two steps in one call.
+"""
+
+import numpy as np
+import pytest
+
+from _support import grid_desc, soa
+from scenes.synthetic import tiny_latent
+
+pytestmark = pytest.mark.gpu
+
+Z_TOL = 5e-2
+OBJ_TOL = 2e-2
+
+# (seed, n_N, n_S, r, width, depth, n_grid, dt)
+MIX = [
+    (41, 600, 600, 6, 64, 4, 16, 1e-4),
+    (42, 3000, 2000, 16, 64, 3, 32, 5e-5),     # many Gauss-Newton tiles: a CTA group
+    (43, 150, 1, 12, 128, 5, 16, 1e-4),
+    (44, 1200, 60, 6, 128, 2, 32, 2e-4),
+    (45, 97, 97, 3, 64, 2, 16, 1e-4),
+    (46, 2500, 125, 12, 128, 4, 32, 5e-5),
+]
+
+
+@pytest.fixture(scope="module")
+def nsf():
+    import paper_2310_17790_gb300 as m
+    return m
+
+
+def _scenes():
+    out = []
+    for seed, n_N, n_S, r, w, d, ng, dt in MIX:
+        sc = tiny_latent(seed, n_N=n_N, n_S=n_S, r=r, width=w, depth=d, n_grid=ng,
+                         precision="bf16", dt=dt)
+        rng = np.random.Generator(np.random.PCG64(seed + 7))
+        # a velocity large enough that one step's displacement (~1e-2 dx) is
+        # well above the BF16 resolution of the fields
+        sc.z_prev = sc.z0 - 5e-2 * rng.normal(size=sc.z0.size)
+        out.append(sc)
+    return out
+
+
+def _single(nsf, sc, calls):
+    """Per call of one step each (the second and later reuse the cached
+    g(X, z_prev)): z, z_prev and the objective of that step's Gauss-Newton
+    problem as a function of z."""
+    import torch
+    F = nsf.Fields.from_spec(sc.fields)
+    X = soa(sc.X)
+    st = nsf.LatentStepper(F, X, sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid))
+    z = torch.tensor(sc.z0, dtype=torch.float64, device="cuda")
+    zp = torch.tensor(sc.z_prev, dtype=torch.float64, device="cuda")
+    XS = X[:, :sc.n_S].contiguous()
+    res = []
+    for k in range(calls):
+        tgt = torch.zeros(3, sc.n_S, device="cuda")
+        taps = nsf._native.nsf_latent_taps()
+        taps.u_next_S = tgt.data_ptr()
+        z_in = z.cpu().numpy().copy()
+        st.step(z, zp, sc.dt, t0=k * sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping,
+                reuse_prev=k > 0, taps=taps)
+        torch.cuda.synchronize()
+        assert st.read_status() == 0
+        target = tgt.cpu().numpy().astype(np.float64)      # x^{n+1} - X on S
+
+        def objective(zz, F=F, XS=XS, target=target):
+            u = torch.empty(3, sc.n_S, device="cuda")
+            nsf.nsf_eval_fields(F, XS, torch.tensor(zz, device="cuda"), x=u)
+            torch.cuda.synchronize()
+            d = u.cpu().numpy().astype(np.float64) - XS.cpu().numpy() - target
+            return float((d ** 2).sum())
+        res.append((z.cpu().numpy().copy(), zp.cpu().numpy().copy(), objective, z_in))
+    return res
+
+
+def _batched(nsf, scenes, calls, order=None, nsteps=1):
+    import torch
+    order = list(range(len(scenes))) if order is None else order
+    keep, entries, zs = [], [], []
+    for i in order:
+        sc = scenes[i]
+        F = nsf.Fields.from_spec(sc.fields)
+        X = soa(sc.X)
+        z = torch.tensor(sc.z0, dtype=torch.float64, device="cuda")
+        zp = torch.tensor(sc.z_prev, dtype=torch.float64, device="cuda")
+        keep += [F, X]
+        zs.append((i, z, zp))
+        entries.append((F, X, sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid), sc.dt, z, zp))
+    b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping)
+    res = []
+    for k in range(calls):
+        b.step(t0=0.0, nsteps=nsteps, reuse_prev=k > 0)
+        torch.cuda.synchronize()
+        assert b.read_status() == 0, nsf.status_string(b.read_status())
+        snap = {}
+        for i, z, zp in zs:
+            snap[i] = (z.cpu().numpy().copy(), zp.cpu().numpy().copy())
+        res.append(snap)
+    b.close()
+    return res
+
+
+def _close(a, b):
+    return np.abs(a - b).max() <= Z_TOL * max(1.0, np.abs(b).max())
+
+
+def test_batch_matches_single_scene_steps(nsf):
+    scenes = _scenes()
+    single = [_single(nsf, sc, 2) for sc in scenes]
+    batch = _batched(nsf, scenes, 2)
+    for call in range(2):
+        for i, sc in enumerate(scenes):
+            zb, zpb = batch[call][i]
+            zs, zps, f, z_in = single[i][call]
+            f_b, f_s, f_0 = f(zb), f(zs), f(z_in)
+            print(f"call {call} scene {i}: |dz| {np.abs(zb - zs).max():.3e} objective "
+                  f"start {f_0:.4e} single {f_s:.4e} batch {f_b:.4e}")
+            assert f_b <= f_s + OBJ_TOL * max(f_0 - f_s, 0.0) + 1e-3 * f_0, (call, i)
+            assert _close(zb, zs), (call, i, zb, zs)
+            assert _close(zpb, zps), (call, i)
+    # the first call's z_prev is the input z exactly
+    for i, sc in enumerate(scenes):
+        np.testing.assert_array_equal(batch[0][i][1], sc.z0)
+
+
+def test_batch_result_does_not_depend_on_scene_order(nsf):
+    scenes = _scenes()
+    a = _batched(nsf, scenes, 1)
+    b = _batched(nsf, scenes, 1, order=[5, 2, 0, 4, 1, 3])
+    for i in range(len(scenes)):
+        assert _close(a[0][i][0], b[0][i][0]), i
+
+
+def test_batch_two_steps_in_one_call_match_two_calls(nsf):
+    scenes = _scenes()[:3]
+    two_calls = _batched(nsf, scenes, 2)
+    one_call = _batched(nsf, scenes, 1, nsteps=2)
+    for i in range(len(scenes)):
+        assert _close(one_call[0][i][0], two_calls[1][i][0]), i
+        assert _close(one_call[0][i][1], two_calls[1][i][1]), i

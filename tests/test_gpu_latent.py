@@ -210,6 +210,20 @@ def test_latent_step_config3_scale_bf16(nsf, width, depth, r):
     _check_stages(sc, sc.z0, zp, out, field_tol=2e-3, z_tol=0.5, z_exact=False)
 
 
+def test_latent_step_bf16_more_sample_tiles_than_ctas(nsf):
+    # 2,500 sample particles are 313 Gauss-Newton tiles of 8 points (the last
+    # one partial) over at most one CTA per SM: every CTA revisits several
+    # tiles in every iteration; the float64 normal equations of each iterate
+    # must still be those of all sample particles exactly
+    from scenes.synthetic import latent_scene
+    base = latent_config3(precision="bf16", width=64, depth=3)
+    sc = latent_scene(2405, 3000, 2500, 6, 64, 3, "bf16", base.grid, 5e-5,
+                      X=base.X[:3000], E=2e5, vol_total=base.vol0 * 200000, n_total=200000)
+    zp = _perturbed_prev(sc, 5, eps=1e-3)
+    out, _ = _run_step(nsf, sc, sc.z0, zp)
+    _check_stages(sc, sc.z0, zp, out, field_tol=2e-3, z_tol=0.5, z_exact=False)
+
+
 def test_multi_step_matches_repeated_single_steps(nsf):
     # nsteps = 3 in one call equals three calls of one step (cache reuse of
     # g(X, z_n) as the next step's g(X, z_{n-1}))
