@@ -262,10 +262,12 @@ def run_gpu(args, rank, world, local):
     roof["traffic"] = traffic
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     throughput = run_throughput(args, nsf, fs, dev, peaks, peak_src) if args.precision == "bf16" else None
-    clocks.__exit__(None, None, None)
 
     # e2e: through the public API with host buffers, copies inside the timed region
     e2e = run_e2e(args, nsf, sc, F, gd, dev)
+
+    batched = run_batched(args, nsf, dev, flush, peaks, peak_src) if args.precision == "bf16" else None
+    clocks.__exit__(None, None, None)
 
     full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
     full_plastic = run_full(args, nsf, full_config2(model="von_mises", steps=args.steps), dev,
@@ -288,6 +290,7 @@ def run_gpu(args, rank, world, local):
         "roofline": roof,
         "mlp_throughput": throughput,
         "e2e": e2e,
+        "batched": batched,
         "full_order": full,
         "full_order_plastic": full_plastic,
         "gpu_launches": launches_per_step * K,
@@ -416,6 +419,119 @@ def run_full(args, nsf, fc, dev, flush):
     return {"steps_per_s": Kf / (ms / 1e3), "ms_per_step": ms / Kf, "steps": Kf,
             "workload": fc.name, "status": st.read_status(),
             "note": "blade time frozen at t=0 inside the replayed graph"}
+
+
+def run_batched(args, nsf, dev, flush, peaks, peak_src):
+    """256 independent latent scenes stepped together (nsf_latent_step_batched),
+    one CUDA-graph replay per batched step, L2 flushed between steps; stage
+    times from the library's stage events and each stage against its
+    roofline."""
+    import torch
+    from paper_2310_17790_gb300 import _native as N
+    from scenes.synthetic import batch_config4
+
+    scenes = batch_config4(steps=args.steps)
+    keep, entries = [], []
+    for sc in scenes:
+        F = nsf.Fields.from_spec(sc.fields)
+        X = torch.from_numpy(np.ascontiguousarray(sc.X.T)).to(dev)
+        z = torch.tensor(sc.z0, dtype=torch.float64, device=dev)
+        zp = z.clone()
+        gd = nsf.grid_desc(sc.grid.n, sc.grid.dx, sc.grid.gravity, sc.grid.wall_cells)
+        keep.append((F, X, z, zp))
+        entries.append((F, X, sc.n_S, sc.mass, sc.vol0, gd, sc.dt, z, zp))
+    b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping)
+    stream = torch.cuda.Stream(device=dev)
+    nst = N.NSF_LATENT_STAGES
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+    with torch.cuda.stream(stream):
+        for e in ev_b + ev_e:
+            e.record(stream)
+    torch.cuda.synchronize()
+    evs = N.nsf_batch_events()
+    for i in range(nst):
+        evs.ev_begin[i] = ev_b[i].cuda_event
+        evs.ev_end[i] = ev_e[i].cuda_event
+    with torch.cuda.stream(stream):
+        b.step(t0=0.0, nsteps=1, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.step(t0=0.0, nsteps=1, events=evs, stream=stream, reuse_prev=True)
+    torch.cuda.synchronize()
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert b.read_status() == 0, nsf.status_string(b.read_status())
+    K = max(1, min(args.steps, 100))
+    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    st_acc = np.zeros(nst)
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.fill_(float(k))
+            s_ev[k].record(stream)
+            graph.replay()
+            e_ev[k].record(stream)
+            if k < 20:
+                torch.cuda.synchronize()
+                st_acc += [ev_b[i].elapsed_time(ev_e[i]) for i in range(nst)]
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in zip(s_ev, e_ev)) / K
+    st_ms = st_acc / min(K, 20)
+    status = b.read_status()
+
+    n_N = np.array([sc.X.shape[0] for sc in scenes], np.float64)
+    n_S = np.array([sc.n_S for sc in scenes], np.float64)
+    fl_inf, fl_gn = 0.0, 0.0
+    for sc, nn, ns in zip(scenes, n_N, n_S):
+        fs = sc.fields
+        macs = [mlp_macs(fs.r, fs.width[i], fs.depth[i], od) for i, od in enumerate((3, 6, 9))]
+        fl_inf += 2.0 * nn * sum(macs)
+        fl_gn += 2.0 * sc.gn_iters * ns * (1 + fs.r) * macs[0]
+    # algorithmic bytes of the MPM launch: P2G reads X, u_n, u_{n-1}, tau, C
+    # (96 B per integration particle); every touched grid node is written by
+    # P2G (16 B), read and re-zeroed by the grid update (32 B) and its velocity
+    # written (16 B); G2P reads X, u_n and writes x^{n+1} (36 B per sample
+    # particle).  Touched nodes: the 3^3 stencils of the reference positions.
+    touched = 0
+    for sc in scenes:
+        base = np.floor(sc.X.astype(np.float64) / sc.grid.dx - 0.5).astype(np.int64)
+        ng = sc.grid.n[0]
+        off = np.array([(a, b, c) for a in range(3) for b in range(3) for c in range(3)])
+        nodes = (base[:, None, :] + off[None]).reshape(-1, 3)
+        touched += np.unique((nodes[:, 0] * ng + nodes[:, 1]) * ng + nodes[:, 2]).size
+    mpm_bytes = 96.0 * n_N.sum() + 64.0 * touched + 36.0 * n_S.sum()
+    names = N.NSF_STAGE_NAMES
+    stages = {names[i]: float(st_ms[i]) for i in range(nst)}
+    pk = peaks["bf16_tflops"]
+
+    def tf(flops, t_ms):
+        return flops / (t_ms / 1e3) / 1e12
+    roof = {
+        "inference": {"kernel": "k_fields_batch", "bound": "tensor", "unit": "TFLOP/s",
+                      "achieved": tf(fl_inf, st_ms[0]), "peak": pk,
+                      "frac": tf(fl_inf, st_ms[0]) / pk, "work": fl_inf},
+        "mpm": {"kernel": "k_mpm_batch", "bound": "hbm", "unit": "GB/s",
+                "achieved": mpm_bytes / (st_ms[1] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "frac": mpm_bytes / (st_ms[1] / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "work": mpm_bytes, "touched_nodes": int(touched),
+                "note": "96 B per integration particle + 64 B per touched node + 36 B per "
+                        "sample particle; P2G adds into the grid with float4 atomics"},
+        "gauss_newton": {"kernel": "k_jac_batch", "bound": "tensor", "unit": "TFLOP/s",
+                         "achieved": tf(fl_gn, st_ms[2]), "peak": pk,
+                         "frac": tf(fl_gn, st_ms[2]) / pk, "work": fl_gn},
+    }
+    b.close()
+    return {"workload": f"batch-{len(scenes)}scenes-{int(n_N.sum())}N-{int(n_S.sum())}S-bf16",
+            "scenes": len(scenes), "n_integration_total": int(n_N.sum()),
+            "n_sample_total": int(n_S.sum()), "steps": K, "ms_per_step": ms,
+            "batched_steps_per_s": 1e3 / ms, "scene_steps_per_s": len(scenes) * 1e3 / ms,
+            "stages_ms": stages, "roofline": roof, "status": status,
+            "launches_per_step": 2 + len({sc.fields.width[0] for sc in scenes}),
+            "peak_source": f"measured ({peak_src})",
+            "note": "one CUDA-graph replay of one batched step; L2 flushed between steps"}
 
 
 # ---------------------------------------------------------- CPU oracle ---

@@ -750,11 +750,12 @@ WidthPlan plan_width(int W, int n, const nsf_latent_batch_item *items, bool with
     return P;
 }
 
-// Gauss-Newton CTA schedule: scenes whose cost is at least two CTAs' share get
-// that many dedicated CTAs (a group that combines its sums behind the scene's
-// barrier); the others are packed whole onto the remaining CTAs, longest
-// first, each onto the least loaded CTA.
+// Gauss-Newton CTA schedule: a scene whose cost is above 1.15 CTA shares gets
+// ceil(cost / 1.15 shares) dedicated CTAs (a group that combines its sums
+// behind the scene's barrier); the others are packed whole onto the remaining
+// CTAs, longest first, each onto the least loaded CTA.
 struct GnPlan {
+    std::vector<int> cw;
     std::vector<GnBatchEntry> entries;
     std::vector<int> cta_entry;
     int nctas = 0;
@@ -774,21 +775,29 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
     double total = 0.0;
     for (int s = 0; s < n; ++s) {
         const nsf_fields_desc &d = items[s].fields->desc;
-        const int P = jac_points_per_cta_tile(d.r);
+        const int W = d.width[NSF_FIELD_G], D = d.depth[NSF_FIELD_G];
+        const int cw = jac_batch_cw(d.r, W, D);
+        G.cw.push_back(cw);
+        const int P = 8 * cw / jac_slots_host(d.r);
         tiles[s] = (items[s].scene.n_S + P - 1) / P;
-        const double wq = (double)d.width[NSF_FIELD_G] / 64.0;
+        // measured: a tile's pass through one layer costs about the same for
+        // any width up to 128 (products have M = 128 neuron rows; one neuron
+        // per thread), twice that above; per point it scales with the slots
         const int L = jac_slots_host(d.r);
-        cost[s] = (double)tiles[s] * d.depth[NSF_FIELD_G] * wq * wq * (L > 8 ? L : 8) / 8.0;
+        cost[s] = (double)items[s].scene.n_S * (D + 1) * L * (W > 128 ? 2.0 : 1.0);
         total += cost[s];
-        const size_t sm = jac_tc_smem_bytes(d.r, d.width[NSF_FIELD_G], d.depth[NSF_FIELD_G]);
+        const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw);
         G.smem = sm > G.smem ? sm : G.smem;
     }
     const int cap = sms < kGnMaxCtas ? sms : kGnMaxCtas;
     const double share = total / cap;
     std::vector<int> group(n, 0);
     int used = 0, nsmall = 0;
+    // a scene above 1.15 shares is split so that no CTA carries more than
+    // about 1.15 shares of the whole run
+    const double unit = 1.15 * share;
     for (int s = 0; s < n; ++s) {
-        int g = (int)(cost[s] / share);
+        int g = cost[s] > unit ? (int)std::ceil(cost[s] / unit) : 1;
         if (g > tiles[s]) g = tiles[s];
         if (g > cap) g = cap;
         if (g >= 2) {
@@ -987,6 +996,7 @@ nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
         pb.X = it.scene.d_X;
         pb.n = it.scene.n_S;
         pb.ld = it.scene.n_N;
+        pb.cw = G.cw[i];
         pb.gn = gn_args(base, L.gn);
         pb.gn.target = sd.dnext;
         pb.gn.target_ld = it.scene.n_S;

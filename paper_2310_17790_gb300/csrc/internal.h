@@ -188,12 +188,15 @@ struct GnBatchProblem {
     const FieldsDev *fd;       // device copy of the scene's fields
     const float *X;            // [3][ld] reference positions (first n are the samples)
     int n, ld;
+    int cw;                    // columns per warpgroup of its tiles (8, 16 or 32)
     GnArgs gn;                 // target, z, slots (sized for the group), barrier word
 };
 struct GnBatchEntry {
     int problem, rank, size;
 };
 int jac_points_per_cta_tile(int r);
+int jac_batch_cw(int r, int width, int depth);
+size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW);
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
                              const int *cta_entry, int nctas, size_t smem, int *status,
                              cudaStream_t s);

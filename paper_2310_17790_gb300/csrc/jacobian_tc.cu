@@ -61,9 +61,10 @@ struct JacLayout {
     int blob, b, w0v, w0t, b0, bias, xs, tg, o3, bars, tmem, total;
 };
 
-__host__ __device__ inline JacLayout jac_layout(int r, int W, int D) {
+// Layout for CW columns per warpgroup (N = 8 CW slots, N / L points per tile).
+__host__ __device__ inline JacLayout jac_layout(int r, int W, int D, int CW) {
     JacLayout L;
-    const int N = jac_cols(r), P = jac_points(r);
+    const int N = kWG * CW, P = N / jac_slots(r);
     int o = 0;
     L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + kMaxOut * W * 2, 1024);
     // activations (MN-major); at least 16 KB, the reach of the padded rows
@@ -120,7 +121,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
     const int lane = tid & 31;
     const int n0 = wg * CW;                  // first column of this warpgroup
     const int sbo_b = (N / 64) * 1024;
-    const JacLayout Lo = jac_layout(r, W, D);
+    const JacLayout Lo = jac_layout(r, W, D, CW);
     uint8_t *blob = base + Lo.blob;
     uint8_t *B = base + Lo.b;
     float4 *W0v = reinterpret_cast<float4 *>(base + Lo.w0v);
@@ -399,9 +400,8 @@ k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__rest
     for (int e = e0; e < e1; ++e) {
         const GnBatchEntry en = entries[e];
         const GnBatchProblem &pb = probs[en.problem];
-        const int cw = jac_cw(pb.fd->r);
-        if (cw == 8) jac_batch_problem<8>(pb, en, smem_dyn, status);
-        else if (cw == 16) jac_batch_problem<16>(pb, en, smem_dyn, status);
+        if (pb.cw == 8) jac_batch_problem<8>(pb, en, smem_dyn, status);
+        else if (pb.cw == 16) jac_batch_problem<16>(pb, en, smem_dyn, status);
         else jac_batch_problem<32>(pb, en, smem_dyn, status);
         __syncthreads();
     }
@@ -409,8 +409,18 @@ k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__rest
 
 }  // namespace
 
+// Shared memory of the Jacobian kernel with CW columns per warpgroup; 0 if
+// it (or its tensor memory) does not fit.
+size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW) {
+    if (CW < jac_slots(r)) return 0;
+    const JacLayout L = jac_layout(r, width, depth, CW);
+    if (jac_halves(width) * kWG * CW > 512) return 0;           // tensor memory columns
+    if ((size_t)L.total + sizeof(GnFF) + 64 > (size_t)kMaxSmem) return 0;
+    return (size_t)L.total;
+}
+
 size_t jac_tc_smem_bytes(int r, int width, int depth) {
-    const JacLayout L = jac_layout(r, width, depth);
+    const JacLayout L = jac_layout(r, width, depth, jac_cw(r));
     if (jac_halves(width) * jac_cols(r) > 512) return 0;        // tensor memory columns
     if ((size_t)L.total + sizeof(GnFF) + 64 > (size_t)kMaxSmem) return 0;
     return (size_t)L.total;
@@ -470,6 +480,16 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
 }
 
 int jac_points_per_cta_tile(int r) { return jac_points(r); }
+
+// Columns per warpgroup for a batched problem: the narrowest tile that holds a
+// point's value and tangent slots.  Wider tiles (more points per pass through
+// the layers) measured no faster per point, since the epilogue work grows
+// with the columns a thread handles, and they spill registers at 32 columns.
+int jac_batch_cw(int r, int width, int depth) {
+    for (int cw = 8; cw <= 32; cw <<= 1)
+        if (jac_tc_smem_bytes_cw(r, width, depth, cw)) return cw;
+    return 0;
+}
 
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
                              const int *cta_entry, int nctas, size_t smem, int *status,

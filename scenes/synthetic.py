@@ -194,3 +194,27 @@ def tiny_latent(seed, n_N=200, n_S=60, r=6, width=32, depth=2,
     grid = GridSpec(n=(n_grid,) * 3, dx=1.0 / n_grid)
     return latent_scene(seed, n_N, n_S, r, width, depth, precision, grid, dt,
                         lo=lo, hi=hi, name="tiny")
+
+
+def batch_config4(seed=2314, n_scenes=256, steps=500):
+    """Independent latent scenes for batched stepping: |N| log-uniform in
+    [1,000, 20,000]; r from {6, 12, 16}; grid 64^3 (dt 1e-4) or 128^3 (dt
+    5e-5); BF16 fields of width 64 or 128 and depth 4 or 5 (the same for g, h,
+    l of a scene); S = N when |N| <= 2,000, else the first 5 % of N.
+    Positions uniform in [0.3, 0.7]^3, each scene with its own seeded fields
+    and z0 ~ N(0, 0.1^2), z_prev = z0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_scenes):
+        n_N = int(round(np.exp(rng.uniform(np.log(1000.0), np.log(20000.0)))))
+        r = int(rng.choice([6, 12, 16]))
+        ng = int(rng.choice([64, 128]))
+        width = int(rng.choice([64, 128]))
+        depth = int(rng.choice([4, 5]))
+        n_S = n_N if n_N <= 2000 else max(1, n_N // 20)
+        grid = GridSpec(n=(ng, ng, ng), dx=1.0 / ng)
+        dt = 1e-4 if ng == 64 else 5e-5
+        out.append(latent_scene(seed * 1000 + i, n_N, n_S, r, width, depth, "bf16", grid, dt,
+                                lo=0.3, hi=0.7, steps=steps,
+                                name=f"batch{i}-{n_N}N-{n_S}S-r{r}-w{width}d{depth}-grid{ng}"))
+    return out
