@@ -430,7 +430,7 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
     from paper_2310_17790_gb300 import _native as N
     from scenes.synthetic import batch_config4
 
-    scenes = batch_config4(steps=args.steps)
+    scenes = batch_config4(n_scenes=args.batch_scenes, steps=args.steps)
     keep, entries = [], []
     for sc in scenes:
         F = nsf.Fields.from_spec(sc.fields)
@@ -534,6 +534,21 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
             "note": "one CUDA-graph replay of one batched step; L2 flushed between steps"}
 
 
+def run_part(args):
+    """One part of the benchmark alone (for profiling captures)."""
+    import torch
+    import paper_2310_17790_gb300 as nsf
+    from scenes.synthetic import latent_config3
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    peaks, peak_src = load_peaks()
+    if args.only == "mlp":
+        return run_throughput(args, nsf, latent_config3(precision="bf16", steps=1).fields, dev,
+                              peaks, peak_src)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    return run_batched(args, nsf, dev, flush, peaks, peak_src)
+
+
 # ---------------------------------------------------------- CPU oracle ---
 def run_oracle(args, budget_s):
     """The FP64 oracle's latent step on the same workload (bounded sample)."""
@@ -582,6 +597,9 @@ def main():
     ap.add_argument("--impl", default="nsf", choices=["nsf", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--only", default="all", choices=["all", "batched", "mlp"],
+                    help="batched / mlp: run that part alone (profiling runs) and print its JSON")
+    ap.add_argument("--batch-scenes", type=int, default=256)
     args = ap.parse_args()
     rank, world, local = dist_env()
 
@@ -602,6 +620,9 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.only != "all":
+        print(json.dumps(run_part(args)))
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
