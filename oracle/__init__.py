@@ -20,10 +20,11 @@ paper's order and notation, so that it can be read against the paper by eye:
                    (§5.3, Eq. 9).
 * ``metrics``      the relative deformation error delta (Eq. 10) and the
                    dimension-reduction ratio gamma.
+* ``subsets``      sample / integration particle construction (§5.4).
 
 Pinned by ``tests/test_oracle_*.py`` against closed forms, conservation laws,
 brute force and finite differences.  Multi-step trajectories of random fields
 have no external pin ("parity unpinned"); only their drift is reported.
 """
 
-from . import constitutive, fields, latent, metrics, mpm  # noqa: F401
+from . import constitutive, fields, latent, metrics, mpm, subsets  # noqa: F401
