@@ -284,6 +284,34 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
                               int *d_status, void *stream);
 
 /*
+ * Sample and integration particles (paper §5.4).  With the particle positions
+ * x_p = g(X_p, z) of all n_all particles P at the latent code z:
+ *   I = grid nodes in the quadratic B-spline stencil (base + {0,1,2}^3, base =
+ *       floor(x_p / dx - 0.5)) of some sample particle p in S,
+ *   N = every particle whose stencil contains a node of I.
+ * An MPM step on N then moves the sample particles exactly as a step on all of
+ * P does (§5.2).
+ * d_X [3][n_all]: reference positions of P.  d_sample [n_S]: indices of S in P
+ * (distinct, in [0, n_all); out-of-range ones are reported as
+ * NSF_ERR_INVALID_ARG in *d_status and skipped).  d_z [r].
+ * Outputs (device): d_index_out [n_all capacity]: N as indices into P, S first
+ * in the given order, then the other members in increasing index; *d_count_out
+ * = |N|; d_X_out (optional, [3][x_out_ld] with x_out_ld >= n_all) the
+ * reference positions of N in the same order -- a nsf_latent_scene with d_X =
+ * d_X_out, n_N = |N| and n_S has S as its prefix, as nsf_latent_step expects.
+ * A sample particle whose stencil leaves the grid sets NSF_ERR_OUT_OF_GRID.
+ * Enqueues on `stream` (workspace of nsf_integration_set_workspace_size bytes,
+ * any contents; the call clears what it needs).
+ */
+nsf_status nsf_integration_set_workspace_size(const nsf_grid_desc *grid, int n_all,
+                                              size_t *bytes);
+nsf_status nsf_integration_set(const nsf_fields *fields, const nsf_grid_desc *grid,
+                               const float *d_X, int n_all, const int *d_sample, int n_S,
+                               const double *d_z, int *d_index_out, int *d_count_out,
+                               float *d_X_out, int x_out_ld, void *d_workspace,
+                               size_t workspace_bytes, int *d_status, void *stream);
+
+/*
  * Batched latent stepping: many independent reduced-order scenes advanced
  * together, each step as a few launches for the whole batch (field inference
  * per field width, one MPM launch, one Gauss-Newton launch) instead of three

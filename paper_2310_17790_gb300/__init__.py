@@ -184,6 +184,40 @@ def nsf_project_static(fields, X_S, x_target, z, opts, status, z_iter=None, resi
           "nsf_project_static")
 
 
+def nsf_integration_set_workspace_size(grid, n_all):
+    b = C.c_size_t()
+    check(N.lib.nsf_integration_set_workspace_size(C.byref(grid), int(n_all), C.byref(b)),
+          "nsf_integration_set_workspace_size")
+    return b.value
+
+
+def nsf_integration_set(fields, grid, X, sample, z, index_out, count_out, workspace, status,
+                        X_out=None, stream=None):
+    check(N.lib.nsf_integration_set(fields.handle, C.byref(grid), _ptr(X), int(X.shape[1]),
+                                    _ptr(sample), int(sample.numel()), _ptr(z), _ptr(index_out),
+                                    _ptr(count_out), _ptr(X_out),
+                                    int(X_out.shape[1]) if X_out is not None else 0,
+                                    _ptr(workspace), workspace.numel(), _ptr(status),
+                                    _stream(stream)), "nsf_integration_set")
+
+
+def integration_set(fields, grid, X, sample, z, stream=None):
+    """The integration particles of sample set `sample` (int32 indices into the
+    particles X [3, n]) at latent code z: (indices [|N|] int32 with S first,
+    X_N [3, |N|], status).  Synchronises to read |N|."""
+    torch = _torch()
+    n = int(X.shape[1])
+    dev = X.device
+    ws = _zeros_u8(nsf_integration_set_workspace_size(grid, n), dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    Xo = torch.empty(3, n, dtype=torch.float32, device=dev)
+    nsf_integration_set(fields, grid, X, sample, z, idx, cnt, ws, st, X_out=Xo, stream=stream)
+    k = int(cnt.item())
+    return idx[:k].clone(), Xo[:, :k].contiguous(), int(st.item())
+
+
 def batch_items(entries):
     """entries: sequence of (Fields, X [3, n_N] tensor, n_S, mass, vol0, grid_desc, dt,
     z [r] float64 tensor, z_prev [r] float64 tensor) -> ctypes array of

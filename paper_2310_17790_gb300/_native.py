@@ -107,6 +107,9 @@ SIGNATURES = [
     ("nsf_project_workspace_size", _ST, [_P, _I, C.POINTER(_S)]),
     ("nsf_project", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _S, _P, _P]),
     ("nsf_project_static", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _P]),
+    ("nsf_integration_set_workspace_size", _ST, [C.POINTER(nsf_grid_desc), _I, C.POINTER(_S)]),
+    ("nsf_integration_set", _ST, [_P, C.POINTER(nsf_grid_desc), _P, _I, _P, _I, _P, _P, _P, _P,
+                                  _I, _P, _S, _P, _P]),
     ("nsf_latent_batch_workspace_size", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(_S)]),
     ("nsf_latent_batch_create", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(nsf_gn_opts),
                                       _P, _S, C.POINTER(_P)]),

@@ -565,6 +565,74 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
     return NSF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+struct SubsetLayout {
+    size_t u, bitmap, in_S, bcount, boff, total;
+    size_t bitmap_bytes;
+};
+
+SubsetLayout subset_layout(const nsf_grid_desc *g, int n) {
+    Carver c;
+    SubsetLayout L;
+    const size_t nodes = (size_t)g->n[0] * g->n[1] * g->n[2];
+    const size_t nb = ((size_t)n + 255) / 256;
+    L.u = c.take(3 * (size_t)n * 4);
+    L.bitmap_bytes = (nodes + 31) / 32 * 4;
+    L.bitmap = c.take(L.bitmap_bytes);
+    L.in_S = c.take((size_t)n);
+    L.bcount = c.take(nb * 4);
+    L.boff = c.take(nb * 4);
+    L.total = c.off;
+    return L;
+}
+}  // namespace
+
+extern "C" {
+
+nsf_status nsf_integration_set_workspace_size(const nsf_grid_desc *grid, int n_all,
+                                              size_t *bytes) {
+    if (!valid_grid(grid) || n_all < 1 || !bytes) return NSF_ERR_INVALID_ARG;
+    *bytes = subset_layout(grid, n_all).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_integration_set(const nsf_fields *f, const nsf_grid_desc *grid, const float *d_X,
+                               int n_all, const int *d_sample, int n_S, const double *d_z,
+                               int *d_index_out, int *d_count_out, float *d_X_out, int x_out_ld,
+                               void *d_ws, size_t ws_bytes, int *d_status, void *stream) {
+    if (!f || !valid_grid(grid) || !d_X || n_all < 1 || n_S < 0 || n_S > n_all ||
+        (n_S > 0 && !d_sample) || !d_z || !d_index_out || !d_count_out ||
+        (d_X_out && x_out_ld < n_all))
+        return NSF_ERR_INVALID_ARG;
+    const SubsetLayout L = subset_layout(grid, n_all);
+    if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(d_ws);
+    float *u = reinterpret_cast<float *>(base + L.u);
+    NSF_CUDA_TRY(cudaMemsetAsync(base + L.bitmap, 0, L.bitmap_bytes, s));
+    NSF_CUDA_TRY(cudaMemsetAsync(base + L.in_S, 0, (size_t)n_all, s));
+    FieldJob job{NSF_FIELD_G, d_z, u};
+    NSF_CUDA_TRY(run_fields(f->dev, d_X, n_all, n_all, 1, &job, d_status, s));
+    SubsetArgs a;
+    a.X = d_X;
+    a.u = u;
+    a.residual = f->dev.residual_g;
+    a.n = n_all;
+    a.sample = d_sample;
+    a.n_S = n_S;
+    for (int d = 0; d < 3; ++d) a.dims[d] = grid->n[d];
+    a.inv_dx = 1.f / grid->dx;
+    a.bitmap = reinterpret_cast<unsigned *>(base + L.bitmap);
+    a.in_S = reinterpret_cast<unsigned char *>(base + L.in_S);
+    a.block_count = reinterpret_cast<int *>(base + L.bcount);
+    a.block_off = reinterpret_cast<int *>(base + L.boff);
+    a.index_out = d_index_out;
+    NSF_CUDA_TRY(launch_subset(a, d_count_out, d_X_out, x_out_ld, d_status, s));
+    return NSF_OK;
+}
+
 nsf_status nsf_full_workspace_size(const nsf_grid_desc *g, int n, size_t *bytes) {
     if (!valid_grid(g) || n < 1 || !bytes) return NSF_ERR_INVALID_ARG;
     *bytes = full_layout(g, n).total;

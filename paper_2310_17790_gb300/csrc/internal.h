@@ -139,6 +139,25 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
                                const double *z, float *u, float *dudz,
                                const GnArgs *gn, int *status, cudaStream_t s);
 
+// ------------------------------------------------- integration particles ---
+// Construction of N from S (subset.cu, paper §5.4).
+struct SubsetArgs {
+    const float *X;            // [3][n] reference positions of all particles
+    const float *u;            // [3][n] g(X, z) (displacement for a residual g)
+    int residual;              // 1: x = X + u
+    int n;                     // |P|
+    const int *sample;         // [n_S] indices of S in P
+    int n_S;
+    int dims[3];
+    float inv_dx;
+    unsigned *bitmap;          // ceil(nodes / 32) words, zero on entry
+    unsigned char *in_S;       // [n], zero on entry
+    int *block_count, *block_off;   // [ceil(n / 256)]
+    int *index_out;            // [n] capacity
+};
+cudaError_t launch_subset(const SubsetArgs &a, int *count_out, float *X_out, int ld_out,
+                          int *status, cudaStream_t s);
+
 // ------------------------------------------------------------- batches ---
 // One scene of a batched latent step, in device memory: its fields, reference
 // positions and the per-scene part of the batch workspace.

@@ -118,3 +118,17 @@ def test_batch_validation_without_gpu(native):
     assert lib.nsf_latent_batch_create(2, items, C.byref(opts), None, 0,
                                        C.byref(h)) == native.NSF_ERR_INVALID_ARG
     assert lib.nsf_latent_step_batched(None, 0.0, 1, 0, None, None, None) == native.NSF_ERR_INVALID_ARG
+
+
+def test_integration_set_validation_without_gpu(native):
+    lib = native.lib
+    g = native.nsf_grid_desc()
+    for i in range(3):
+        g.n[i] = 32
+    g.dx = 1.0 / 32
+    size = C.c_size_t()
+    assert lib.nsf_integration_set_workspace_size(C.byref(g), 1000, C.byref(size)) == 0
+    assert size.value >= 32 ** 3 // 8 + 1000 * 12      # node bitmap + positions
+    assert lib.nsf_integration_set_workspace_size(C.byref(g), 0, C.byref(size)) == native.NSF_ERR_INVALID_ARG
+    assert lib.nsf_integration_set(None, C.byref(g), None, 10, None, 1, None, None, None, None, 0,
+                                   None, 0, None, None) == native.NSF_ERR_INVALID_ARG
