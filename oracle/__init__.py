@@ -21,10 +21,12 @@ paper's order and notation, so that it can be read against the paper by eye:
 * ``metrics``      the relative deformation error delta (Eq. 10) and the
                    dimension-reduction ratio gamma.
 * ``subsets``      sample / integration particle construction (§5.4).
+* ``training``     loss, reverse-mode weight / latent-code gradients and Adam
+                   for fitting a field to snapshots (App. D).
 
 Pinned by ``tests/test_oracle_*.py`` against closed forms, conservation laws,
 brute force and finite differences.  Multi-step trajectories of random fields
 have no external pin ("parity unpinned"); only their drift is reported.
 """
 
-from . import constitutive, fields, latent, metrics, mpm, subsets  # noqa: F401
+from . import constitutive, fields, latent, metrics, mpm, subsets, training  # noqa: F401
