@@ -284,6 +284,47 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
                               int *d_status, void *stream);
 
 /*
+ * Fitting a field to full-order snapshots (paper App. D): loss, gradients and
+ * Adam.  Training points p = 0 .. n-1 each belong to a snapshot code[p] whose
+ * latent code is row code[p] of the float32 table d_z_table [n_codes][r]
+ * (learned jointly with the weights).  With y_p the de-normalised output of
+ * field `field` at [X_p; z_code(p)] (X_p + MLP for a residual g) and y*_p the
+ * target (d_target [out_dim][n]), the loss is the mean squared normalised
+ * error  L = sum_p sum_a ((y_pa - y*_pa) / out_scale_a)^2 / (n out_dim)
+ * (the training data are normalised, App. D).
+ *
+ * nsf_field_loss_grad writes L to *d_loss, dL/dW to d_grad_w (float32, the
+ * flat host layout of that field's weights: W_l row-major then b_l per layer;
+ * nsf_field_weight_count values) and, if d_grad_z is not NULL, dL/dz to
+ * d_grad_z [n_codes][r] (rows of codes absent from the batch are zero).  The
+ * forward pass runs in the fields' precision (BF16: every product with bf16
+ * operands and FP32 accumulation on the tensor cores, the input layer in
+ * FP32); the backward pass is FP32 on the forward's activations, which the
+ * workspace keeps (nsf_train_workspace_size bytes).  Dense products go to
+ * cuBLAS; the first training call on a device creates its cuBLAS handle.
+ * A negative code[p] sets NSF_ERR_INVALID_ARG in *d_status.
+ *
+ * nsf_adam_step: one Adam step (Kingma and Ba 2014; App. D) on count float32
+ * parameters in place, step >= 1 (bias correction).
+ *
+ * nsf_fields_set_weights: replaces field `field`'s weights from a device
+ * float32 array in the flat host layout (rounding the matrices to bf16 for a
+ * BF16 fields object), on `stream`.  Shapes stay those of the descriptor.
+ */
+nsf_status nsf_field_weight_count(const nsf_fields *fields, int field, size_t *count);
+nsf_status nsf_train_workspace_size(const nsf_fields *fields, int field, int n, size_t *bytes);
+nsf_status nsf_field_loss_grad(const nsf_fields *fields, int field, const float *d_X,
+                               const int *d_code, const float *d_target, int n,
+                               const float *d_z_table, int n_codes, float *d_loss,
+                               float *d_grad_w, float *d_grad_z, void *d_workspace,
+                               size_t workspace_bytes, int *d_status, void *stream);
+nsf_status nsf_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v,
+                         size_t count, int step, float lr, float beta1, float beta2, float eps,
+                         void *stream);
+nsf_status nsf_fields_set_weights(nsf_fields *fields, int field, const float *d_weights,
+                                  void *stream);
+
+/*
  * Sample and integration particles (paper §5.4).  With the particle positions
  * x_p = g(X_p, z) of all n_all particles P at the latent code z:
  *   I = grid nodes in the quadratic B-spline stencil (base + {0,1,2}^3, base =

@@ -184,6 +184,110 @@ def nsf_project_static(fields, X_S, x_target, z, opts, status, z_iter=None, resi
           "nsf_project_static")
 
 
+# ------------------------------------------------------------ training ---
+FIELD_INDEX = {"g": N.NSF_FIELD_G, "h": N.NSF_FIELD_H, "l": N.NSF_FIELD_L}
+
+
+def nsf_field_weight_count(fields, field):
+    c = C.c_size_t()
+    check(N.lib.nsf_field_weight_count(fields.handle, int(field), C.byref(c)),
+          "nsf_field_weight_count")
+    return c.value
+
+
+def nsf_train_workspace_size(fields, field, n):
+    b = C.c_size_t()
+    check(N.lib.nsf_train_workspace_size(fields.handle, int(field), int(n), C.byref(b)),
+          "nsf_train_workspace_size")
+    return b.value
+
+
+def nsf_field_loss_grad(fields, field, X, code, target, z_table, loss, grad_w, grad_z,
+                        workspace, status, stream=None):
+    check(N.lib.nsf_field_loss_grad(fields.handle, int(field), _ptr(X), _ptr(code), _ptr(target),
+                                    int(X.shape[1]), _ptr(z_table), int(z_table.shape[0]),
+                                    _ptr(loss), _ptr(grad_w), _ptr(grad_z), _ptr(workspace),
+                                    workspace.numel(), _ptr(status), _stream(stream)),
+          "nsf_field_loss_grad")
+
+
+def nsf_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(N.lib.nsf_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
+                              int(step), float(lr), float(beta1), float(beta2), float(eps),
+                              _stream(stream)), "nsf_adam_step")
+
+
+def nsf_fields_set_weights(fields, field, weights, stream=None):
+    check(N.lib.nsf_fields_set_weights(fields.handle, int(field), _ptr(weights), _stream(stream)),
+          "nsf_fields_set_weights")
+
+
+def _field_loss_function():
+    """torch.autograd.Function whose backward is the library's hand-written
+    one: forward(weights, z_table, fields, field, X, code, target) -> loss,
+    with weights the field's flat float32 master weights (synced into the
+    fields object first) and z_table [n_codes, r] float32."""
+    torch = _torch()
+
+    class FieldLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, weights, z_table, fields, field, X, code, target):
+            dev = X.device
+            nsf_fields_set_weights(fields, field, weights)
+            ws = _zeros_u8(nsf_train_workspace_size(fields, field, X.shape[1]), dev)
+            loss = torch.zeros(1, dtype=torch.float32, device=dev)
+            gw = torch.empty_like(weights)
+            gz = torch.empty_like(z_table)
+            st = torch.zeros(1, dtype=torch.int32, device=dev)
+            nsf_field_loss_grad(fields, field, X, code, target, z_table, loss, gw, gz, ws, st)
+            ctx.save_for_backward(gw, gz)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, g):
+            gw, gz = ctx.saved_tensors
+            return g * gw, g * gz, None, None, None, None, None
+
+    return FieldLoss
+
+
+def field_loss(weights, z_table, fields, field, X, code, target):
+    """Training loss of one field (App. D) with the library's gradients."""
+    return _field_loss_function().apply(weights, z_table, fields, FIELD_INDEX.get(field, field),
+                                        X, code, target)
+
+
+class FieldTrainer:
+    """Adam on one field's FP32 master weights and a table of per-snapshot
+    latent codes, every step in the library: loss and gradients
+    (nsf_field_loss_grad), Adam (nsf_adam_step), re-pack of the new weights
+    into the fields object (nsf_fields_set_weights)."""
+
+    def __init__(self, fields, field, weights, z_table, batch, lr=1e-4):
+        torch = _torch()
+        self.fields, self.field = fields, FIELD_INDEX.get(field, field)
+        self.w = weights.detach().clone().float().contiguous()
+        self.z = z_table.detach().clone().float().contiguous()
+        self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
+        self.mz, self.vz = torch.zeros_like(self.z), torch.zeros_like(self.z)
+        self.gw, self.gz = torch.empty_like(self.w), torch.empty_like(self.z)
+        dev = self.w.device
+        self.ws = _zeros_u8(nsf_train_workspace_size(fields, self.field, batch), dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.lr, self.t = lr, 0
+        nsf_fields_set_weights(fields, self.field, self.w)
+
+    def step(self, X, code, target, stream=None):
+        self.t += 1
+        nsf_field_loss_grad(self.fields, self.field, X, code, target, self.z, self.loss, self.gw,
+                            self.gz, self.ws, self.status, stream)
+        nsf_adam_step(self.w, self.gw, self.mw, self.vw, self.t, self.lr, stream=stream)
+        nsf_adam_step(self.z, self.gz, self.mz, self.vz, self.t, self.lr, stream=stream)
+        nsf_fields_set_weights(self.fields, self.field, self.w, stream)
+        return self.loss
+
+
 def nsf_integration_set_workspace_size(grid, n_all):
     b = C.c_size_t()
     check(N.lib.nsf_integration_set_workspace_size(C.byref(grid), int(n_all), C.byref(b)),

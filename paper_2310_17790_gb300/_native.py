@@ -107,6 +107,11 @@ SIGNATURES = [
     ("nsf_project_workspace_size", _ST, [_P, _I, C.POINTER(_S)]),
     ("nsf_project", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _S, _P, _P]),
     ("nsf_project_static", _ST, [_P, _P, _P, _I, _P, C.POINTER(nsf_gn_opts), _P, _P, _P, _P]),
+    ("nsf_field_weight_count", _ST, [_P, _I, C.POINTER(_S)]),
+    ("nsf_train_workspace_size", _ST, [_P, _I, _I, C.POINTER(_S)]),
+    ("nsf_field_loss_grad", _ST, [_P, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _S, _P, _P]),
+    ("nsf_adam_step", _ST, [_P, _P, _P, _P, _S, _I, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+    ("nsf_fields_set_weights", _ST, [_P, _I, _P, _P]),
     ("nsf_integration_set_workspace_size", _ST, [C.POINTER(nsf_grid_desc), _I, C.POINTER(_S)]),
     ("nsf_integration_set", _ST, [_P, C.POINTER(nsf_grid_desc), _P, _I, _P, _I, _P, _P, _P, _P,
                                   _I, _P, _S, _P, _P]),

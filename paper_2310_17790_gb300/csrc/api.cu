@@ -591,6 +591,58 @@ SubsetLayout subset_layout(const nsf_grid_desc *g, int n) {
 
 extern "C" {
 
+nsf_status nsf_field_weight_count(const nsf_fields *f, int field, size_t *count) {
+    if (!f || field < 0 || field > 2 || !count) return NSF_ERR_INVALID_ARG;
+    const int r = f->desc.r, W = f->desc.width[field], D = f->desc.depth[field];
+    size_t c = 0;
+    for (int l = 0; l <= D; ++l) {
+        const int in = l == 0 ? 3 + r : W, out = l == D ? kOutDim[field] : W;
+        c += (size_t)in * out + out;
+    }
+    *count = c;
+    return NSF_OK;
+}
+
+nsf_status nsf_train_workspace_size(const nsf_fields *f, int field, int n, size_t *bytes) {
+    if (!f || field < 0 || field > 2 || n < 1 || !bytes) return NSF_ERR_INVALID_ARG;
+    *bytes = train_layout(f->desc.r, f->desc.width[field], f->desc.depth[field], kOutDim[field],
+                          n).total;
+    return NSF_OK;
+}
+
+nsf_status nsf_field_loss_grad(const nsf_fields *f, int field, const float *d_X, const int *d_code,
+                               const float *d_target, int n, const float *d_z_table, int n_codes,
+                               float *d_loss, float *d_grad_w, float *d_grad_z, void *d_ws,
+                               size_t ws_bytes, int *d_status, void *stream) {
+    if (!f || field < 0 || field > 2 || !d_X || !d_code || !d_target || n < 1 || !d_z_table ||
+        n_codes < 1 || !d_loss || !d_grad_w)
+        return NSF_ERR_INVALID_ARG;
+    const TrainLayout L = train_layout(f->desc.r, f->desc.width[field], f->desc.depth[field],
+                                       kOutDim[field], n);
+    if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
+    cudaError_t e = run_loss_grad(f->dev, field, d_X, d_code, d_target, n, d_z_table, n_codes,
+                                  d_loss, d_grad_w, d_grad_z, static_cast<char *>(d_ws), d_status,
+                                  static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? NSF_OK : NSF_ERR_CUDA;
+}
+
+nsf_status nsf_adam_step(float *d_param, const float *d_grad, float *d_m, float *d_v, size_t count,
+                         int step, float lr, float beta1, float beta2, float eps, void *stream) {
+    if (!d_param || !d_grad || !d_m || !d_v || step < 1 || !(lr >= 0.f) || !(beta1 >= 0.f) ||
+        !(beta1 < 1.f) || !(beta2 >= 0.f) || !(beta2 < 1.f) || !(eps >= 0.f))
+        return NSF_ERR_INVALID_ARG;
+    if (count == 0) return NSF_OK;
+    NSF_CUDA_TRY(launch_adam(d_param, d_grad, d_m, d_v, (long long)count, step, lr, beta1, beta2,
+                             eps, static_cast<cudaStream_t>(stream)));
+    return NSF_OK;
+}
+
+nsf_status nsf_fields_set_weights(nsf_fields *f, int field, const float *d_weights, void *stream) {
+    if (!f || field < 0 || field > 2 || !d_weights) return NSF_ERR_INVALID_ARG;
+    NSF_CUDA_TRY(launch_repack(f->dev, field, d_weights, static_cast<cudaStream_t>(stream)));
+    return NSF_OK;
+}
+
 nsf_status nsf_integration_set_workspace_size(const nsf_grid_desc *grid, int n_all,
                                               size_t *bytes) {
     if (!valid_grid(grid) || n_all < 1 || !bytes) return NSF_ERR_INVALID_ARG;

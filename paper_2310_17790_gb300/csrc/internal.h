@@ -158,6 +158,23 @@ struct SubsetArgs {
 cudaError_t launch_subset(const SubsetArgs &a, int *count_out, float *X_out, int ld_out,
                           int *status, cudaStream_t s);
 
+// --------------------------------------------------------------- training ---
+// Workspace of one loss/gradient evaluation (train.cu).
+struct TrainLayout {
+    size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, w16,
+        total;
+};
+TrainLayout train_layout(int r, int W, int D, int od, int n);
+cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const int *code,
+                          const float *target, int n, const float *z_table, int n_codes,
+                          float *loss, float *grad_w, float *grad_z, char *ws, int *status,
+                          cudaStream_t s);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, long long count, int step,
+                        float lr, float b1, float b2, float eps, cudaStream_t s);
+// Rewrites field `field`'s device weights (FP32 copies and, for BF16, the
+// swizzled tensor-core operand) from a flat array in the host layout.
+cudaError_t launch_repack(const FieldsDev &fd, int field, const float *flat, cudaStream_t s);
+
 // ------------------------------------------------------------- batches ---
 // One scene of a batched latent step, in device memory: its fields, reference
 // positions and the per-scene part of the batch workspace.
