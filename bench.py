@@ -267,6 +267,7 @@ def run_gpu(args, rank, world, local):
     e2e = run_e2e(args, nsf, sc, F, gd, dev)
 
     batched = run_batched(args, nsf, dev, flush, peaks, peak_src) if args.precision == "bf16" else None
+    training = run_training(args, nsf, dev, peaks, peak_src)
     clocks.__exit__(None, None, None)
 
     full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
@@ -291,6 +292,7 @@ def run_gpu(args, rank, world, local):
         "mlp_throughput": throughput,
         "e2e": e2e,
         "batched": batched,
+        "training": training,
         "full_order": full,
         "full_order_plastic": full_plastic,
         "gpu_launches": launches_per_step * K,
@@ -534,6 +536,70 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
             "note": "one CUDA-graph replay of one batched step; L2 flushed between steps"}
 
 
+def run_training(args, nsf, dev, peaks, peak_src):
+    """One training step of the deformation field on full-order snapshots
+    (App. D): 64 snapshots of the 200,000-particle slab from the library's
+    full-order step (5 steps apart), minibatches of 65,536 (particle,
+    snapshot) pairs, field g of 5 hidden layers x 256 (BF16 forward, TF32
+    backward products, FP32 master weights), per-snapshot latent codes r = 6 learned
+    jointly, Adam lr 1e-4.  A step = loss and gradients + Adam on weights and
+    codes + re-pack of the weights, all through the C ABI."""
+    import torch
+    from scenes.synthetic import full_config2, make_fields
+    fc = full_config2(steps=1)
+    x, v = (torch.from_numpy(np.ascontiguousarray(a.T)).to(dev) for a in (fc.x, fc.v))
+    Cm, Fm = (torch.from_numpy(np.ascontiguousarray(a.T)).to(dev) for a in (fc.C, fc.F))
+    X_ref = x.clone()
+    gd = nsf.grid_desc(fc.grid.n, fc.grid.dx, fc.grid.gravity, fc.grid.wall_cells, fc.grid.blade)
+    st = nsf.FullStepper(gd, nsf.material(**fc.material), x, v, Cm, Fm, fc.mass, fc.vol0)
+    snaps = []
+    for t in range(64):
+        st.step(fc.dt, t0=t * 5 * fc.dt, nsteps=5)
+        snaps.append(x.clone())
+    torch.cuda.synchronize()
+    snaps = torch.stack(snaps)                                   # [64, 3, n]
+    n_all = X_ref.shape[1]
+    B = 65536
+    rng = np.random.Generator(np.random.PCG64(2315))
+    spec = make_fields(rng, 6, 256, 5, "bf16", {"g": 1e-2, "h": 1e4, "l": 1.0})
+    F = nsf.Fields.from_spec(spec)
+    z0 = torch.from_numpy(rng.normal(0, 0.1, size=(64, 6)).astype(np.float32)).to(dev)
+    w0 = torch.from_numpy(np.asarray(spec.weights["g"], np.float32)).to(dev)
+    tr = nsf.FieldTrainer(F, "g", w0, z0, B, lr=1e-4)
+
+    def batch(seed):
+        r_ = np.random.Generator(np.random.PCG64(seed))
+        p = torch.from_numpy(r_.integers(0, n_all, size=B)).to(dev)
+        t = torch.from_numpy(r_.integers(0, 64, size=B)).to(dev)
+        X = X_ref[:, p].contiguous()
+        tgt = snaps[t, :, p].T.contiguous()
+        return X, t.to(torch.int32).contiguous(), tgt
+    batches = [batch(2400 + k) for k in range(4)]
+    for k in range(3):
+        tr.step(*batches[k % 4])
+    torch.cuda.synchronize()
+    K = max(1, min(args.steps, 50))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    first = float(tr.step(*batches[0]).item())
+    a.record()
+    for k in range(K):
+        tr.step(*batches[k % 4])
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    last = float(tr.loss.item())
+    mac = mlp_macs(6, 256, 5, 3)
+    flops = 6.0 * B * mac        # forward 2 n MAC, backward 4 n MAC
+    return {"workload": "train-g-w256d5-r6-bf16fwd-tf32bwd-batch65536-64snapshots-200k",
+            "ms_per_step": ms, "steps": K, "points_per_s": B / (ms / 1e3),
+            "tflops": flops / (ms / 1e3) / 1e12, "flops_per_step": flops,
+            "loss_first": first, "loss_last": last,
+            "note": "loss and gradients (forward BF16 GEMMs, backward TF32 GEMMs via cuBLAS "
+                    "with FP32 accumulation, chain-rule kernels), Adam on weights and codes, "
+                    "weight re-pack"}
+
+
 def run_part(args):
     """One part of the benchmark alone (for profiling captures)."""
     import torch
@@ -545,6 +611,8 @@ def run_part(args):
     if args.only == "mlp":
         return run_throughput(args, nsf, latent_config3(precision="bf16", steps=1).fields, dev,
                               peaks, peak_src)
+    if args.only == "training":
+        return run_training(args, nsf, dev, peaks, peak_src)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     return run_batched(args, nsf, dev, flush, peaks, peak_src)
 
@@ -597,7 +665,7 @@ def main():
     ap.add_argument("--impl", default="nsf", choices=["nsf", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "mlp"],
+    ap.add_argument("--only", default="all", choices=["all", "batched", "mlp", "training"],
                     help="batched / mlp: run that part alone (profiling runs) and print its JSON")
     ap.add_argument("--batch-scenes", type=int, default=256)
     args = ap.parse_args()

@@ -87,10 +87,12 @@ enum { NSF_PREC_FP32 = 0, NSF_PREC_BF16 = 1 };
  *   accumulation in tensor memory, activations entering them rounded to bf16;
  *   the K = 3 + r input layer, ELU and the output de-normalisation stay FP32,
  *   and biases keep ~16 significant bits (a bf16 head and tail).
- * Limits: 1 <= r <= NSF_MAX_R; width[f] a multiple of 16 in [16, NSF_MAX_WIDTH]
- * (BF16: 64, 128 or 192 for any depth, 256 while the field's weights fit in
- * shared memory; otherwise nsf_create_fields returns NSF_ERR_UNSUPPORTED);
- * 1 <= depth[f] <= NSF_MAX_DEPTH.
+ * Limits: 1 <= r <= NSF_MAX_R; width[f] a multiple of 16 in [16, NSF_MAX_WIDTH];
+ * 1 <= depth[f] <= NSF_MAX_DEPTH.  BF16 widths are 64, 128, 192 or 256; the
+ * tensor-core inference kernels keep a field's weights in shared memory, so a
+ * BF16 fields object whose weights do not fit there (e.g. 256 wide and 5
+ * deep) serves the training calls only: the inference calls (evaluation,
+ * stepping, projection, integration sets, batches) return NSF_ERR_UNSUPPORTED.
  */
 typedef struct nsf_fields_desc {
     int r;
@@ -300,7 +302,8 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
  * forward pass runs in the fields' precision (BF16: every product with bf16
  * operands and FP32 accumulation on the tensor cores, the input layer in
  * FP32); the backward pass is FP32 on the forward's activations, which the
- * workspace keeps (nsf_train_workspace_size bytes).  Dense products go to
+ * workspace keeps (nsf_train_workspace_size bytes), with its products in TF32
+ * (FP32 accumulation) for BF16 fields.  Dense products go to
  * cuBLAS; the first training call on a device creates its cuBLAS handle.
  * A negative code[p] sets NSF_ERR_INVALID_ARG in *d_status.
  *

@@ -16,6 +16,9 @@ struct nsf_fields {
     FieldsDev dev;
     void *d_mem;
     size_t bytes;
+    // the inference kernels can run these fields (a BF16 field whose weights do
+    // not fit in shared memory is created for training only)
+    int infer_ok;
 };
 
 namespace {
@@ -300,9 +303,10 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
         return o;
     };
     auto round_bf16 = [](float v) { return __bfloat162float(__float2bfloat16_rn(v)); };
+    int infer_ok = 1;
     if (bf16)
         for (int f = 0; f < 3; ++f)
-            if (tc_smem_bytes(r, desc->width[f], desc->depth[f]) == 0) return NSF_ERR_UNSUPPORTED;
+            if (tc_smem_bytes(r, desc->width[f], desc->depth[f]) == 0) infer_ok = 0;
     for (int f = 0; f < 3; ++f) {
         const int W = desc->width[f], D = desc->depth[f], od = kOutDim[f];
         const float *src = host_weights[f];
@@ -365,6 +369,7 @@ nsf_status nsf_create_fields(const nsf_fields_desc *desc, const float *const hos
     }
     std::memset(F, 0, sizeof(*F));
     F->desc = *desc;
+    F->infer_ok = infer_ok;
     F->d_mem = mem;
     F->bytes = fbytes + hbytes;
     const float *fb = static_cast<const float *>(mem);
@@ -408,6 +413,7 @@ nsf_status nsf_eval_fields(const nsf_fields *f, const float *d_X, int n, const d
                            float *d_x, float *d_tau6, float *d_C9, float *d_dxdz,
                            int *d_status, void *stream) {
     if (!f || n < 0 || (n > 0 && (!d_X || !d_z))) return NSF_ERR_INVALID_ARG;
+    if (!f->infer_ok) return NSF_ERR_UNSUPPORTED;
     if (n == 0) return NSF_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FieldJob jobs[3];
@@ -439,6 +445,7 @@ nsf_status nsf_latent_step(const nsf_fields *f, const nsf_latent_scene *sc, doub
         !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t0) || !(sc->mass > 0.f) ||
         !(sc->vol0 > 0.f) || (flags & ~(unsigned)NSF_LATENT_REUSE_PREV))
         return NSF_ERR_INVALID_ARG;
+    if (!f->infer_ok) return NSF_ERR_UNSUPPORTED;
     if (nsteps == 0) return NSF_OK;
     LatentLayout L = latent_layout(f, sc);
     if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
@@ -536,6 +543,7 @@ nsf_status nsf_project(const nsf_fields *f, const float *d_X_S, const float *d_x
                        void *stream) {
     if (!f || !d_X_S || !d_x_target || n_S < 1 || !d_z_inout || !valid_gn(opts))
         return NSF_ERR_INVALID_ARG;
+    if (!f->infer_ok) return NSF_ERR_UNSUPPORTED;
     ProjectLayout L = project_layout(f, n_S);
     if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -658,6 +666,7 @@ nsf_status nsf_integration_set(const nsf_fields *f, const nsf_grid_desc *grid, c
         (n_S > 0 && !d_sample) || !d_z || !d_index_out || !d_count_out ||
         (d_X_out && x_out_ld < n_all))
         return NSF_ERR_INVALID_ARG;
+    if (!f->infer_ok) return NSF_ERR_UNSUPPORTED;
     const SubsetLayout L = subset_layout(grid, n_all);
     if (!d_ws || ws_bytes < L.total) return NSF_ERR_WORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1026,7 +1035,7 @@ nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
     for (int i = 0; i < n; ++i) {
         if (!valid_batch_item(items[i])) return NSF_ERR_INVALID_ARG;
         const nsf_fields_desc &d = items[i].fields->desc;
-        if (d.precision != NSF_PREC_BF16) return NSF_ERR_UNSUPPORTED;
+        if (d.precision != NSF_PREC_BF16 || !items[i].fields->infer_ok) return NSF_ERR_UNSUPPORTED;
     }
     const BatchLayout BL = batch_layout(n, items);
     if (!d_ws || ws_bytes < BL.total) return NSF_ERR_WORKSPACE;

@@ -161,7 +161,7 @@ cudaError_t launch_subset(const SubsetArgs &a, int *count_out, float *X_out, int
 // --------------------------------------------------------------- training ---
 // Workspace of one loss/gradient evaluation (train.cu).
 struct TrainLayout {
-    size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, w16,
+    size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, w16, ones,
         total;
 };
 TrainLayout train_layout(int r, int W, int D, int od, int n);

@@ -8,9 +8,10 @@
 // precision (BF16 fields: bf16 operands, FP32 accumulation on the tensor
 // cores; the activations entering a product are rounded to bf16).  Loss: the
 // mean squared normalised error L = sum ((y - y*) / scale)^2 / (n out_dim).
-// Backward in FP32 on the forward's activations:
+// Backward in FP32 (TF32 products for BF16 fields) on the forward's
+// activations:
 //   delta_out = dL/draw = 2 (y - y*) / (scale n out_dim)
-//   dW_l = delta_l H_{l-1}^T,  db_l = row sums of delta_l,
+//   dW_l = delta_l H_{l-1}^T,  db_l = delta_l x ones (row sums),
 //   delta_{l-1} = (W_l^T delta_l) * ELU'(A_{l-1}),
 //   dz_t += (W_0^T delta_0)[3:, p] over the points p of snapshot t.
 // The dense products go to cuBLAS (plain GEMMs); the chain rule around them
@@ -51,19 +52,24 @@ __global__ void k_inputs(const float *__restrict__ X, const int *__restrict__ co
     for (int k = 0; k < r; ++k) col[3 + k] = z_table[(size_t)c * r + k];
 }
 
-// H = ELU(A + b) over a rows x n block; H32 gets the value entering the next
-// product (bf16-rounded when round_bf16), H16 (optional) its bf16 copy.
-__global__ void k_bias_elu(float *A, const float *__restrict__ b, int rows, long long count,
-                           float *H32, __nv_bfloat16 *H16, int round_bf16) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const float a = A[i] + b[i % rows];
+// H = ELU(A + b) over a rows x n block (CTA y = a group of points, thread x a
+// row); H32 gets the value entering the next product (bf16-rounded when
+// round_bf16), H16 (optional) its bf16 copy.
+__global__ void k_bias_elu(float *A, const float *__restrict__ b, int rows, int n, float *H32,
+                           __nv_bfloat16 *H16, int round_bf16) {
+    const int o = threadIdx.x;
+    if (o >= rows) return;
+    const float bo = b[o];
+    for (int p = blockIdx.x; p < n; p += gridDim.x) {
+    const size_t i = (size_t)p * rows + o;
+    const float a = A[i] + bo;
     A[i] = a;
     float h = a > 0.f ? a : expm1f(a);
     const __nv_bfloat16 hb = __float2bfloat16_rn(h);
     if (round_bf16) h = __bfloat162float(hb);
     H32[i] = h;
     if (H16) H16[i] = hb;
+    }
 }
 
 // Outputs, loss and dL/draw.  raw: od x n (column-major), target [od][n].
@@ -99,29 +105,34 @@ __global__ void k_elu_grad(float *delta, const float *__restrict__ A, long long 
     delta[i] *= a > 0.f ? 1.f : expf(a);
 }
 
-// db[o] = sum_p delta[o + p rows]: one CTA per row, strided over points.
-__global__ void k_row_sums(const float *__restrict__ delta, int rows, int n, float *db) {
-    __shared__ float part[kT];
-    const int o = blockIdx.x;
-    float s = 0.f;
-    for (int p = threadIdx.x; p < n; p += kT) s += delta[(size_t)p * rows + o];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int k = kT / 2; k > 0; k >>= 1) {
-        if (threadIdx.x < k) part[threadIdx.x] += part[threadIdx.x + k];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[o] = part[0];
+__global__ void k_fill(float *a, float v, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) a[i] = v;
 }
 
-// dz_code(p) += dinp[3:, p]
+// dz_code(p) += dinp[3:, p]: per CTA into a shared copy of the table (when it
+// fits), then one global atomic per entry the CTA touched.
+constexpr int kDzShared = 4096;
 __global__ void k_scatter_dz(const float *__restrict__ dinp, const int *__restrict__ code, int n,
                              int r, int n_codes, float *gz) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const int c = code[p];
-    if (c < 0 || c >= n_codes) return;
-    for (int k = 0; k < r; ++k) atomicAdd(&gz[(size_t)c * r + k], dinp[(size_t)p * (3 + r) + 3 + k]);
+    __shared__ float tab[kDzShared];
+    const bool local = n_codes * r <= kDzShared;
+    if (local)
+        for (int i = threadIdx.x; i < n_codes * r; i += blockDim.x) tab[i] = 0.f;
+    __syncthreads();
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int c = code[p];
+        if (c < 0 || c >= n_codes) continue;
+        for (int k = 0; k < r; ++k) {
+            const float v = dinp[(size_t)p * (3 + r) + 3 + k];
+            if (local) atomicAdd(&tab[c * r + k], v);
+            else atomicAdd(&gz[(size_t)c * r + k], v);
+        }
+    }
+    if (!local) return;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_codes * r; i += blockDim.x)
+        if (tab[i] != 0.f) atomicAdd(&gz[i], tab[i]);
 }
 
 __global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *b, long long count) {
@@ -248,6 +259,7 @@ TrainLayout train_layout(int r, int W, int D, int od, int n) {
     L.d1 = take((size_t)W * nn * 4);
     L.d2 = take((size_t)W * nn * 4);
     L.w16 = take((size_t)W * W * 2);
+    L.ones = take(nn * 4);
     L.total = o;
     return L;
 }
@@ -271,8 +283,9 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     // ---- forward
     k_inputs<<<blocks(n), kT, 0, s>>>(X, code, z_table, n, r, P(L.inp), status);
     NSF_CB(sgemm(h, true, false, W, n, K0, F.W0, K0, P(L.inp), K0, P(L.A[0]), W));
-    k_bias_elu<<<blocks(nW), kT, 0, s>>>(P(L.A[0]), F.b[0], W, nW, P(L.H[0]),
-                                         bf16 ? P16(L.H16[0]) : nullptr, bf16 ? 1 : 0);
+    const int ecta = n < 4 * 152 * 8 ? n : 4 * 152 * 8;      // CTAs of the row-wise kernels
+    k_bias_elu<<<ecta, W, 0, s>>>(P(L.A[0]), F.b[0], W, n, P(L.H[0]),
+                                  bf16 ? P16(L.H16[0]) : nullptr, bf16 ? 1 : 0);
     for (int l = 1; l < D; ++l) {
         if (bf16) {
             k_to_bf16<<<blocks((long long)W * W), kT, 0, s>>>(F.Wt[l], P16(L.w16), (long long)W * W);
@@ -281,8 +294,8 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
         } else {
             NSF_CB(sgemm(h, false, false, W, n, W, F.Wt[l], W, P(L.H[l - 1]), W, P(L.A[l]), W));
         }
-        k_bias_elu<<<blocks(nW), kT, 0, s>>>(P(L.A[l]), F.b[l], W, nW, P(L.H[l]),
-                                             bf16 ? P16(L.H16[l]) : nullptr, bf16 ? 1 : 0);
+        k_bias_elu<<<ecta, W, 0, s>>>(P(L.A[l]), F.b[l], W, n, P(L.H[l]),
+                                      bf16 ? P16(L.H16[l]) : nullptr, bf16 ? 1 : 0);
     }
     if (bf16) {
         k_to_bf16<<<blocks((long long)od * W), kT, 0, s>>>(F.Wout, P16(L.w16), (long long)od * W);
@@ -296,7 +309,15 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     if (e != cudaSuccess) return e;
     k_loss<<<blocks(n), kT, 0, s>>>(P(L.raw), F.b[D], X, target, n, od, F, residual ? 1 : 0,
                                     P(L.dout), loss);
-    // ---- backward; gradient offsets in the flat layout
+    // ---- backward; gradient offsets in the flat layout.  BF16 fields take
+    // their backward products in TF32 on the tensor cores (10-bit mantissa
+    // operands, FP32 accumulation: well inside the bf16 forward's rounding);
+    // FP32 fields keep FP32 products.
+    if (bf16) NSF_CB(cublasSetMathMode(h, CUBLAS_TF32_TENSOR_OP_MATH));
+    struct MathReset {
+        cublasHandle_t h;
+        ~MathReset() { cublasSetMathMode(h, CUBLAS_DEFAULT_MATH); }
+    } reset{h};
     std::vector<size_t> goff(D + 1);
     {
         size_t o = 0;
@@ -308,13 +329,18 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     }
     // output layer: dWout (row-major od x W) = H_{D-1} dout^T as a W x od column-major
     NSF_CB(sgemm(h, false, true, W, od, n, P(L.H[D - 1]), W, P(L.dout), od, grad_w + goff[D], W));
-    k_row_sums<<<od, kT, 0, s>>>(P(L.dout), od, n, grad_w + goff[D] + (size_t)od * W);
+    // bias gradients: row sums of delta = delta x ones
+    k_fill<<<blocks(n), kT, 0, s>>>(P(L.ones), 1.f, n);
+    const float one = 1.f, zero = 0.f;
+    NSF_CB(cublasSgemv(h, CUBLAS_OP_N, od, n, &one, P(L.dout), od, P(L.ones), 1, &zero,
+                       grad_w + goff[D] + (size_t)od * W, 1));
     float *dcur = P(L.d1), *dnext = P(L.d2);
     NSF_CB(sgemm(h, false, false, W, n, od, F.Wout, W, P(L.dout), od, dcur, W));
     for (int l = D - 1; l >= 1; --l) {
         k_elu_grad<<<blocks(nW), kT, 0, s>>>(dcur, P(L.A[l]), nW);
         NSF_CB(sgemm(h, false, true, W, W, n, P(L.H[l - 1]), W, dcur, W, grad_w + goff[l], W));
-        k_row_sums<<<W, kT, 0, s>>>(dcur, W, n, grad_w + goff[l] + (size_t)W * W);
+        NSF_CB(cublasSgemv(h, CUBLAS_OP_N, W, n, &one, dcur, W, P(L.ones), 1, &zero,
+                           grad_w + goff[l] + (size_t)W * W, 1));
         NSF_CB(sgemm(h, true, false, W, n, W, F.Wt[l], W, dcur, W, dnext, W));
         float *t = dcur;
         dcur = dnext;
@@ -322,12 +348,14 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     }
     k_elu_grad<<<blocks(nW), kT, 0, s>>>(dcur, P(L.A[0]), nW);
     NSF_CB(sgemm(h, false, true, K0, W, n, P(L.inp), K0, dcur, W, grad_w + goff[0], K0));
-    k_row_sums<<<W, kT, 0, s>>>(dcur, W, n, grad_w + goff[0] + (size_t)K0 * W);
+    NSF_CB(cublasSgemv(h, CUBLAS_OP_N, W, n, &one, dcur, W, P(L.ones), 1, &zero,
+                       grad_w + goff[0] + (size_t)K0 * W, 1));
     if (grad_z) {
         e = cudaMemsetAsync(grad_z, 0, (size_t)n_codes * r * sizeof(float), s);
         if (e != cudaSuccess) return e;
         NSF_CB(sgemm(h, false, false, K0, n, W, F.W0, K0, dcur, W, P(L.dinp), K0));
-        k_scatter_dz<<<blocks(n), kT, 0, s>>>(P(L.dinp), code, n, r, n_codes, grad_z);
+        k_scatter_dz<<<blocks(n) < 304 ? blocks(n) : 304, kT, 0, s>>>(P(L.dinp), code, n, r,
+                                                                   n_codes, grad_z);
     }
 #undef NSF_CB
     return cudaGetLastError();
