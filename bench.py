@@ -261,6 +261,11 @@ def run_gpu(args, rank, world, local):
     traffic = load_traffic(KERNEL_OF_STAGE.get(dom_name))
     roof["traffic"] = traffic
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    if args.only == "latent":
+        clocks.__exit__(None, None, None)
+        return {"value": steps_per_s, "unit": "steps/s", "ms_per_step": ms_per_step,
+                "stages_ms": {names[i]: float(st_ms[i]) for i in range(nst)},
+                "roofline": roof, "status": status}, clocks
     throughput = run_throughput(args, nsf, fs, dev, peaks, peak_src) if args.precision == "bf16" else None
 
     # e2e: through the public API with host buffers, copies inside the timed region
@@ -665,7 +670,8 @@ def main():
     ap.add_argument("--impl", default="nsf", choices=["nsf", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--only", default="all", choices=["all", "batched", "mlp", "training"],
+    ap.add_argument("--only", default="all",
+                    choices=["all", "latent", "batched", "mlp", "training"],
                     help="batched / mlp: run that part alone (profiling runs) and print its JSON")
     ap.add_argument("--batch-scenes", type=int, default=256)
     args = ap.parse_args()
@@ -688,6 +694,10 @@ def main():
         print(json.dumps(out))
         return
 
+    if args.only == "latent":
+        out, _ = run_gpu(args, rank, world, local)
+        print(json.dumps(out))
+        return
     if args.only != "all":
         print(json.dumps(run_part(args)))
         return

@@ -481,12 +481,16 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
 
 int jac_points_per_cta_tile(int r) { return jac_points(r); }
 
-// Columns per warpgroup for a batched problem: the narrowest tile that holds a
-// point's value and tangent slots.  Wider tiles (more points per pass through
-// the layers) measured no faster per point, since the epilogue work grows
-// with the columns a thread handles, and they spill registers at 32 columns.
+// Columns per warpgroup for a batched problem: at least 16, else the
+// narrowest tile that holds a point's value and tangent slots.  A layer's
+// products cost about the same per instruction issue up to 128 columns, so 16
+// columns (16 points at r <= 7) measured 3.5 % faster on the 256-scene batch
+// than 8; 32 columns spill registers and were no faster per point.
+#ifndef NSF_BATCH_MIN_CW
+#define NSF_BATCH_MIN_CW 16
+#endif
 int jac_batch_cw(int r, int width, int depth) {
-    for (int cw = 8; cw <= 32; cw <<= 1)
+    for (int cw = NSF_BATCH_MIN_CW; cw <= 32; cw <<= 1)
         if (jac_tc_smem_bytes_cw(r, width, depth, cw)) return cw;
     return 0;
 }
