@@ -907,7 +907,7 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
         const int W = d.width[NSF_FIELD_G], D = d.depth[NSF_FIELD_G];
         const int cw = jac_batch_cw(d.r, W, D);
         G.cw.push_back(cw);
-        const int P = 8 * cw / jac_slots_host(d.r);
+        const int P = jac_batch_points(d.r, cw);
         tiles[s] = (items[s].scene.n_S + P - 1) / P;
         // measured: a tile's pass through one layer costs about the same for
         // any width up to 128 (products have M = 128 neuron rows; one neuron
@@ -915,7 +915,7 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
         const int L = jac_slots_host(d.r);
         cost[s] = (double)items[s].scene.n_S * (D + 1) * L * (W > 128 ? 2.0 : 1.0);
         total += cost[s];
-        const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw);
+        const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw, 4);
         G.smem = sm > G.smem ? sm : G.smem;
     }
     const int cap = sms < kGnMaxCtas ? sms : kGnMaxCtas;

@@ -224,7 +224,7 @@ struct GnBatchProblem {
     const FieldsDev *fd;       // device copy of the scene's fields
     const float *X;            // [3][ld] reference positions (first n are the samples)
     int n, ld;
-    int cw;                    // columns per warpgroup of its tiles (8, 16 or 32)
+    int cw;                    // columns per warpgroup of its tiles (32 or 64, four warpgroups)
     GnArgs gn;                 // target, z, slots (sized for the group), barrier word
 };
 struct GnBatchEntry {
@@ -232,7 +232,8 @@ struct GnBatchEntry {
 };
 int jac_points_per_cta_tile(int r);
 int jac_batch_cw(int r, int width, int depth);
-size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW);
+int jac_batch_points(int r, int cw);
+size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW, int NWG);
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
                              const int *cta_entry, int nctas, size_t smem, int *status,
                              cudaStream_t s);

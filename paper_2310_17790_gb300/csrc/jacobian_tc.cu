@@ -43,6 +43,8 @@ using namespace tc;
 
 namespace {
 
+constexpr int kBatchWG = 4;             // warpgroups per CTA of the batched kernel
+
 __host__ __device__ inline int jac_slots(int r) {
     int L = 2;
     while (L < 1 + r) L <<= 1;
@@ -62,9 +64,9 @@ struct JacLayout {
 };
 
 // Layout for CW columns per warpgroup (N = 8 CW slots, N / L points per tile).
-__host__ __device__ inline JacLayout jac_layout(int r, int W, int D, int CW) {
+__host__ __device__ inline JacLayout jac_layout(int r, int W, int D, int CW, int NWG = kWG) {
     JacLayout L;
-    const int N = kWG * CW, P = N / jac_slots(r);
+    const int N = NWG * CW, P = N / jac_slots(r);
     int o = 0;
     L.blob = o; o = align_to(o + (D - 1) * W * W * 2 + kMaxOut * W * 2, 1024);
     // activations (MN-major); at least 16 KB, the reach of the padded rows
@@ -99,8 +101,9 @@ __device__ __forceinline__ void store_b_row(uint8_t *B, int k, int n0, int sbo, 
 
 // One CTA's share of a Jacobian evaluation or Gauss-Newton run: the CTA is
 // `rank` of the `gsize` CTAs that work on this point set (tiles rank, rank +
-// gsize, ...) and, for Gauss-Newton, combine their sums behind gn.bar.
-template <int CW>
+// gsize, ...) and, for Gauss-Newton, combine their sums behind gn.bar.  The
+// CTA has NWG warpgroups of CW columns each (a tile of NWG CW point slots).
+template <int CW, int NWG = kWG>
 __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n, int ld,
                          const double *zj, float *u, float *dudz, const GnArgs &gn, int gn_on,
                          int rank, int gsize, bool last_alloc, uint8_t *smem_dyn, int *status) {
@@ -111,7 +114,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
     const int W = F.width, D = F.depth, r = fd.r;
     const int L = jac_slots(r);
     const int lgL = __ffs(L) - 1;
-    constexpr int N = kWG * CW;              // columns (point slots) per tile
+    constexpr int N = NWG * CW;              // columns (point slots) per tile
     const int P = N / L;                     // points per tile
     const int MH = jac_halves(W);            // 128-neuron accumulators
     const int tiles = (n + P - 1) / P;
@@ -121,7 +124,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
     const int lane = tid & 31;
     const int n0 = wg * CW;                  // first column of this warpgroup
     const int sbo_b = (N / 64) * 1024;
-    const JacLayout Lo = jac_layout(r, W, D, CW);
+    const JacLayout Lo = jac_layout(r, W, D, CW, NWG);
     uint8_t *blob = base + Lo.blob;
     uint8_t *B = base + Lo.b;
     float4 *W0v = reinterpret_cast<float4 *>(base + Lo.w0v);
@@ -152,7 +155,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
 
     if (tid == 0) bulk_load(blob, F.tc_blob, (uint32_t)F.tc_blob_bytes, bar_w);
     const int in0 = 3 + r;
-    for (int j = tid; j < W; j += kThreads) {
+    for (int j = tid; j < W; j += NWG * kWgThreads) {
         const float *w = F.W0 + (size_t)j * in0;
         W0v[j] = make_float4(w[0], w[1], w[2], 0.f);
         b0s[j] = F.b[0][j];
@@ -160,7 +163,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
     }
     for (int l = 1; l <= D; ++l) {
         const int o = l == D ? F.out_dim : W;
-        for (int j = tid; j < o; j += kThreads) bias[(l - 1) * W + j] = F.b[l][j];
+        for (int j = tid; j < o; j += NWG * kWgThreads) bias[(l - 1) * W + j] = F.b[l][j];
     }
     // positions (and Gauss-Newton targets) of a tile of this CTA
     auto load_tile = [&](int t0) {
@@ -189,7 +192,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
     for (int it = 0; it < n_iter; ++it) {
         __syncthreads();
         // z-part of the input layer folded into its bias: c0 = b0 + W0[:, 3:] z
-        for (int j = tid; j < W; j += kThreads) {
+        for (int j = tid; j < W; j += NWG * kWgThreads) {
             float a = b0s[j];
             for (int k = 0; k < r; ++k) {
                 const float zk = gn_on ? g_gn.z[k].hi : (float)__ldcg(&zj[k]);
@@ -214,19 +217,23 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                 const int j = h * 128 + wq * 32 + lane;
                 if (j < W) {
                     const float4 w = W0v[j];
-                    float v[CW];
-                    float g = 0.f;
+                    constexpr int kC0 = CW < 32 ? CW : 32;      // whole points per chunk
 #pragma unroll
-                    for (int c = 0; c < CW; ++c) {
-                        const int s = c & (L - 1);
-                        if (s == 0) {
-                            const float4 x = xs[(n0 + c) >> lgL];
-                            v[c] = elu_fast(fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w))), g);
-                        } else {
-                            v[c] = s <= r ? g * W0t[(s - 1) * W + j] : 0.f;
+                    for (int c0 = 0; c0 < CW; c0 += kC0) {
+                        float v[kC0];
+                        float g = 0.f;
+#pragma unroll
+                        for (int c = 0; c < kC0; ++c) {
+                            const int s = c & (L - 1);
+                            if (s == 0) {
+                                const float4 x = xs[(n0 + c0 + c) >> lgL];
+                                v[c] = elu_fast(fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w))), g);
+                            } else {
+                                v[c] = s <= r ? g * W0t[(s - 1) * W + j] : 0.f;
+                            }
                         }
+                        store_b_row<kC0>(B, j, n0 + c0, sbo_b, v);
                     }
-                    store_b_row<CW>(B, j, n0, sbo_b, v);
                 }
             }
             fence_proxy_async();
@@ -270,23 +277,29 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                 if (s_abort) goto mma_timeout;
                 if (!out_layer) {
                     const float *bl = bias + (l - 1) * W;
+                    // in chunks of at most 32 columns (whole points: L <= 32
+                    // divides the chunk), which bounds the live registers
+                    constexpr int kC = CW < 32 ? CW : 32;
                     for (int h = 0; h < MH; ++h) {
                         const int j = h * 128 + wq * 32 + lane;
                         if (j < W) {                 // uniform per warp: W % 64 == 0
-                            float v[CW];
-#pragma unroll
-                            for (int g8 = 0; g8 < CW / 8; ++g8)
-                                tmem_ld8(tq + (uint32_t)(h * N + n0 + 8 * g8), v + 8 * g8);
-                            tmem_wait_ld();
                             const float b = bl[j];
-                            float g = 0.f;
 #pragma unroll
-                            for (int c = 0; c < CW; ++c) {
-                                const int s = c & (L - 1);
-                                if (s == 0) v[c] = elu_fast(v[c] + b, g);
-                                else v[c] = s <= r ? g * v[c] : 0.f;
+                            for (int c0 = 0; c0 < CW; c0 += kC) {
+                                float v[kC];
+#pragma unroll
+                                for (int g8 = 0; g8 < kC / 8; ++g8)
+                                    tmem_ld8(tq + (uint32_t)(h * N + n0 + c0 + 8 * g8), v + 8 * g8);
+                                tmem_wait_ld();
+                                float g = 0.f;
+#pragma unroll
+                                for (int c = 0; c < kC; ++c) {
+                                    const int s = c & (L - 1);
+                                    if (s == 0) v[c] = elu_fast(v[c] + b, g);
+                                    else v[c] = s <= r ? g * v[c] : 0.f;
+                                }
+                                store_b_row<kC>(B, j, n0 + c0, sbo_b, v);
                             }
-                            store_b_row<CW>(B, j, n0, sbo_b, v);
                         }
                     }
                     tc_fence_before();
@@ -294,18 +307,22 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                     __syncthreads();
                 } else {
                     bool bad = false;
-                    if (wq == 0) {
-                        float v[CW];
+                    constexpr int kC = CW < 32 ? CW : 32;
 #pragma unroll
-                        for (int g8 = 0; g8 < CW / 8; ++g8) tmem_ld8(tq + (uint32_t)(n0 + 8 * g8), v + 8 * g8);
+                    for (int c0 = 0; c0 < CW; c0 += kC) {
+                    if (wq == 0) {
+                        float v[kC];
+#pragma unroll
+                        for (int g8 = 0; g8 < kC / 8; ++g8)
+                            tmem_ld8(tq + (uint32_t)(n0 + c0 + 8 * g8), v + 8 * g8);
                         tmem_wait_ld();
                         if (lane < 3) {
                             const int a = lane;
                             const float sc = F.scale[a], sh = F.shift[a];
                             const float bo = bias[(D - 1) * W + a];
 #pragma unroll
-                            for (int c = 0; c < CW; ++c) {
-                                const int col = n0 + c;
+                            for (int c = 0; c < kC; ++c) {
+                                const int col = n0 + c0 + c;
                                 const int s = col & (L - 1);
                                 const int p = p0 + (col >> lgL);
                                 const bool valid = p < n && s <= r;
@@ -322,6 +339,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                                 O3[col * 3 + a] = valid ? y : 0.f;
                             }
                         }
+                    }
                     }
                     tc_fence_before();
                     if (bad) set_status(status, NSF_ERR_NONFINITE);
@@ -378,21 +396,25 @@ k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int 
                  smem_dyn, status);
 }
 
-// One Gauss-Newton problem of a batch (out of line, so that each latent-size
-// class keeps its own register allocation).
+// One Gauss-Newton problem of a batch (inlined: out of line, the bodies spilled
+// ~450 bytes per thread at 128 registers; inlined, 112).
 template <int CW>
-__device__ __noinline__ void jac_batch_problem(const GnBatchProblem &pb, const GnBatchEntry &en,
+__device__ __forceinline__ void jac_batch_problem(const GnBatchProblem &pb, const GnBatchEntry &en,
                                                uint8_t *smem_dyn, int *status) {
-    jac_body<CW>(*pb.fd, pb.X, pb.n, pb.ld, nullptr, nullptr, nullptr, pb.gn, 1, en.rank, en.size,
-                 false, smem_dyn, status);
+    jac_body<CW, kBatchWG>(*pb.fd, pb.X, pb.n, pb.ld, nullptr, nullptr, nullptr, pb.gn, 1,
+                           en.rank, en.size, false, smem_dyn, status);
 }
 
 // Batched Gauss-Newton: CTA c runs the problems of its entries
 // cta_entry[c] .. cta_entry[c + 1] - 1 in order; an entry names a problem, the
 // CTA's rank in that problem's CTA group and the group size.  A CTA that
 // shares a problem with others (group size > 1) has no other entry, so the
-// group barriers of different problems never wait on each other.
-__global__ void __launch_bounds__(kThreads, 1)
+// group barriers of different problems never wait on each other.  The CTAs
+// have four warpgroups of 32 or 64 columns: tiles of up to 256 point slots,
+// whose products take as many tcgen05.mma instructions as the single-problem
+// kernel's 64-slot tiles (a layer's instructions cost about the same per
+// issue up to this size), at 128 registers per thread.
+__global__ void __launch_bounds__(kBatchWG * kWgThreads, 1)
 k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__restrict__ entries,
             const int *__restrict__ cta_entry, int *status) {
     extern __shared__ uint8_t smem_dyn[];
@@ -400,9 +422,8 @@ k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__rest
     for (int e = e0; e < e1; ++e) {
         const GnBatchEntry en = entries[e];
         const GnBatchProblem &pb = probs[en.problem];
-        if (pb.cw == 8) jac_batch_problem<8>(pb, en, smem_dyn, status);
-        else if (pb.cw == 16) jac_batch_problem<16>(pb, en, smem_dyn, status);
-        else jac_batch_problem<32>(pb, en, smem_dyn, status);
+        if (pb.cw == 32) jac_batch_problem<32>(pb, en, smem_dyn, status);
+        else jac_batch_problem<64>(pb, en, smem_dyn, status);
         __syncthreads();
     }
 }
@@ -411,10 +432,10 @@ k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__rest
 
 // Shared memory of the Jacobian kernel with CW columns per warpgroup; 0 if
 // it (or its tensor memory) does not fit.
-size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW) {
+size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW, int NWG) {
     if (CW < jac_slots(r)) return 0;
-    const JacLayout L = jac_layout(r, width, depth, CW);
-    if (jac_halves(width) * kWG * CW > 512) return 0;           // tensor memory columns
+    const JacLayout L = jac_layout(r, width, depth, CW, NWG);
+    if (jac_halves(width) * NWG * CW > 512) return 0;           // tensor memory columns
     if ((size_t)L.total + sizeof(GnFF) + 64 > (size_t)kMaxSmem) return 0;
     return (size_t)L.total;
 }
@@ -481,19 +502,14 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
 
 int jac_points_per_cta_tile(int r) { return jac_points(r); }
 
-// Columns per warpgroup for a batched problem: at least 16, else the
-// narrowest tile that holds a point's value and tangent slots.  A layer's
-// products cost about the same per instruction issue up to 128 columns, so 16
-// columns (16 points at r <= 7) measured 3.5 % faster on the 256-scene batch
-// than 8; 32 columns spill registers and were no faster per point.
-#ifndef NSF_BATCH_MIN_CW
-#define NSF_BATCH_MIN_CW 16
-#endif
+// Columns per warpgroup of a batched problem (four warpgroups per CTA): 64 if
+// the operands fit (a 256-slot tile), else 32; 0 if neither fits.
 int jac_batch_cw(int r, int width, int depth) {
-    for (int cw = NSF_BATCH_MIN_CW; cw <= 32; cw <<= 1)
-        if (jac_tc_smem_bytes_cw(r, width, depth, cw)) return cw;
+    for (int cw = 64; cw >= 32; cw >>= 1)
+        if (jac_tc_smem_bytes_cw(r, width, depth, cw, kBatchWG)) return cw;
     return 0;
 }
+int jac_batch_points(int r, int cw) { return kBatchWG * cw / jac_slots(r); }
 
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
                              const int *cta_entry, int nctas, size_t smem, int *status,
@@ -503,7 +519,7 @@ cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *en
     set_max_dynamic_smem(k_jac_batch, done);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nctas);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kBatchWG * kWgThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
