@@ -2,6 +2,7 @@
 // packing, workspace layout and the launch sequence of each call.
 #include <algorithm>
 #include <cmath>
+#include <queue>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -879,10 +880,13 @@ WidthPlan plan_width(int W, int n, const nsf_latent_batch_item *items, bool with
     return P;
 }
 
-// Gauss-Newton CTA schedule: a scene whose cost is above 1.15 CTA shares gets
-// ceil(cost / 1.15 shares) dedicated CTAs (a group that combines its sums
-// behind the scene's barrier); the others are packed whole onto the remaining
-// CTAs, longest first, each onto the least loaded CTA.
+// Gauss-Newton CTA schedule.  A scene whose cost is above a threshold T is
+// split over ceil(cost / T) CTAs (a group that combines its sums behind the
+// scene's barrier) and is the FIRST entry of each of them, so that every
+// member of a group reaches the group's barriers while inside that scene.
+// The other scenes are then packed whole, longest first, each after the least
+// loaded CTA's entries.  T is searched between half a CTA share and two
+// shares for the smallest estimated makespan.
 struct GnPlan {
     std::vector<int> cw;
     std::vector<GnBatchEntry> entries;
@@ -897,6 +901,19 @@ int jac_slots_host(int r) {
     return L;
 }
 
+// Relative cost of one point through one layer of the batched Jacobian kernel
+// with L slots a point.  A 256-slot tile costs about the same at every L, so
+// per point the cost grows with L; the normal-equation sums (r(r+1)/2 terms a
+// point) add a little more at large r.  Fitted to GB300 timings of single-CTA
+// scenes: 1 : 2.2 : 4.8 for L = 8, 16, 32.
+double jac_point_layer_cost(int L) {
+    return (double)L / 8.0 * (1.0 + 0.1 * std::log2((double)L / 8.0));
+}
+
+// A scene split over g CTAs costs each of them a little more than cost / g
+// (its group barriers and the combine of its sums).
+constexpr double kGnSplitOverhead = 1.03;
+
 GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
     GnPlan G;
     std::vector<double> cost(n);
@@ -909,67 +926,74 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
         G.cw.push_back(cw);
         const int P = jac_batch_points(d.r, cw);
         tiles[s] = (items[s].scene.n_S + P - 1) / P;
-        // measured: a tile's pass through one layer costs about the same for
-        // any width up to 128 (products have M = 128 neuron rows; one neuron
-        // per thread), twice that above; per point it scales with the slots
-        const int L = jac_slots_host(d.r);
-        cost[s] = (double)items[s].scene.n_S * (D + 1) * L * (W > 128 ? 2.0 : 1.0);
+        // a group is no larger than the scene's Gauss-Newton slots hold
+        const int slots = jac_grid_size_tc(items[s].fields->dev, items[s].scene.n_S);
+        if (tiles[s] > slots) tiles[s] = slots;
+        // products have M = 128 neuron rows, so widths up to 128 cost the
+        // same per layer and wider ones twice that
+        cost[s] = (double)items[s].scene.n_S * (D + 1) * jac_point_layer_cost(jac_slots_host(d.r)) *
+                  (W > 128 ? 2.0 : 1.0);
         total += cost[s];
         const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw, 4);
         G.smem = sm > G.smem ? sm : G.smem;
     }
     const int cap = sms < kGnMaxCtas ? sms : kGnMaxCtas;
     const double share = total / cap;
-    std::vector<int> group(n, 0);
-    int used = 0, nsmall = 0;
-    // a scene above 1.15 shares is split so that no CTA carries more than
-    // about 1.15 shares of the whole run
-    const double unit = 1.15 * share;
-    for (int s = 0; s < n; ++s) {
-        int g = cost[s] > unit ? (int)std::ceil(cost[s] / unit) : 1;
-        if (g > tiles[s]) g = tiles[s];
-        if (g > cap) g = cap;
-        if (g >= 2) {
-            group[s] = g;
-            used += g;
-        } else {
-            ++nsmall;
-        }
-    }
-    // leave at least one CTA for the small scenes
-    while (used > cap - (nsmall > 0 ? 1 : 0)) {
-        int big = -1;
-        for (int s = 0; s < n; ++s)
-            if (group[s] >= 2 && (big < 0 || group[s] > group[big])) big = s;
-        if (group[big] == 2) {
-            group[big] = 0;
-            used -= 2;
-            ++nsmall;
-        } else {
-            --group[big];
-            --used;
-        }
-    }
-    std::vector<std::vector<GnBatchEntry>> per;
-    for (int s = 0; s < n; ++s)
-        for (int k = 0; k < group[s]; ++k) per.push_back({GnBatchEntry{s, k, group[s]}});
-    int room = cap - used;
-    if (nsmall > 0) {
-        const int m = nsmall < room ? nsmall : room;
-        std::vector<int> order;
-        for (int s = 0; s < n; ++s)
-            if (group[s] < 2) order.push_back(s);
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-        std::vector<double> load(m, 0.0);
-        std::vector<std::vector<GnBatchEntry>> small(m);
+    std::vector<int> order(n);
+    for (int s = 0; s < n; ++s) order[s] = s;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+    // the plan for threshold T and its estimated makespan
+    auto plan_for = [&](double T, std::vector<std::vector<GnBatchEntry>> &per) -> double {
+        per.assign(cap, {});
+        std::vector<double> load(cap, 0.0);
+        std::vector<int> group(n, 1);
+        int used = 0;
         for (int s : order) {
-            int best = 0;
-            for (int c = 1; c < m; ++c)
-                if (load[c] < load[best]) best = c;
-            load[best] += cost[s];
-            small[best].push_back(GnBatchEntry{s, 0, 1});
+            if (cost[s] <= T) continue;
+            int g = (int)std::ceil(cost[s] / T);
+            if (g > tiles[s]) g = tiles[s];
+            if (g < 2 || used + g > cap) continue;
+            group[s] = g;
+            for (int k = 0; k < g; ++k) {
+                per[used + k].push_back(GnBatchEntry{s, k, g});
+                load[used + k] = cost[s] / g * kGnSplitOverhead;
+            }
+            used += g;
         }
-        for (auto &v : small) per.push_back(v);
+        // least loaded CTA first (min-heap on load, then index)
+        using Slot = std::pair<double, int>;
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int c = 0; c < cap; ++c) heap.push({load[c], c});
+        for (int s : order) {
+            if (group[s] > 1) continue;
+            Slot top = heap.top();
+            heap.pop();
+            per[top.second].push_back(GnBatchEntry{s, 0, 1});
+            top.first += cost[s];
+            heap.push(top);
+        }
+        double span = 0.0;
+        for (int c = 0; c < cap; ++c) span = std::max(span, load[c]);
+        while (!heap.empty()) {
+            span = std::max(span, heap.top().first);
+            heap.pop();
+        }
+        // CTAs without entries are not launched
+        per.erase(std::remove_if(per.begin(), per.end(),
+                                 [](const std::vector<GnBatchEntry> &v) { return v.empty(); }),
+                  per.end());
+        return span;
+    };
+
+    std::vector<std::vector<GnBatchEntry>> per, trial;
+    double best = plan_for(share, per);
+    for (int k = 0; k <= 150; ++k) {
+        const double span = plan_for(share * (0.5 + 0.01 * k), trial);
+        if (span < best) {
+            best = span;
+            per.swap(trial);
+        }
     }
     G.nctas = (int)per.size();
     G.cta_entry.push_back(0);

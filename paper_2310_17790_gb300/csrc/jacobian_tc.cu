@@ -407,9 +407,10 @@ __device__ __forceinline__ void jac_batch_problem(const GnBatchProblem &pb, cons
 
 // Batched Gauss-Newton: CTA c runs the problems of its entries
 // cta_entry[c] .. cta_entry[c + 1] - 1 in order; an entry names a problem, the
-// CTA's rank in that problem's CTA group and the group size.  A CTA that
-// shares a problem with others (group size > 1) has no other entry, so the
-// group barriers of different problems never wait on each other.  The CTAs
+// CTA's rank in that problem's CTA group and the group size.  A problem
+// shared by a group of CTAs (group size > 1) is the first entry of each of
+// them, so every member reaches the group's barriers inside that problem and
+// no barrier waits on a CTA that is still busy with another problem.  The CTAs
 // have four warpgroups of 32 or 64 columns: tiles of up to 256 point slots,
 // whose products take as many tcgen05.mma instructions as the single-problem
 // kernel's 64-slot tiles (a layer's instructions cost about the same per
