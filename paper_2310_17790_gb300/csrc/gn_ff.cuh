@@ -58,12 +58,6 @@ __device__ __forceinline__ void gn_tri_pair(int e, int r, int &i, int &j) {
     j = ii + (e - off);
 }
 
-__device__ __forceinline__ ff ff_dot3(const float *a, const float *b) {
-    ff s = ff_prod(a[0], b[0]);
-    s = ff_add(s, ff_prod(a[1], b[1]));
-    return ff_add(s, ff_prod(a[2], b[2]));
-}
-
 // Start of a run: z from global memory, CTA sums cleared.
 __device__ inline void gn_ff_begin(const GnArgs &g, int r) {
     GnFF &sh = g_gn;
@@ -77,25 +71,46 @@ __device__ inline void gn_ff_begin(const GnArgs &g, int r) {
     for (int e = tid; e < gn_stride(r); e += blockDim.x) sh.part[e] = ff{0.f, 0.f};
 }
 
-// Step 1 for one tile: point q's residual is O3 row q L, its Jacobian column
-// k O3 row q L + 1 + k (three values per row); npts points are live.  Every
-// thread calls.
+// Step 1 for one tile whose point q has L slots, columns q L .. q L + L - 1
+// (npts points live): output a of column c is O3[3 c + c / 8 + a], slot 0
+// the residual and slot 1 + k the Jacobian column d/dz_k.  The pad after
+// every 8 columns puts the same entry of consecutive points (3 L + L / 8
+// floats apart) in distinct banks for the lanes of one group of G; a warp
+// takes 32 / G entries at a time, so tiles of few points still use all
+// lanes.  Every thread calls.
 __device__ __noinline__ void gn_ff_tile_partials(const float *O3, int L, int npts, int r) {
     GnFF &sh = g_gn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int T = r * (r + 1) / 2, S = gn_stride(r);
-    for (int e = warp; e < S; e += nwarps) {
-        int i = -1, j = -1;
-        if (e < T) gn_tri_pair(e, r, i, j);
-        ff acc{0.f, 0.f};
-        for (int q = lane; q < npts; q += 32) {
-            const float *res = O3 + q * L * 3;
-            if (e < T) acc = ff_add(acc, ff_dot3(res + (1 + i) * 3, res + (1 + j) * 3));
-            else if (e < T + r) acc = ff_add(acc, ff_dot3(res + (1 + e - T) * 3, res));
-            else acc = ff_add(acc, ff_dot3(res, res));
+    int G = 1;
+    while (G < npts && G < 32) G <<= 1;
+    const int per = 32 / G, sub = lane / G, ql = lane - sub * G;
+    for (int e0 = warp * per; e0 < S; e0 += nwarps * per) {
+        const int e = e0 + sub;
+        // rows of the two factors: slot 1 + i against slot 1 + j (J^T J),
+        // slot 1 + k against the residual (J^T r), the residual against itself
+        int si = 0, sj = 0;
+        if (e < T) {
+            int i, j;
+            gn_tri_pair(e, r, i, j);
+            si = 1 + i;
+            sj = 1 + j;
+        } else if (e < T + r) {
+            si = 1 + e - T;
         }
-        acc = npts <= 16 ? ff_half_warp_sum(acc) : ff_warp_sum(acc);
-        if (lane == 0) sh.part[e] = ff_add(sh.part[e], acc);
+        ff acc{0.f, 0.f};
+        if (e < S) {
+            for (int q = ql; q < npts; q += G) {
+                const int ca = q * L + si, cb = q * L + sj;
+                const float *ra = O3 + 3 * ca + (ca >> 3), *rb = O3 + 3 * cb + (cb >> 3);
+                ff d = ff_prod(ra[0], rb[0]);
+                d = ff_add(d, ff_prod(ra[1], rb[1]));
+                d = ff_add(d, ff_prod(ra[2], rb[2]));
+                acc = ff_add(acc, d);
+            }
+        }
+        for (int m = G >> 1; m >= 1; m >>= 1) acc = ff_add(acc, ff_shfl_xor(acc, m));
+        if (ql == 0 && e < S) sh.part[e] = ff_add(sh.part[e], acc);
     }
 }
 

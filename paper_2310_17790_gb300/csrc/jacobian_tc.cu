@@ -78,7 +78,7 @@ __host__ __device__ inline JacLayout jac_layout(int r, int W, int D, int CW, int
     L.bias = o; o = align_to(o + D * W * 4, 16);               // hidden biases, output bias
     L.xs = o;   o = align_to(o + P * 16, 16);                  // tile positions
     L.tg = o;   o = align_to(o + P * 16, 16);                  // tile Gauss-Newton targets
-    L.o3 = o;   o = align_to(o + N * 3 * 4, 16);               // outputs per column
+    L.o3 = o;   o = align_to(o + (3 * N + N / 8) * 4, 16);     // outputs, a pad per 8 columns
     L.bars = o; o = align_to(o + 2 * 8, 16);
     L.tmem = o; o = align_to(o + 16, 16);
     L.total = o + 1024;
@@ -320,6 +320,9 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                             const int a = lane;
                             const float sc = F.scale[a], sh = F.shift[a];
                             const float bo = bias[(D - 1) * W + a];
+                            // n0 + c0 is a multiple of 8: the pads of this
+                            // chunk sit at fixed offsets from its start
+                            float *o3 = O3 + (n0 + c0) * 3 + ((n0 + c0) >> 3) + a;
 #pragma unroll
                             for (int c = 0; c < kC; ++c) {
                                 const int col = n0 + c0 + c;
@@ -336,7 +339,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                                     }
                                 }
                                 if (valid && s > 0 && dudz) dudz[(size_t)(a * r + s - 1) * ld + p] = y;
-                                O3[col * 3 + a] = valid ? y : 0.f;
+                                o3[c * 3 + (c >> 3)] = valid ? y : 0.f;
                             }
                         }
                     }
