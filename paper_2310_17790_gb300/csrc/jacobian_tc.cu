@@ -103,6 +103,69 @@ __device__ __forceinline__ void store_b_row(uint8_t *B, int k, int n0, int sbo, 
 // `rank` of the `gsize` CTAs that work on this point set (tiles rank, rank +
 // gsize, ...) and, for Gauss-Newton, combine their sums behind gn.bar.  The
 // CTA has NWG warpgroups of CW columns each (a tile of NWG CW point slots).
+// Input-layer epilogue of one chunk of kC columns holding kC / LT whole
+// points of LT slots: the value slot of a point is ELU(a), a = W0 [x; z] + b0
+// (the z part folded into w.w), tangent slot s (1 <= s <= r) is
+// ELU'(a) W0[:, 3 + s - 1], the slots past r are zero.  w0t points at this
+// neuron's entry of the first z column of W0 (columns W apart); x at the
+// chunk's first point.
+template <int kC, int LT>
+__device__ __forceinline__ void input_tangents(float *v, float4 w, const float4 *x, const float *w0t,
+                                               int W, int r) {
+    float t[LT];
+    t[0] = 0.f;
+#pragma unroll
+    for (int s = 1; s < LT; ++s) t[s] = s <= r ? w0t[(s - 1) * W] : 0.f;
+#pragma unroll
+    for (int p = 0; p < kC; p += LT) {
+        const float4 xp = x[p / LT];
+        float g;
+        v[p] = elu_fast(fmaf(w.x, xp.x, fmaf(w.y, xp.y, fmaf(w.z, xp.z, w.w))), g);
+#pragma unroll
+        for (int s = 1; s < LT; ++s) v[p + s] = g * t[s];
+    }
+}
+
+// Hidden-layer epilogue of one chunk: ELU on each point's value slot (sum +
+// bias b) and the chain rule ELU'(a) (W dh/dz) on its tangent slots.  Slots
+// past r hold exact zeros (zero columns in, zero products out) and stay zero.
+template <int kC, int LT>
+__device__ __forceinline__ void elu_tangents(float *v, float b) {
+#pragma unroll
+    for (int p = 0; p < kC; p += LT) {
+        float g;
+        v[p] = elu_fast(v[p] + b, g);
+        v[p + 1] *= g;
+#pragma unroll
+        for (int s = 2; s < LT; s += 2) {
+            const float2 t = __fmul2_rn(make_float2(v[p + s], v[p + s + 1]), make_float2(g, g));
+            v[p + s] = t.x;
+            v[p + s + 1] = t.y;
+        }
+    }
+}
+
+// The two epilogues for the run-time slot count L (a power of two, 2 <= L <=
+// kC): one uniform branch per chunk, straight-line code inside.
+template <int kC>
+__device__ __forceinline__ void input_tangents_l(int L, float *v, float4 w, const float4 *x,
+                                                 const float *w0t, int W, int r) {
+    if (L == 2) input_tangents<kC, 2>(v, w, x, w0t, W, r);
+    else if (L == 4) input_tangents<kC, 4>(v, w, x, w0t, W, r);
+    else if (L == 8) input_tangents<kC, 8>(v, w, x, w0t, W, r);
+    else if (L == 16) { if constexpr (kC >= 16) input_tangents<kC, 16>(v, w, x, w0t, W, r); }
+    else { if constexpr (kC >= 32) input_tangents<kC, 32>(v, w, x, w0t, W, r); }
+}
+
+template <int kC>
+__device__ __forceinline__ void elu_tangents_l(int L, float *v, float b) {
+    if (L == 2) elu_tangents<kC, 2>(v, b);
+    else if (L == 4) elu_tangents<kC, 4>(v, b);
+    else if (L == 8) elu_tangents<kC, 8>(v, b);
+    else if (L == 16) { if constexpr (kC >= 16) elu_tangents<kC, 16>(v, b); }
+    else { if constexpr (kC >= 32) elu_tangents<kC, 32>(v, b); }
+}
+
 template <int CW, int NWG = kWG>
 __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n, int ld,
                          const double *zj, float *u, float *dudz, const GnArgs &gn, int gn_on,
@@ -221,17 +284,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
 #pragma unroll
                     for (int c0 = 0; c0 < CW; c0 += kC0) {
                         float v[kC0];
-                        float g = 0.f;
-#pragma unroll
-                        for (int c = 0; c < kC0; ++c) {
-                            const int s = c & (L - 1);
-                            if (s == 0) {
-                                const float4 x = xs[(n0 + c0 + c) >> lgL];
-                                v[c] = elu_fast(fmaf(w.x, x.x, fmaf(w.y, x.y, fmaf(w.z, x.z, w.w))), g);
-                            } else {
-                                v[c] = s <= r ? g * W0t[(s - 1) * W + j] : 0.f;
-                            }
-                        }
+                        input_tangents_l<kC0>(L, v, w, xs + ((n0 + c0) >> lgL), W0t + j, W, r);
                         store_b_row<kC0>(B, j, n0 + c0, sbo_b, v);
                     }
                 }
@@ -291,13 +344,7 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                                 for (int g8 = 0; g8 < kC / 8; ++g8)
                                     tmem_ld8(tq + (uint32_t)(h * N + n0 + c0 + 8 * g8), v + 8 * g8);
                                 tmem_wait_ld();
-                                float g = 0.f;
-#pragma unroll
-                                for (int c = 0; c < kC; ++c) {
-                                    const int s = c & (L - 1);
-                                    if (s == 0) v[c] = elu_fast(v[c] + b, g);
-                                    else v[c] = s <= r ? g * v[c] : 0.f;
-                                }
+                                elu_tangents_l<kC>(L, v, b);
                                 store_b_row<kC>(B, j, n0 + c0, sbo_b, v);
                             }
                         }
@@ -306,45 +353,51 @@ __device__ void jac_body(const FieldsDev &fd, const float *__restrict__ X, int n
                     fence_proxy_async();
                     __syncthreads();
                 } else {
-                    bool bad = false;
+                    // output layer: rows 0-2 (the three outputs) sit in TMEM
+                    // lanes 0-2, which only warp 0 of a warpgroup reads; it
+                    // parks the raw sums of its columns in O3, then every
+                    // thread finishes whole entries (one column, one output)
                     constexpr int kC = CW < 32 ? CW : 32;
-#pragma unroll
-                    for (int c0 = 0; c0 < CW; c0 += kC) {
                     if (wq == 0) {
-                        float v[kC];
 #pragma unroll
-                        for (int g8 = 0; g8 < kC / 8; ++g8)
-                            tmem_ld8(tq + (uint32_t)(n0 + c0 + 8 * g8), v + 8 * g8);
-                        tmem_wait_ld();
-                        if (lane < 3) {
-                            const int a = lane;
-                            const float sc = F.scale[a], sh = F.shift[a];
-                            const float bo = bias[(D - 1) * W + a];
-                            // n0 + c0 is a multiple of 8: the pads of this
-                            // chunk sit at fixed offsets from its start
-                            float *o3 = O3 + (n0 + c0) * 3 + ((n0 + c0) >> 3) + a;
+                        for (int c0 = 0; c0 < CW; c0 += kC) {
+                            float v[kC];
 #pragma unroll
-                            for (int c = 0; c < kC; ++c) {
-                                const int col = n0 + c0 + c;
-                                const int s = col & (L - 1);
-                                const int p = p0 + (col >> lgL);
-                                const bool valid = p < n && s <= r;
-                                float y = s == 0 ? fmaf(sc, v[c] + bo, sh) : sc * v[c];
-                                if (valid) bad |= !isfinite(y);
-                                if (valid && s == 0) {
-                                    if (u) u[(size_t)a * ld + p] = y;
-                                    if (gn_on) {
-                                        const float4 t = tg[col >> lgL];
-                                        y -= a == 0 ? t.x : (a == 1 ? t.y : t.z);
-                                    }
-                                }
-                                if (valid && s > 0 && dudz) dudz[(size_t)(a * r + s - 1) * ld + p] = y;
-                                o3[c * 3 + (c >> 3)] = valid ? y : 0.f;
+                            for (int g8 = 0; g8 < kC / 8; ++g8)
+                                tmem_ld8(tq + (uint32_t)(n0 + c0 + 8 * g8), v + 8 * g8);
+                            tmem_wait_ld();
+                            if (lane < 3) {
+                                // n0 + c0 is a multiple of 8: the pads of this
+                                // chunk sit at fixed offsets from its start
+                                float *o3 = O3 + (n0 + c0) * 3 + ((n0 + c0) >> 3) + lane;
+#pragma unroll
+                                for (int c = 0; c < kC; ++c) o3[c * 3 + (c >> 3)] = v[c];
                             }
                         }
                     }
-                    }
                     tc_fence_before();
+                    __syncthreads();
+                    bool bad = false;
+                    for (int e = tid; e < 3 * N; e += NWG * kWgThreads) {
+                        const int col = e / 3, a = e - 3 * col;
+                        const int s = col & (L - 1);
+                        const int p = p0 + (col >> lgL);
+                        const bool valid = p < n && s <= r;
+                        float *o = O3 + col * 3 + (col >> 3) + a;
+                        const float v = *o;
+                        const float sc = F.scale[a];
+                        float y = s == 0 ? fmaf(sc, v + bias[(D - 1) * W + a], F.shift[a]) : sc * v;
+                        if (valid) bad |= !isfinite(y);
+                        if (valid && s == 0) {
+                            if (u) u[(size_t)a * ld + p] = y;
+                            if (gn_on) {
+                                const float4 t = tg[col >> lgL];
+                                y -= a == 0 ? t.x : (a == 1 ? t.y : t.z);
+                            }
+                        }
+                        if (valid && s > 0 && dudz) dudz[(size_t)(a * r + s - 1) * ld + p] = y;
+                        *o = valid ? y : 0.f;
+                    }
                     if (bad) set_status(status, NSF_ERR_NONFINITE);
                     __syncthreads();
                     if (gn_on) {
