@@ -221,55 +221,73 @@ __device__ void phase_activate(const GridWs &g, int np, int epoch) {
 }
 
 // --------------------------------------------------------------- grid ----
-// Node l (0 .. 63) of active grid block number idx of the step.
-__device__ __forceinline__ void grid_node(const GridWs &g, const GridParams &gp, float dt,
-                                          double blade_z, int idx, int l, float *tap_mp,
-                                          float *tap_v) {
+// Node l (0 .. 63) of active grid block gb, whose accumulated (m, m v) is a:
+// velocity update (gravity, walls, blade) into g.vel, and the accumulator
+// cleared for the next step's P2G (skipped when it already holds zeros: in a
+// sparse scene most nodes of an active block were not touched).
+__device__ __forceinline__ void grid_node_update(const GridWs &g, const GridParams &gp, float dt,
+                                                 double blade_z, int gb, int l, float4 a,
+                                                 float *tap_mp, float *tap_v) {
     const int lx = l >> 4, ly = (l >> 2) & 3, lz = l & 3;
-    {
-        const int gb = __ldcg(&g.glist[idx]);
-        const int bz = gb % g.nb2, tt = gb / g.nb2, by = tt % g.nb1, bx = tt / g.nb1;
-        const int i = bx * 4 + lx, j = by * 4 + ly, k = bz * 4 + lz;
-        const int addr = gb * 64 + l;
-        const float4 a = __ldcg(&g.acc[addr]);
-        g.acc[addr] = make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 v = make_float4(0.f, 0.f, 0.f, a.x);
-        if (a.x > 0.f) {
-            const float im = 1.f / a.x;
-            v.x = a.y * im + dt * gp.gx;
-            v.y = a.z * im + dt * gp.gy;
-            v.z = a.w * im + dt * gp.gz;
-            const int wc = gp.wall_cells;
-            if (wc > 0) {
-                if ((i < wc && v.x < 0.f) || (i > g.n0 - 1 - wc && v.x > 0.f)) v.x = 0.f;
-                if ((j < wc && v.y < 0.f) || (j > g.n1 - 1 - wc && v.y > 0.f)) v.y = 0.f;
-                if ((k < wc && v.z < 0.f) || (k > g.n2 - 1 - wc && v.z > 0.f)) v.z = 0.f;
-            }
-            if (gp.blade_enable) {
-                const float xi = (float)i * gp.dx;
-                const double zi = (double)k * (double)gp.dx;
-                if (fabsf(xi - gp.blade_x) < gp.dx && zi > blade_z) {
-                    v.x = 0.f;
-                    v.y = 0.f;
-                    v.z = gp.blade_vz;
-                }
+    const int bz = gb % g.nb2, tt = gb / g.nb2, by = tt % g.nb1, bx = tt / g.nb1;
+    const int i = bx * 4 + lx, j = by * 4 + ly, k = bz * 4 + lz;
+    const int addr = gb * 64 + l;
+    if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) g.acc[addr] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = make_float4(0.f, 0.f, 0.f, a.x);
+    if (a.x > 0.f) {
+        const float im = 1.f / a.x;
+        v.x = a.y * im + dt * gp.gx;
+        v.y = a.z * im + dt * gp.gy;
+        v.z = a.w * im + dt * gp.gz;
+        const int wc = gp.wall_cells;
+        if (wc > 0) {
+            if ((i < wc && v.x < 0.f) || (i > g.n0 - 1 - wc && v.x > 0.f)) v.x = 0.f;
+            if ((j < wc && v.y < 0.f) || (j > g.n1 - 1 - wc && v.y > 0.f)) v.y = 0.f;
+            if ((k < wc && v.z < 0.f) || (k > g.n2 - 1 - wc && v.z > 0.f)) v.z = 0.f;
+        }
+        if (gp.blade_enable) {
+            const float xi = (float)i * gp.dx;
+            const double zi = (double)k * (double)gp.dx;
+            if (fabsf(xi - gp.blade_x) < gp.dx && zi > blade_z) {
+                v.x = 0.f;
+                v.y = 0.f;
+                v.z = gp.blade_vz;
             }
         }
-        g.vel[addr] = v;
-        const size_t nat = (((size_t)i * g.n1 + j) * g.n2 + k) * 4;
-        if (tap_mp) *reinterpret_cast<float4 *>(tap_mp + nat) = a;
-        if (tap_v) *reinterpret_cast<float4 *>(tap_v + nat) = v;
     }
+    g.vel[addr] = v;
+    const size_t nat = (((size_t)i * g.n1 + j) * g.n2 + k) * 4;
+    if (tap_mp) *reinterpret_cast<float4 *>(tap_mp + nat) = a;
+    if (tap_v) *reinterpret_cast<float4 *>(tap_v + nat) = v;
 }
+
+// Grid blocks a thread updates per pass: their index and node loads are
+// issued together, so a thread has kGridUnroll memory chains in flight
+// instead of one.
+constexpr int kGridUnroll = 4;
 
 __device__ void phase_grid(const GridWs &g, const GridParams &gp, float dt, double t,
                            float *tap_mp, float *tap_v) {
     const int ngb = __ldcg(&g.ctl->n_g_atomic);
     const int per = blockDim.x >> 6;                 // grid blocks per CTA pass
     const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+    const int stride = gridDim.x * per;
     const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
-    for (int idx = sub * gridDim.x + blockIdx.x; idx < ngb; idx += gridDim.x * per)
-        grid_node(g, gp, dt, blade_z, idx, l, tap_mp, tap_v);
+    for (int i0 = sub * gridDim.x + blockIdx.x; i0 < ngb; i0 += kGridUnroll * stride) {
+        int gb[kGridUnroll];
+        float4 a[kGridUnroll];
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u) {
+            const int idx = i0 + u * stride;
+            gb[u] = idx < ngb ? __ldcg(&g.glist[idx]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u)
+            if (gb[u] >= 0) a[u] = __ldcg(&g.acc[gb[u] * 64 + l]);
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u)
+            if (gb[u] >= 0) grid_node_update(g, gp, dt, blade_z, gb[u], l, a[u], tap_mp, tap_v);
+    }
 }
 
 // ---------------------------------------------------------------- G2P ----
@@ -527,7 +545,7 @@ __device__ __forceinline__ P2gLatentArgs latent_args(const BatchSceneDev &sc, in
 // once (a flat index over the scenes' particles, active particle blocks,
 // active grid blocks and sample particles), with one grid barrier between
 // phases for the whole batch.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_mpm_batch(MpmBatchArgs b, int *status) {
     __shared__ int off[kMaxBatchScenes + 1];
     const int ns = b.nscenes;
@@ -571,12 +589,30 @@ k_mpm_batch(MpmBatchArgs b, int *status) {
     {
         const int per = blockDim.x >> 6;
         const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
-        for (int u = sub * gridDim.x + blockIdx.x; u < off[ns]; u += gridDim.x * per) {
-            const int sidx = find_scene(off, ns, u);
-            const BatchSceneDev &sc = b.scenes[sidx];
-            const double t = b.t0 + (double)b.step * (double)sc.dt;
-            const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
-            grid_node(sc.g, sc.gp, sc.dt, blade_z, u - off[sidx], l, nullptr, nullptr);
+        const int nblk = off[ns], gstride = gridDim.x * per;
+        for (int u0 = sub * gridDim.x + blockIdx.x; u0 < nblk; u0 += kGridUnroll * gstride) {
+            int sidx[kGridUnroll], gb[kGridUnroll];
+            float4 a[kGridUnroll];
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k) {
+                const int u = u0 + k * gstride;
+                sidx[k] = -1;
+                if (u < nblk) {
+                    sidx[k] = find_scene(off, ns, u);
+                    gb[k] = __ldcg(&b.scenes[sidx[k]].g.glist[u - off[sidx[k]]]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k)
+                if (sidx[k] >= 0) a[k] = __ldcg(&b.scenes[sidx[k]].g.acc[gb[k] * 64 + l]);
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k) {
+                if (sidx[k] < 0) continue;
+                const BatchSceneDev &sc = b.scenes[sidx[k]];
+                const double t = b.t0 + (double)b.step * (double)sc.dt;
+                const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
+                grid_node_update(sc.g, sc.gp, sc.dt, blade_z, gb[k], l, a[k], nullptr, nullptr);
+            }
         }
     }
     if (!grid_barrier(b.bar, status)) return;
