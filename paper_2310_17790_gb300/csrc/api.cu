@@ -902,12 +902,13 @@ int jac_slots_host(int r) {
 }
 
 // Relative cost of one point through one layer of the batched Jacobian kernel
-// with L slots a point.  A 256-slot tile costs about the same at every L, so
-// per point the cost grows with L; the normal-equation sums (r(r+1)/2 terms a
-// point) add a little more at large r.  Fitted to GB300 timings of single-CTA
-// scenes: 1 : 2.2 : 4.8 for L = 8, 16, 32.
-double jac_point_layer_cost(int L) {
-    return (double)L / 8.0 * (1.0 + 0.1 * std::log2((double)L / 8.0));
+// with L slots a point and hidden width W.  A 256-slot tile costs about the
+// same at every L, so per point the cost follows L; widths above 64 add
+// ~14 % (a longer product), above 128 twice that again (a second 128-neuron
+// product).  Fitted to GB300 timings of single-CTA scenes: 1 : 1.97 : 3.89
+// for L = 8, 16, 32 at W = 64, and 1.10 : 2.30 : 4.41 at W = 128.
+double jac_point_layer_cost(int L, int W) {
+    return (double)L / 8.0 * (W > 64 ? 1.14 : 1.0) * (W > 128 ? 2.0 : 1.0);
 }
 
 // A scene split over g CTAs costs each of them a little more than cost / g
@@ -929,10 +930,7 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
         // a group is no larger than the scene's Gauss-Newton slots hold
         const int slots = jac_grid_size_tc(items[s].fields->dev, items[s].scene.n_S);
         if (tiles[s] > slots) tiles[s] = slots;
-        // products have M = 128 neuron rows, so widths up to 128 cost the
-        // same per layer and wider ones twice that
-        cost[s] = (double)items[s].scene.n_S * (D + 1) * jac_point_layer_cost(jac_slots_host(d.r)) *
-                  (W > 128 ? 2.0 : 1.0);
+        cost[s] = (double)items[s].scene.n_S * (D + 1) * jac_point_layer_cost(jac_slots_host(d.r), W);
         total += cost[s];
         const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw, 4);
         G.smem = sm > G.smem ? sm : G.smem;
