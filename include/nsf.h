@@ -54,7 +54,7 @@ typedef enum nsf_status {
     NSF_ERR_NONFINITE = -4,     /* device: NaN or Inf in a field output       */
     NSF_ERR_SINGULAR = -5,      /* device: Gauss-Newton matrix not SPD        */
     NSF_ERR_ITER_CAP = -6,      /* device: a bounded wait gave up             */
-    NSF_ERR_UNSUPPORTED = -7,   /* valid request this build does not provide  */
+    NSF_ERR_UNSUPPORTED = -7,   /* valid request the library does not provide */
     NSF_ERR_NO_MEMORY = -8,     /* nsf_create_fields could not allocate       */
     NSF_ERR_WORKSPACE = -9      /* workspace pointer NULL or too small        */
 } nsf_status;
