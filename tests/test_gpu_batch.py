@@ -162,3 +162,39 @@ def test_batch_two_steps_in_one_call_match_two_calls(nsf):
     for i in range(len(scenes)):
         assert _close(one_call[0][i][0], two_calls[1][i][0]), i
         assert _close(one_call[0][i][1], two_calls[1][i][1]), i
+
+
+def test_full_size_batch_sampled_scenes_match_single_steps(nsf):
+    """The 256-scene batch the bench times (1.50 M integration / 160 k sample
+    particles: the same plan and launches), one step; in every (r, width)
+    class the scene with the fewest and the one with the most sample
+    particles (the latter split over a group of CTAs) checked against its own
+    single-scene step by the criteria above."""
+    from scenes.synthetic import batch_config4
+    scenes = batch_config4()
+    rng = np.random.Generator(np.random.PCG64(2024))
+    for sc in scenes:
+        sc.z_prev = sc.z0 - 5e-2 * rng.normal(size=sc.z0.size)
+    batch = _batched(nsf, scenes, 1)
+    picks = {}
+    for i, sc in enumerate(scenes):
+        key = (sc.fields.r, sc.fields.width[0])
+        lo, hi = picks.get(key, (i, i))
+        if sc.n_S < scenes[lo].n_S:
+            lo = i
+        if sc.n_S > scenes[hi].n_S:
+            hi = i
+        picks[key] = (lo, hi)
+    sample = sorted({i for pair in picks.values() for i in pair})
+    assert len(sample) >= 6
+    for i in sample:
+        sc = scenes[i]
+        zb, zpb = batch[0][i]
+        zs, zps, f, z_in = _single(nsf, sc, 1)[0]
+        f_b, f_s, f_0 = f(zb), f(zs), f(z_in)
+        print(f"scene {i} (r {sc.fields.r}, W {sc.fields.width[0]}, S {sc.n_S}): "
+              f"|dz| {np.abs(zb - zs).max():.3e} objective start {f_0:.4e} single {f_s:.4e} "
+              f"batch {f_b:.4e}")
+        assert f_b <= f_s + OBJ_TOL * max(f_0 - f_s, 0.0) + 1e-3 * f_0, i
+        assert _close(zb, zs), (i, zb, zs)
+        np.testing.assert_array_equal(zpb, sc.z0)
