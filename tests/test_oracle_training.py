@@ -69,3 +69,29 @@ def test_adam_first_step_moves_by_lr_times_sign():
     np.testing.assert_allclose(p, -1e-3 * np.sign(g), rtol=1e-12)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_closed_form():
+    # with g fixed, m_t = g (1 - b1^t) and v_t = g^2 (1 - b2^t) (geometric
+    # sums), so the bias-corrected moments are exactly g and g^2 and every
+    # step moves by lr * sign(g): after T steps p = -T lr sign(g)
+    g = np.array([2.0, -0.25, 5e-3])
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    T, lr = 20, 1e-2
+    for t in range(1, T + 1):
+        p, m, v = training.adam_step(p, g, m, v, t, lr=lr, eps=0.0)
+        np.testing.assert_allclose(m, g * (1 - 0.9 ** t), rtol=1e-12)
+        np.testing.assert_allclose(v, g * g * (1 - 0.999 ** t), rtol=1e-12)
+    np.testing.assert_allclose(p, -T * lr * np.sign(g), rtol=1e-10)
+
+
+def test_adam_alternating_gradient_second_step_by_hand():
+    # g then -g: m_2 = 0.9 * 0.1 g - 0.1 g = -0.01 g, v_2 = (0.999 * 0.001 + 0.001) g^2
+    # = 0.001999 g^2; bias-corrected: m = -0.01 g / 0.19, v = g^2, so the second
+    # step moves p by +lr * (1 / 19) sign(g) after the first step's -lr sign(g)
+    g = np.array([4.0, -3.0])
+    p, m, v = training.adam_step(np.zeros(2), g, np.zeros(2), np.zeros(2), 1, lr=1.0, eps=0.0)
+    p, m, v = training.adam_step(p, -g, m, v, 2, lr=1.0, eps=0.0)
+    np.testing.assert_allclose(m, -0.01 * g, rtol=1e-12)
+    np.testing.assert_allclose(v, 0.001999 * g * g, rtol=1e-12)
+    np.testing.assert_allclose(p, (-1.0 + 1.0 / 19.0) * np.sign(g), rtol=1e-12)
