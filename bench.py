@@ -240,26 +240,33 @@ def run_gpu(args, rank, world, local):
     r = fs.r
     macs = [mlp_macs(r, fs.width[i], fs.depth[i], od) for i, od in enumerate((3, 6, 9))]
     n_N, n_S = sc.X.shape[0], sc.n_S
+    # Gauss-Newton: per sample point and iteration one value pass plus the
+    # cheaper of 3 reverse (VJP) and r forward (JVP) passes for dg/dz
     flops = {
         "inference": 2.0 * n_N * sum(macs),
-        "gauss_newton": 2.0 * sc.gn_iters * n_S * (1 + r) * macs[0],
+        "gauss_newton": 2.0 * sc.gn_iters * n_S * (1 + min(3, r)) * macs[0],
     }
     names = N.NSF_STAGE_NAMES
+    mpm_bytes, touched = latent_mpm_bytes([sc])
+    peak_t = peaks["bf16_tflops"] if args.precision == "bf16" else None
+    stage_roof = {}
+    for i, nm in enumerate(names):
+        if nm in flops:
+            ach = flops[nm] / (st_ms[i] / 1e3) / 1e12
+            stage_roof[nm] = {"kernel": KERNEL_OF_STAGE[nm], "bound": "tensor", "achieved": ach,
+                              "peak": peak_t, "unit": "TFLOP/s",
+                              "frac": (ach / peak_t) if peak_t else None, "work": flops[nm],
+                              "peak_source": f"bf16 dense burst, {peak_src}"}
+        else:
+            ach = mpm_bytes / (st_ms[i] / 1e3) / 1e9
+            stage_roof[nm] = {"kernel": KERNEL_OF_STAGE[nm], "bound": "hbm", "achieved": ach,
+                              "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": ach / peaks["hbm_gbs"], "work": mpm_bytes,
+                              "touched_nodes": touched,
+                              "peak_source": f"copy bandwidth, {peak_src}"}
     dom = int(np.argmax(st_ms))
-    dom_name = names[dom]
-    if dom_name in flops:
-        peak = peaks["bf16_tflops"] if args.precision == "bf16" else peaks.get("fp32_tflops", 0) or None
-        achieved = flops[dom_name] / (st_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": dom_name, "bound": "tensor", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None,
-                "peak_source": f"bf16 dense burst, {peak_src}", "traffic": None}
-    else:
-        roof = {"kernel": dom_name, "bound": "hbm", "achieved": None,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None}
-
-    traffic = load_traffic(KERNEL_OF_STAGE.get(dom_name))
-    roof["traffic"] = traffic
+    roof = dict(stage_roof[names[dom]])
+    roof["traffic"] = load_traffic(KERNEL_OF_STAGE.get(names[dom]))
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     if args.only == "latent":
         clocks.__exit__(None, None, None)
@@ -294,6 +301,7 @@ def run_gpu(args, rank, world, local):
                    "parallelism": f"replicas{world}", "graph": "one CUDA graph per step"},
         "stages_ms": {names[i]: float(st_ms[i]) for i in range(nst)},
         "roofline": roof,
+        "roofline_stages": stage_roof,
         "mlp_throughput": throughput,
         "e2e": e2e,
         "batched": batched,
@@ -304,6 +312,25 @@ def run_gpu(args, rank, world, local):
         "status": status,
     }
     return out, clocks
+
+
+def latent_mpm_bytes(scenes):
+    """Algorithmic bytes of the MPM stage of a latent step over `scenes`: P2G
+    reads X, u_n, u_{n-1}, tau, C (96 B per integration particle); every
+    touched grid node is written by P2G (16 B), read and re-zeroed by the grid
+    update (32 B) and its velocity written (16 B); G2P reads X, u_n and writes
+    x^{n+1} (36 B per sample particle).  Touched nodes: the 3^3 stencils of the
+    reference positions.  Returns (bytes, touched nodes)."""
+    touched, n_N, n_S = 0, 0, 0
+    off = np.array([(a, b, c) for a in range(3) for b in range(3) for c in range(3)])
+    for sc in scenes:
+        base = np.floor(sc.X.astype(np.float64) / sc.grid.dx - 0.5).astype(np.int64)
+        ng = sc.grid.n[0]
+        nodes = (base[:, None, :] + off[None]).reshape(-1, 3)
+        touched += np.unique((nodes[:, 0] * ng + nodes[:, 1]) * ng + nodes[:, 2]).size
+        n_N += sc.X.shape[0]
+        n_S += sc.n_S
+    return 96.0 * n_N + 64.0 * touched + 36.0 * n_S, int(touched)
 
 
 # The library's kernel that implements each latent stage.
@@ -496,20 +523,8 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
         fs = sc.fields
         macs = [mlp_macs(fs.r, fs.width[i], fs.depth[i], od) for i, od in enumerate((3, 6, 9))]
         fl_inf += 2.0 * nn * sum(macs)
-        fl_gn += 2.0 * sc.gn_iters * ns * (1 + fs.r) * macs[0]
-    # algorithmic bytes of the MPM launch: P2G reads X, u_n, u_{n-1}, tau, C
-    # (96 B per integration particle); every touched grid node is written by
-    # P2G (16 B), read and re-zeroed by the grid update (32 B) and its velocity
-    # written (16 B); G2P reads X, u_n and writes x^{n+1} (36 B per sample
-    # particle).  Touched nodes: the 3^3 stencils of the reference positions.
-    touched = 0
-    for sc in scenes:
-        base = np.floor(sc.X.astype(np.float64) / sc.grid.dx - 0.5).astype(np.int64)
-        ng = sc.grid.n[0]
-        off = np.array([(a, b, c) for a in range(3) for b in range(3) for c in range(3)])
-        nodes = (base[:, None, :] + off[None]).reshape(-1, 3)
-        touched += np.unique((nodes[:, 0] * ng + nodes[:, 1]) * ng + nodes[:, 2]).size
-    mpm_bytes = 96.0 * n_N.sum() + 64.0 * touched + 36.0 * n_S.sum()
+        fl_gn += 2.0 * sc.gn_iters * ns * (1 + min(3, fs.r)) * macs[0]
+    mpm_bytes, touched = latent_mpm_bytes(scenes)
     names = N.NSF_STAGE_NAMES
     stages = {names[i]: float(st_ms[i]) for i in range(nst)}
     pk = peaks["bf16_tflops"]

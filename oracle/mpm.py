@@ -3,7 +3,8 @@
 Paper: §3.2 (MPM discretisation; w_ip = N(x_p - x_i); the grid force of the
 node force balance, Eq. 5, is -sum_p tau_p grad(w_ip) V_p^0) and §3.3 (the
 explicit MPM algorithm: P2G with the APIC momentum, grid update with gravity
-and boundary conditions, G2P of v, x, C and the deformation-gradient update).
+and boundary conditions, G2P of v, x, C and the deformation-gradient update;
+``full_step`` composes them with the stress and return map of App. F).
 
 Conventions (shared with the library only through its documentation):
 
@@ -189,6 +190,45 @@ def g2p(x, v_grid, dt, grid, full=False, grad="mls"):
     if full:
         return xn, vp, Cp, Gp, ok
     return xn, ok
+
+
+def g2p_full(x, F, v_grid, dt, grid, material, grad="mls"):
+    """G2P of the full-order step (§3.3) and the update of F (steps 4-6 of
+    ``full_step``): v_p, x_p^{n+1}, C_p, F_trial = (I + dt grad v_p) F_p and
+    F^E = Z(F_trial), the material's return map (App. F).  Returns a dict with
+    x, v, C, F (= F^E), F_trial and in_grid."""
+    F = np.asarray(F, np.float64).reshape(-1, 3, 3)
+    x_new, v_new, C_new, G, ok = g2p(x, v_grid, dt, grid, full=True, grad=grad)
+    F_trial = np.einsum("nij,njk->nik", np.eye(3) + dt * G, F)
+    F_new = material.return_map(F_trial)
+    return dict(x=x_new, v=v_new, C=C_new, F=F_new, F_trial=F_trial, in_grid=bool(ok.all()))
+
+
+def full_step(x, v, C, F, mass, vol0, dt, grid, material, t=0.0, grad="mls"):
+    """One explicit full-order MPM step of §3.3, in the paper's order.
+
+    x, v: [n,3]; C, F: [n,3,3] (F is the elastic part F^E for the plastic
+    models); material: ``constitutive.Material``.
+      1. Kirchhoff stress tau_p = tau(F_p) of the material (App. F);
+      2. P2G of mass, APIC momentum and the stress force of Eq. 5;
+      3. grid update with gravity and the boundary conditions at time t;
+      4. G2P of v_p, x_p^{n+1} = x_p + dt v_p and C_p;
+      5. deformation-gradient update F_trial = (I + dt grad v_p) F_p, with the
+         MLS velocity gradient grad v_p = C_p (grad="mls") or the exact
+         B-spline one sum_i v_i grad(w_ip)^T (grad="bspline");
+      6. the material's return map F^E = Z(F_trial) (App. F.3, F.4; the
+         identity for the elastic models).
+    Returns a dict with the new x, v, C, F, the trial F, the grid (m, p after
+    P2G, v after the update) and in_grid (every stencil inside the grid)."""
+    x = np.asarray(x, np.float64).reshape(-1, 3)
+    F = np.asarray(F, np.float64).reshape(-1, 3, 3)
+    tau = material.stress(F)
+    m_grid, p_grid, ok = p2g(x, v, C, tau, mass, vol0, dt, grid, grad)
+    v_grid = grid_update(m_grid, p_grid, dt, grid, t)
+    out = g2p_full(x, F, v_grid, dt, grid, material, grad)
+    out.update(m_grid=m_grid, p_grid=p_grid, v_grid=v_grid,
+               in_grid=bool(ok.all() and out["in_grid"]))
+    return out
 
 
 def momentum(x, v, C, mass, dx):

@@ -65,30 +65,41 @@ GridParams make_params(const nsf_grid_desc *g) {
     return p;
 }
 
-// Grid part of a workspace.
+// Grid part of a workspace.  The particle buckets hold up to `cap` particle
+// indices per particle block (min(cap_max, n)); particles past that go to the
+// overflow list, which every grid block's P2G scans (correct, but slow if
+// large), so cap_max is set well above the densest expected packing (8
+// particles per cell fill a block with 512).
+constexpr int kBucketCapScene = 1024;
+constexpr int kBucketCapBatch = 256;
+
 struct GridLayout {
-    size_t acc, vel, gstamp, pstamp, plist, glist, ctl;
-    int nblocks, max_pblocks, max_gblocks;
+    size_t vel, gstamp, bcount, bucket, rec, plist, glist, over, ctl;
+    int nblocks, max_pblocks, max_gblocks, cap;
 };
 
-GridLayout carve_grid(Carver &c, const nsf_grid_desc *g, int n) {
+GridLayout carve_grid(Carver &c, const nsf_grid_desc *g, int n, int cap_max) {
     GridLayout L;
     size_t nodes = (size_t)g->n[0] * g->n[1] * g->n[2];
     L.nblocks = (int)(nodes / 64);
     L.max_pblocks = n < L.nblocks ? n : L.nblocks;
     long long mg = 8LL * L.max_pblocks;
     L.max_gblocks = mg < L.nblocks ? (int)mg : L.nblocks;
+    L.cap = n < cap_max ? n : cap_max;
     L.ctl = c.take(sizeof(Ctl));
-    L.acc = c.take(nodes * sizeof(float4));
     L.vel = c.take(nodes * sizeof(float4));
     L.gstamp = c.take((size_t)L.nblocks * 4);
-    L.pstamp = c.take((size_t)L.nblocks * 4);
+    L.bcount = c.take((size_t)L.nblocks * 4);
+    L.bucket = c.take((size_t)L.nblocks * L.cap * 4);
+    L.rec = c.take((size_t)n * 4 * sizeof(float4));
     L.plist = c.take((size_t)L.max_pblocks * 4);
     L.glist = c.take((size_t)L.max_gblocks * 4);
+    L.over = c.take((size_t)n * 4);
     return L;
 }
 
 GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
+    (void)n;
     GridWs w;
     w.n0 = g->n[0];
     w.n1 = g->n[1];
@@ -97,12 +108,15 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
     w.nb1 = w.n1 / 4;
     w.nb2 = w.n2 / 4;
     w.nblocks = L.nblocks;
-    w.acc = reinterpret_cast<float4 *>(base + L.acc);
     w.vel = reinterpret_cast<float4 *>(base + L.vel);
     w.gstamp = reinterpret_cast<int *>(base + L.gstamp);
-    w.pstamp = reinterpret_cast<int *>(base + L.pstamp);
+    w.bcount = reinterpret_cast<int *>(base + L.bcount);
+    w.bucket = reinterpret_cast<int *>(base + L.bucket);
+    w.cap = L.cap;
+    w.rec = reinterpret_cast<float4 *>(base + L.rec);
     w.plist = reinterpret_cast<int *>(base + L.plist);
     w.glist = reinterpret_cast<int *>(base + L.glist);
+    w.over = reinterpret_cast<int *>(base + L.over);
     w.ctl = reinterpret_cast<Ctl *>(base + L.ctl);
     w.max_pblocks = L.max_pblocks;
     w.max_gblocks = L.max_gblocks;
@@ -146,10 +160,11 @@ struct LatentLayout {
     size_t total;
 };
 
-LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc) {
+LatentLayout latent_layout(const nsf_fields *f, const nsf_latent_scene *sc,
+                           int cap_max = kBucketCapScene) {
     Carver c;
     LatentLayout L;
-    L.grid = carve_grid(c, &sc->grid, sc->n_N);
+    L.grid = carve_grid(c, &sc->grid, sc->n_N, cap_max);
     size_t n = (size_t)sc->n_N;
     L.u[0] = c.take(3 * n * 4);
     L.u[1] = c.take(3 * n * 4);
@@ -185,7 +200,7 @@ struct FullLayout {
 FullLayout full_layout(const nsf_grid_desc *g, int n) {
     Carver c;
     FullLayout L;
-    L.grid = carve_grid(c, g, n);
+    L.grid = carve_grid(c, g, n, kBucketCapScene);
     L.tau = c.take(6 * (size_t)n * 4);
     L.total = c.off;
     return L;
@@ -808,7 +823,7 @@ BatchLayout batch_layout(int n, const nsf_latent_batch_item *items) {
     BatchLayout B;
     size_t off = align_up(256);
     for (int i = 0; i < n; ++i) {
-        LatentLayout L = latent_layout(items[i].fields, &items[i].scene);
+        LatentLayout L = latent_layout(items[i].fields, &items[i].scene, kBucketCapBatch);
         B.base.push_back(off);
         B.scene.push_back(L);
         off = align_up(off + L.total);

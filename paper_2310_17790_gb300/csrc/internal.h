@@ -46,29 +46,45 @@ struct FieldsDev {
 };
 
 // ------------------------------------------------------------- workspace ---
+// Counters of one MPM step.  Two sets alternate with the step's epoch parity:
+// a step uses set (epoch & 1) and clears the other one, which no launch of
+// this step reads (the previous step's launches are complete).
+struct StepCtl {
+    int n_p;            // active particle blocks (binned particles)
+    int n_g;            // active grid blocks
+    int n_over;         // particles past their block's bucket capacity
+    unsigned bound;     // float bits of the largest P2G contribution bound
+};
+
 struct Ctl {
-    int epoch;          // incremented once per MPM step (block stamps)
-    int n_p_atomic;     // active particle blocks of the current step
-    int n_g_atomic;     // active grid blocks of the current step
-    int pad0[29];
+    int epoch;          // incremented once per MPM step (grid-block stamps)
+    int pad0[3];
+    StepCtl st[2];
+    int pad1[20];
     // arrival word of the fused MPM kernel's grid barrier, alone in its
     // 128-byte line
     unsigned bar;
-    unsigned pad1[31];
+    unsigned pad2[31];
 };
 
 // Sparse-in-use, dense-in-address background grid.  Nodes are stored
 // block-linear: 4x4x4-node blocks, block (bx, by, bz) at
 // ((bx * nb1 + by) * nb2 + bz), node (lx, ly, lz) inside at (lx * 4 + ly) * 4 + lz.
+// A particle belongs to the block of its stencil base node ("particle
+// block"); its stencil reaches that grid block and the next one along each
+// axis.
 struct GridWs {
     int n0, n1, n2;
     int nb0, nb1, nb2, nblocks;
-    float4 *acc;        // (m, p) accumulators; all zero between steps
-    float4 *vel;        // (v, m) after the grid update; valid on touched blocks
+    float4 *vel;        // (v, m) after the grid update; valid on the step's active blocks
     int *gstamp;        // epoch stamp of each grid block
-    int *pstamp;        // epoch stamp of each particle block (4^3 cells by stencil base)
+    int *bcount;        // particles binned to each particle block; zero between steps
+    int *bucket;        // [nblocks][cap] particle indices of each particle block
+    int cap;            // bucket capacity per particle block
+    float4 *rec;        // [n][4] P2G record of each particle (x, m v, Q)
     int *plist;         // active particle blocks of the step
     int *glist;         // active grid blocks of the step
+    int *over;          // particles whose block's bucket was full
     Ctl *ctl;
     int max_pblocks, max_gblocks;
 };

@@ -4,23 +4,34 @@
 // Phases of a launch, separated by a grid-wide barrier (all CTAs are
 // co-resident; every wait is bounded in time):
 //
-//   P2G         each particle adds its 27 node contributions (mass, APIC
-//               momentum, MLS stress force) straight into the grid with
-//               vector atomics, and stamps its 4^3-cell particle block (the
-//               block's first stamp of the step appends it to the active list)
-//   activation  every active particle block stamps the 8 grid blocks its
-//               stencils can reach and lists the newly stamped ones
-//   grid        v = p / m + dt g, walls, blade, over the listed grid blocks;
-//               the accumulators are re-zeroed on the way
-//   G2P         latent: x^{n+1} on the sample particles, in the same launch;
-//               full-order: a separate launch (its float64 return map needs
-//               far more registers than the other phases)
+//   bin      each particle forms its P2G record (position, m v and the matrix
+//            Q = m C - dt V0 (4/dx^2) tau that carries the APIC term and the
+//            MLS stress force of Eq. 5) and is binned by its 4^3-cell
+//            particle block (the block of its stencil base node): a warp
+//            aggregates the lanes that share a block (match, popc) into one
+//            counter atomic whose old value gives each lane its slot in the
+//            block's bucket.  The first arrival in a block lists it and
+//            stamps the 8 grid blocks its stencils can reach.
+//   P2G +    each active grid block is owned by one group of threads, which
+//   grid     gathers the particles of the 8 particle blocks that reach it
+//            from their buckets, accumulates their contributions to its 64
+//            nodes in shared memory, then turns each node's (m, p) into
+//            v = p / m + dt g with the walls and the blade, and writes v
+//            once.  No grid value goes through a global atomic.
+//   G2P      latent: x^{n+1} on the sample particles, in the same launch;
+//            full-order: a separate launch (its float64 return map needs
+//            far more registers than the other phases).
 //
-// Direct vector atomics into L2 were measured faster than accumulating each
-// particle block in a shared-memory tile first, for the sparse latent
-// particle sets and for the dense full-order slab (8 particles per cell)
-// alike: the tile's shared-memory float atomics conflict heavily, and the
-// sorting the tile needs (count, scan, scatter) costs three more barriers.
+// Sums are exact.  Every node contribution is rounded once to a 64-bit fixed
+// point number (mass on a scale from the particle mass, momentum on a scale
+// from this step's largest contribution bound, reduced warp by warp in the
+// bin phase) and added as an integer, so a node's total does not depend on
+// the order of the additions: the step is bit-for-bit reproducible.  A
+// contribution of the bounding size maps to < 2^44, leaving 2^19 such
+// contributions of headroom per node; the resolution is 2^-44 of the largest
+// contribution (a smaller one than float32 rounding of a sum of similar
+// terms gives).
+
 #include "constitutive.cuh"
 #include "device_common.cuh"
 
@@ -157,82 +168,192 @@ __device__ __forceinline__ float4 node_contribution(const P2gParticle &q, const 
     return make_float4(w * mass, w * px, w * py, w * pz);
 }
 
-// ---------------------------------------------------------------- P2G ----
-// Particle p's 27 node contributions, added straight into the grid; returns
-// its particle block, or -1 when its stencil leaves the grid (status set).
-template <class Args>
-__device__ __forceinline__ int p2g_particle(const GridWs &g, const GridParams &gp, const Args &a,
-                                            float stress_k, int p, int *status) {
-    P2gParticle q;
-    load_particle(a, stress_k, p, q);
-    const int key = block_key(g, q.x, gp.inv_dx, status);
-    if (key >= 0) {
-        Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
-                  bspline_axis(q.x[2], gp.inv_dx)};
-#pragma unroll
-        for (int ia = 0; ia < 3; ++ia)
-#pragma unroll
-            for (int ib = 0; ib < 3; ++ib)
-#pragma unroll
-                for (int ic = 0; ic < 3; ++ic)
-                    atomicAdd(&g.acc[node_addr(g, s.ax.base + ia, s.ay.base + ib, s.az.base + ic)],
-                              node_contribution(q, s, a.mass, gp.dx, ia, ib, ic));
-    }
-    return key;
+// ------------------------------------------------------- fixed point ----
+// A contribution of the bounding magnitude maps to < 2^kFixBits (integer
+// sums of up to 2^(63 - kFixBits) of them cannot overflow).
+constexpr int kFixBits = 44;
+
+// 2^(kFixBits - e) for the exponent e with bound < 2^e (a power of two, so
+// scaling by it and by its reciprocal is exact); kept inside the normal range.
+__device__ __forceinline__ float fix_scale(float bound) {
+    int e = 0;
+    if (bound > 0.f) frexpf(bound, &e);
+    int k = kFixBits - e;
+    k = k > 126 ? 126 : (k < -126 ? -126 : k);
+    return ldexpf(1.f, k);
 }
 
-// One stamp per distinct (scene tag, block) in the warp; the first stamp of
-// this step appends the block to the scene's active list.  Every lane of the
-// warp calls; key < 0 means no particle.
-__device__ __forceinline__ void stamp_block(const GridWs &g, int tag, int key, int epoch) {
-    const unsigned peers = __match_any_sync(0xffffffffu, key < 0 ? -1 : (tag << 16) | key);
-    if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
-        if (atomicExch(&g.pstamp[key], epoch) != epoch)
-            g.plist[atomicAdd(&g.ctl->n_p_atomic, 1)] = key;
-    }
+__device__ __forceinline__ unsigned long long to_fix(float v, float scale) {
+    return (unsigned long long)__float2ll_rn(v * scale);
 }
 
-template <class Args>
-__device__ void phase_p2g(const GridWs &g, const GridParams &gp, const Args &a,
-                                 float stress_k, int epoch, int *status) {
-    const int n = a.n;
-    const int stride = gridDim.x * blockDim.x;
-    // the loop bound is uniform across each warp (match_any in stamp_block)
-    for (int base = spread_index() & ~31; base < n; base += stride) {
-        const int p = base + (threadIdx.x & 31);
-        const int key = p < n ? p2g_particle(g, gp, a, stress_k, p, status) : -2;
-        stamp_block(g, 0, key, epoch);
-    }
+__device__ __forceinline__ float from_fix(unsigned long long q, float inv_scale) {
+    return __ll2float_rn((long long)q) * inv_scale;
 }
 
-// --------------------------------------------------------- activation ----
-// Every active particle block stamps the grid blocks (bx..bx+1, by..by+1,
-// bz..bz+1) that its particles' stencils can reach; the first stamp of this
-// step lists the grid block.  One thread per (block, corner) pair.
-__device__ void phase_activate(const GridWs &g, int np, int epoch) {
-    for (int q = spread_index(); q < 8 * np; q += gridDim.x * blockDim.x) {
-        const int key = __ldcg(&g.plist[q >> 3]), d = q & 7;
-        const int bz = key % g.nb2, t = key / g.nb2, by = t % g.nb1, bx = t / g.nb1;
-        const int cx = bx + (d >> 2), cy = by + ((d >> 1) & 1), cz = bz + (d & 1);
+// Largest |component| of any node contribution of q: w <= 1 and
+// |x_i - x_p| <= 1.5 dx per axis, so |w (m v + Q (x_i - x_p))| is at most
+// max |m v| + 1.5 dx max_row sum |Q_row|.
+__device__ __forceinline__ float contribution_bound(const P2gParticle &q, float dx) {
+    const float mv = fmaxf(fabsf(q.mv[0]), fmaxf(fabsf(q.mv[1]), fabsf(q.mv[2])));
+    float rmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        rmax = fmaxf(rmax, fabsf(q.Q[3 * i]) + fabsf(q.Q[3 * i + 1]) + fabsf(q.Q[3 * i + 2]));
+    return mv + 1.5f * dx * rmax;
+}
+
+// ----------------------------------------------------------- records ----
+// P2G record of a particle, four float4: (x, mv0), (mv1, mv2, Q0, Q1),
+// (Q2 .. Q5), (Q6, Q7, Q8, 0).
+__device__ __forceinline__ void store_record(float4 *rec, int p, const P2gParticle &q) {
+    float4 *r = rec + 4 * (size_t)p;
+    r[0] = make_float4(q.x[0], q.x[1], q.x[2], q.mv[0]);
+    r[1] = make_float4(q.mv[1], q.mv[2], q.Q[0], q.Q[1]);
+    r[2] = make_float4(q.Q[2], q.Q[3], q.Q[4], q.Q[5]);
+    r[3] = make_float4(q.Q[6], q.Q[7], q.Q[8], 0.f);
+}
+
+// ----------------------------------------------------------- binning ----
+// Stamps the grid blocks (kx..kx+1, ky..ky+1, kz..kz+1) that the stencils of
+// particle block `key` reach; the first stamp of this step lists the block.
+__device__ __forceinline__ void activate_grid_blocks(const GridWs &g, int key, int epoch,
+                                                     StepCtl &st) {
+    const int kz = key % g.nb2, t = key / g.nb2, ky = t % g.nb1, kx = t / g.nb1;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int cx = kx + (d >> 2), cy = ky + ((d >> 1) & 1), cz = kz + (d & 1);
         if (cx >= g.nb0 || cy >= g.nb1 || cz >= g.nb2) continue;
         const int gb = (cx * g.nb1 + cy) * g.nb2 + cz;
-        if (atomicExch(&g.gstamp[gb], epoch) != epoch) g.glist[atomicAdd(&g.ctl->n_g_atomic, 1)] = gb;
+        if (atomicExch(&g.gstamp[gb], epoch) != epoch) g.glist[atomicAdd(&st.n_g, 1)] = gb;
     }
 }
 
-// --------------------------------------------------------------- grid ----
-// Node l (0 .. 63) of active grid block gb, whose accumulated (m, m v) is a:
-// velocity update (gravity, walls, blade) into g.vel, and the accumulator
-// cleared for the next step's P2G (skipped when it already holds zeros: in a
-// sparse scene most nodes of an active block were not touched).
+// Bin particle p (p < 0: no particle) of scene `tag` (0 for a single scene).
+// Every lane of the warp calls (the match below is warp-wide).  The lanes
+// that share a particle block form a group: one counter atomic for the group
+// (its old value plus the lane's rank in the group is the lane's bucket slot),
+// one atomicMax of the group's largest contribution bound, and the group
+// that finds the block empty lists it and activates its grid blocks.
+template <class Args>
+__device__ __forceinline__ void bin_particle(const GridWs &g, const GridParams &gp,
+                                             const Args &a, float stress_k, int tag, int p,
+                                             int epoch, int *status) {
+    const int lane = threadIdx.x & 31;
+    int key = -1;
+    float bnd = 0.f;
+    if (p >= 0) {
+        P2gParticle q;
+        load_particle(a, stress_k, p, q);
+        key = block_key(g, q.x, gp.inv_dx, status);
+        if (key >= 0) {
+            bnd = contribution_bound(q, gp.dx);
+            if (!isfinite(bnd)) {
+                set_status(status, NSF_ERR_NONFINITE);
+                key = -1;
+            } else {
+                store_record(g.rec, p, q);
+            }
+        }
+    }
+    const unsigned long long gkey =
+        key < 0 ? ~0ull : (((unsigned long long)(unsigned)tag << 32) | (unsigned)key);
+    const unsigned peers = __match_any_sync(0xffffffffu, gkey);
+    if (key < 0) return;
+    const int leader = __ffs(peers) - 1;
+    const unsigned bmax = __reduce_max_sync(peers, __float_as_uint(bnd));
+    StepCtl &st = g.ctl->st[epoch & 1];
+    int old = 0;
+    if (lane == leader) {
+        old = atomicAdd(&g.bcount[key], __popc(peers));
+        atomicMax(&st.bound, bmax);
+        if (old == 0) {
+            g.plist[atomicAdd(&st.n_p, 1)] = key;
+            activate_grid_blocks(g, key, epoch, st);
+        }
+    }
+    old = __shfl_sync(peers, old, leader);
+    const int rank = old + __popc(peers & ((1u << lane) - 1u));
+    if (rank < g.cap) g.bucket[(size_t)key * g.cap + rank] = p;
+    else g.over[atomicAdd(&st.n_over, 1)] = p;
+}
+
+// --------------------------------------------------- P2G + grid update ----
+// Threads of one grid-block owner (a CTA runs kThreads / kOwnerThreads
+// owners side by side, each on its own named barrier).
+constexpr int kOwnerThreads = 64;      // one thread per node of the grid block
+constexpr int kOwners = kThreads / kOwnerThreads;
+static_assert(kOwnerThreads == 64 && kThreads % kOwnerThreads == 0, "owner layout");
+
+struct OwnerSmem {
+    unsigned long long acc[64 * 4];   // (m, p) of the block's 64 nodes, fixed point
+    int nb[8];                        // the 8 particle blocks that reach it (-1: none)
+    int off[9];                       // prefix of their particle counts
+};
+
+__device__ __forceinline__ void owner_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kOwnerThreads) : "memory");
+}
+
+// Scales of one step's fixed-point sums.
+struct FixScales {
+    float m, p, inv_m, inv_p;
+};
+
+__device__ __forceinline__ FixScales fix_scales(float mass, unsigned bound_bits) {
+    FixScales s;
+    s.m = fix_scale(mass);
+    s.p = fix_scale(__uint_as_float(bound_bits));
+    s.inv_m = 1.f / s.m;      // exact: powers of two
+    s.inv_p = 1.f / s.p;
+    return s;
+}
+
+// Adds particle p's contributions to the nodes of grid block (ox, oy, oz) +
+// [0, 4)^3 (its stencil nodes inside that block) to the owner's sums.
+__device__ __forceinline__ void owner_add_particle(const GridWs &g, const GridParams &gp,
+                                                   float mass, const FixScales &fs, int p,
+                                                   int ox, int oy, int oz,
+                                                   unsigned long long *acc) {
+    const float4 *r = g.rec + 4 * (size_t)p;
+    const float4 r0 = __ldcg(r);
+    const Axis ax = bspline_axis(r0.x, gp.inv_dx), ay = bspline_axis(r0.y, gp.inv_dx),
+               az = bspline_axis(r0.z, gp.inv_dx);
+    const int a0 = max(0, ox - ax.base), a1 = min(2, ox + 3 - ax.base);
+    const int b0 = max(0, oy - ay.base), b1 = min(2, oy + 3 - ay.base);
+    const int c0 = max(0, oz - az.base), c1 = min(2, oz + 3 - az.base);
+    if (a0 > a1 || b0 > b1 || c0 > c1) return;
+    const float4 r1 = __ldcg(r + 1), r2 = __ldcg(r + 2), r3 = __ldcg(r + 3);
+    P2gParticle q;
+    q.x[0] = r0.x; q.x[1] = r0.y; q.x[2] = r0.z;
+    q.mv[0] = r0.w; q.mv[1] = r1.x; q.mv[2] = r1.y;
+    q.Q[0] = r1.z; q.Q[1] = r1.w;
+    q.Q[2] = r2.x; q.Q[3] = r2.y; q.Q[4] = r2.z; q.Q[5] = r2.w;
+    q.Q[6] = r3.x; q.Q[7] = r3.y; q.Q[8] = r3.z;
+    const Stencil s{ax, ay, az};
+    for (int ia = a0; ia <= a1; ++ia)
+        for (int ib = b0; ib <= b1; ++ib)
+            for (int ic = c0; ic <= c1; ++ic) {
+                const float4 c = node_contribution(q, s, mass, gp.dx, ia, ib, ic);
+                const int l = ((ax.base + ia - ox) * 4 + (ay.base + ib - oy)) * 4 +
+                              (az.base + ic - oz);
+                unsigned long long *n = acc + 4 * l;
+                atomicAdd(n + 0, to_fix(c.x, fs.m));
+                atomicAdd(n + 1, to_fix(c.y, fs.p));
+                atomicAdd(n + 2, to_fix(c.z, fs.p));
+                atomicAdd(n + 3, to_fix(c.w, fs.p));
+            }
+}
+
+// Grid update of node l (0 .. 63) of grid block gb from its (m, p) = a:
+// v = p / m + dt g, walls, blade, written with m to g.vel (§3.3).  Nodes
+// with m = 0 get v = 0 and no boundary condition.
 __device__ __forceinline__ void grid_node_update(const GridWs &g, const GridParams &gp, float dt,
                                                  double blade_z, int gb, int l, float4 a,
                                                  float *tap_mp, float *tap_v) {
     const int lx = l >> 4, ly = (l >> 2) & 3, lz = l & 3;
     const int bz = gb % g.nb2, tt = gb / g.nb2, by = tt % g.nb1, bx = tt / g.nb1;
     const int i = bx * 4 + lx, j = by * 4 + ly, k = bz * 4 + lz;
-    const int addr = gb * 64 + l;
-    if (a.x != 0.f || a.y != 0.f || a.z != 0.f || a.w != 0.f) g.acc[addr] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 v = make_float4(0.f, 0.f, 0.f, a.x);
     if (a.x > 0.f) {
         const float im = 1.f / a.x;
@@ -255,39 +376,115 @@ __device__ __forceinline__ void grid_node_update(const GridWs &g, const GridPara
             }
         }
     }
-    g.vel[addr] = v;
+    g.vel[gb * 64 + l] = v;
     const size_t nat = (((size_t)i * g.n1 + j) * g.n2 + k) * 4;
     if (tap_mp) *reinterpret_cast<float4 *>(tap_mp + nat) = a;
     if (tap_v) *reinterpret_cast<float4 *>(tap_v + nat) = v;
 }
 
-// Grid blocks a thread updates per pass: their index and node loads are
-// issued together, so a thread has kGridUnroll memory chains in flight
-// instead of one.
-constexpr int kGridUnroll = 4;
-
-__device__ void phase_grid(const GridWs &g, const GridParams &gp, float dt, double t,
-                           float *tap_mp, float *tap_v) {
-    const int ngb = __ldcg(&g.ctl->n_g_atomic);
-    const int per = blockDim.x >> 6;                 // grid blocks per CTA pass
-    const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
-    const int stride = gridDim.x * per;
-    const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
-    for (int i0 = sub * gridDim.x + blockIdx.x; i0 < ngb; i0 += kGridUnroll * stride) {
-        int gb[kGridUnroll];
-        float4 a[kGridUnroll];
-#pragma unroll
-        for (int u = 0; u < kGridUnroll; ++u) {
-            const int idx = i0 + u * stride;
-            gb[u] = idx < ngb ? __ldcg(&g.glist[idx]) : -1;
+// One grid block gb owned by this thread group (gt: thread in the group):
+// gather, accumulate, grid update.  Every thread of the group calls.
+__device__ void owner_block(const GridWs &g, const GridParams &gp, float mass, float dt,
+                            double blade_z, const FixScales &fs, int n_over, int gb,
+                            OwnerSmem &sm, int gt, int bar_id, float *tap_mp, float *tap_v) {
+    const int bz = gb % g.nb2, t = gb / g.nb2, by = t % g.nb1, bx = t / g.nb1;
+    for (int i = gt; i < 64 * 4; i += kOwnerThreads) sm.acc[i] = 0ull;
+    if (gt < 8) {
+        const int kx = bx - (gt >> 2), ky = by - ((gt >> 1) & 1), kz = bz - (gt & 1);
+        int key = -1, c = 0;
+        if (kx >= 0 && ky >= 0 && kz >= 0) {
+            key = (kx * g.nb1 + ky) * g.nb2 + kz;
+            c = min(__ldcg(&g.bcount[key]), g.cap);
         }
+        int v = c;
 #pragma unroll
-        for (int u = 0; u < kGridUnroll; ++u)
-            if (gb[u] >= 0) a[u] = __ldcg(&g.acc[gb[u] * 64 + l]);
-#pragma unroll
-        for (int u = 0; u < kGridUnroll; ++u)
-            if (gb[u] >= 0) grid_node_update(g, gp, dt, blade_z, gb[u], l, a[u], tap_mp, tap_v);
+        for (int o = 1; o < 8; o <<= 1) {
+            const int y = __shfl_up_sync(0xffu, v, o, 8);
+            if (gt >= o) v += y;
+        }
+        sm.nb[gt] = key;
+        sm.off[gt + 1] = v;
+        if (gt == 0) sm.off[0] = 0;
     }
+    owner_sync(bar_id);
+    const int total = sm.off[8];
+    const int ox = bx * 4, oy = by * 4, oz = bz * 4;
+    for (int u = gt; u < total; u += kOwnerThreads) {
+        int d = 0;
+        while (u >= sm.off[d + 1]) ++d;
+        const int p = __ldcg(&g.bucket[(size_t)sm.nb[d] * g.cap + (u - sm.off[d])]);
+        owner_add_particle(g, gp, mass, fs, p, ox, oy, oz, sm.acc);
+    }
+    // particles that did not fit in their block's bucket (rare)
+    for (int u = gt; u < n_over; u += kOwnerThreads)
+        owner_add_particle(g, gp, mass, fs, __ldcg(&g.over[u]), ox, oy, oz, sm.acc);
+    owner_sync(bar_id);
+    {
+        const int l = gt;                          // kOwnerThreads == 64 nodes
+        const unsigned long long *n = sm.acc + 4 * l;
+        const float4 a = make_float4(from_fix(n[0], fs.inv_m), from_fix(n[1], fs.inv_p),
+                                     from_fix(n[2], fs.inv_p), from_fix(n[3], fs.inv_p));
+        grid_node_update(g, gp, dt, blade_z, gb, l, a, tap_mp, tap_v);
+    }
+    owner_sync(bar_id);
+}
+
+// Owner loop of a single scene: grid blocks q = owner index, + all owners.
+__device__ void phase_p2g_grid(const GridWs &g, const GridParams &gp, float mass, float dt,
+                               double t, const StepCtl &st, float *tap_mp, float *tap_v) {
+    __shared__ OwnerSmem sm[kOwners];
+    const int grp = threadIdx.x / kOwnerThreads, gt = threadIdx.x % kOwnerThreads;
+    const int n_g = __ldcg(&st.n_g), n_over = __ldcg(&st.n_over);
+    const FixScales fs = fix_scales(mass, __ldcg(&st.bound));
+    const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
+    // owner w of CTA c is global owner w * gridDim.x + c: a short list still
+    // spreads over every SM
+    for (int q = grp * gridDim.x + blockIdx.x; q < n_g; q += kOwners * gridDim.x)
+        owner_block(g, gp, mass, dt, blade_z, fs, n_over, __ldcg(&g.glist[q]), sm[grp], gt,
+                    1 + grp, tap_mp, tap_v);
+}
+
+// Bin phase of a single scene.
+template <class Args>
+__device__ void phase_bin(const GridWs &g, const GridParams &gp, const Args &a, float stress_k,
+                          int epoch, int *status) {
+    const int n = a.n;
+    const int stride = gridDim.x * blockDim.x;
+    // the loop bound is uniform across each warp (the match in bin_particle)
+    for (int base = spread_index() & ~31; base < n; base += stride) {
+        const int p = base + (threadIdx.x & 31);
+        bin_particle(g, gp, a, stress_k, 0, p < n ? p : -1, epoch, status);
+    }
+}
+
+// Clears this step's bucket counters (its listed particle blocks) for the
+// next step.
+__device__ void clear_bins(const GridWs &g, const StepCtl &st) {
+    const int n_p = __ldcg(&st.n_p);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_p; q += gridDim.x * blockDim.x)
+        g.bcount[__ldcg(&g.plist[q])] = 0;
+}
+
+// Start of a step's MPM launch: the step's epoch and, by one thread, the
+// other counter set cleared (no launch of this step uses it).
+__device__ __forceinline__ int begin_step(const GridWs &g) {
+    const int epoch = __ldcg(&g.ctl->epoch) + 1;
+    if (cta0_thread0()) g.ctl->st[(epoch & 1) ^ 1] = StepCtl{0, 0, 0, 0u};
+    return epoch;
+}
+
+// bin | barrier | P2G + grid update.  Returns false if the barrier timed out.
+// After the barrier (every CTA has read the old epoch) CTA 0 publishes the
+// step's epoch, which later launches of the step read.
+template <class Args>
+__device__ bool bin_p2g_grid(const GridWs &g, const GridParams &gp, const Args &a, double t,
+                             int epoch, float *tap_mp, float *tap_v, int *status) {
+    const float stress_k = -a.dt * a.vol0 * 4.f * gp.inv_dx * gp.inv_dx;
+    phase_bin(g, gp, a, stress_k, epoch, status);
+    if (!grid_barrier(&g.ctl->bar, status)) return false;
+    if (cta0_thread0()) g.ctl->epoch = epoch;
+    phase_p2g_grid(g, gp, a.mass, a.dt, t, g.ctl->st[epoch & 1], tap_mp, tap_v);
+    return true;
 }
 
 // ---------------------------------------------------------------- G2P ----
@@ -416,50 +613,30 @@ __device__ void phase_g2p_full(const GridWs &g, const GridParams &gp, const G2pF
     }
 }
 
-// ------------------------------------------------ P2G + grid update ----
-// Returns false if a barrier timed out (the launch then ends early).
-template <class Args>
-__device__ bool p2g_and_grid(const GridWs &g, const GridParams &gp, const Args &a, double t,
-                             int epoch, float *tap_mp, float *tap_v, int *status) {
-    const float stress_k = -a.dt * a.vol0 * 4.f * gp.inv_dx * gp.inv_dx;
-    phase_p2g(g, gp, a, stress_k, epoch, status);
-    if (!grid_barrier(&g.ctl->bar, status)) return false;
-    phase_activate(g, __ldcg(&g.ctl->n_p_atomic), epoch);
-    if (!grid_barrier(&g.ctl->bar, status)) return false;
-    if (cta0_thread0()) g.ctl->n_p_atomic = 0;          // every CTA has read it
-    phase_grid(g, gp, a.dt, t, tap_mp, tap_v);
-    return true;
-}
-
+// ------------------------------------------------------------- kernels ---
 __global__ void __launch_bounds__(kThreads)
 k_mpm_latent(GridWs g, GridParams gp, P2gLatentArgs a, int n_S, double t, float *d_next,
              float *tap_mp, float *tap_v, int *status) {
-    const int epoch = __ldcg(&g.ctl->epoch) + 1;
-    if (!p2g_and_grid(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
+    const int epoch = begin_step(g);
+    if (!bin_p2g_grid(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
     if (!grid_barrier(&g.ctl->bar, status)) return;
     phase_g2p_latent(g, gp, a.X, a.u, a.n, n_S, a.dt, d_next, status);
-    if (cta0_thread0()) {
-        g.ctl->n_g_atomic = 0;                            // read by the grid phase only
-        g.ctl->epoch = epoch;
-    }
+    clear_bins(g, g.ctl->st[epoch & 1]);
 }
 
 __global__ void __launch_bounds__(kThreads)
 k_mpm_full(GridWs g, GridParams gp, P2gFullArgs a, double t, float *tap_mp, float *tap_v,
            int *status) {
-    const int epoch = __ldcg(&g.ctl->epoch) + 1;
-    p2g_and_grid(g, gp, a, t, epoch, tap_mp, tap_v, status);
+    const int epoch = begin_step(g);
+    bin_p2g_grid(g, gp, a, t, epoch, tap_mp, tap_v, status);
 }
 
-// Full-order G2P, one thread per particle; it also closes the step's
-// bookkeeping (grid-block counter, epoch) that the MPM launch left open.
+// Full-order G2P, one thread per particle; it also clears the step's bucket
+// counters (the MPM launch published the step's epoch).
 __global__ void __launch_bounds__(kThreads)
 k_g2p_full(GridWs g, GridParams gp, G2pFullArgs a, int *status) {
     phase_g2p_full(g, gp, a, status);
-    if (cta0_thread0()) {
-        g.ctl->n_g_atomic = 0;
-        g.ctl->epoch = g.ctl->epoch + 1;
-    }
+    clear_bins(g, g.ctl->st[__ldcg(&g.ctl->epoch) & 1]);
 }
 
 // Kirchhoff stress of F (no return map) for the SVD-based models, float64.
@@ -541,78 +718,58 @@ __device__ __forceinline__ P2gLatentArgs latent_args(const BatchSceneDev &sc, in
     return a;
 }
 
+
+
 // The MPM part of a batched latent step: every phase runs over all scenes at
-// once (a flat index over the scenes' particles, active particle blocks,
-// active grid blocks and sample particles), with one grid barrier between
-// phases for the whole batch.
+// once (a flat index over the scenes' particles, active grid blocks and
+// sample particles), with one grid barrier between phases for the whole
+// batch.  Each scene keeps its own counters, epoch and buckets.
 __global__ void __launch_bounds__(kThreads, 4)
 k_mpm_batch(MpmBatchArgs b, int *status) {
     __shared__ int off[kMaxBatchScenes + 1];
+    __shared__ int s_epoch[kMaxBatchScenes];
+    __shared__ OwnerSmem sm[kOwners];
     const int ns = b.nscenes;
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    // P2G
+    // every scene's step epoch, read before the first barrier; block 0 clears
+    // each scene's other counter set
+    for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) {
+        const Ctl *c = b.scenes[sc].g.ctl;
+        s_epoch[sc] = __ldcg(&c->epoch) + 1;
+        if (blockIdx.x == 0) b.scenes[sc].g.ctl->st[(s_epoch[sc] & 1) ^ 1] = StepCtl{0, 0, 0, 0u};
+    }
+    __syncthreads();
+    // bin
     const int total_N = __ldg(&b.n_off[ns]);
     for (int base = spread_index() & ~31; base < total_N; base += stride) {
         const int q = base + lane;
-        int key = -2, sidx = 0;
-        if (q < total_N) sidx = find_scene(b.n_off, ns, q);
+        const int sidx = q < total_N ? find_scene(b.n_off, ns, q) : 0;
         const BatchSceneDev &sc = b.scenes[sidx];
-        const int epoch = __ldcg(&sc.g.ctl->epoch) + 1;
-        if (q < total_N) {
-            const float stress_k = -sc.dt * sc.vol0 * 4.f * sc.gp.inv_dx * sc.gp.inv_dx;
-            key = p2g_particle(sc.g, sc.gp, latent_args(sc, b.parity), stress_k,
-                               q - __ldg(&b.n_off[sidx]), status);
-        }
-        stamp_block(sc.g, sidx, key, epoch);
-    }
-    if (!grid_barrier(b.bar, status)) return;
-    // block activation
-    block_offsets(ns, off, [&](int sc) { return 8 * __ldcg(&b.scenes[sc].g.ctl->n_p_atomic); });
-    for (int q = spread_index(); q < off[ns]; q += stride) {
-        const int sidx = find_scene(off, ns, q);
-        const GridWs &g = b.scenes[sidx].g;
-        const int epoch = __ldcg(&g.ctl->epoch) + 1;
-        const int k = q - off[sidx];
-        const int key = __ldcg(&g.plist[k >> 3]), d = k & 7;
-        const int bz = key % g.nb2, t = key / g.nb2, by = t % g.nb1, bx = t / g.nb1;
-        const int cx = bx + (d >> 2), cy = by + ((d >> 1) & 1), cz = bz + (d & 1);
-        if (cx >= g.nb0 || cy >= g.nb1 || cz >= g.nb2) continue;
-        const int gb = (cx * g.nb1 + cy) * g.nb2 + cz;
-        if (atomicExch(&g.gstamp[gb], epoch) != epoch) g.glist[atomicAdd(&g.ctl->n_g_atomic, 1)] = gb;
+        const float stress_k = -sc.dt * sc.vol0 * 4.f * sc.gp.inv_dx * sc.gp.inv_dx;
+        bin_particle(sc.g, sc.gp, latent_args(sc, b.parity), stress_k, sidx,
+                     q < total_N ? q - __ldg(&b.n_off[sidx]) : -1, s_epoch[sidx], status);
     }
     if (!grid_barrier(b.bar, status)) return;
     if (blockIdx.x == 0)                         // every CTA has read them
-        for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) b.scenes[sc].g.ctl->n_p_atomic = 0;
-    // grid update
-    block_offsets(ns, off, [&](int sc) { return __ldcg(&b.scenes[sc].g.ctl->n_g_atomic); });
+        for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) b.scenes[sc].g.ctl->epoch = s_epoch[sc];
+    // P2G + grid update over every scene's active grid blocks
+    block_offsets(ns, off, [&](int sc) {
+        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_g);
+    });
     {
-        const int per = blockDim.x >> 6;
-        const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
-        const int nblk = off[ns], gstride = gridDim.x * per;
-        for (int u0 = sub * gridDim.x + blockIdx.x; u0 < nblk; u0 += kGridUnroll * gstride) {
-            int sidx[kGridUnroll], gb[kGridUnroll];
-            float4 a[kGridUnroll];
-#pragma unroll
-            for (int k = 0; k < kGridUnroll; ++k) {
-                const int u = u0 + k * gstride;
-                sidx[k] = -1;
-                if (u < nblk) {
-                    sidx[k] = find_scene(off, ns, u);
-                    gb[k] = __ldcg(&b.scenes[sidx[k]].g.glist[u - off[sidx[k]]]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kGridUnroll; ++k)
-                if (sidx[k] >= 0) a[k] = __ldcg(&b.scenes[sidx[k]].g.acc[gb[k] * 64 + l]);
-#pragma unroll
-            for (int k = 0; k < kGridUnroll; ++k) {
-                if (sidx[k] < 0) continue;
-                const BatchSceneDev &sc = b.scenes[sidx[k]];
-                const double t = b.t0 + (double)b.step * (double)sc.dt;
-                const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
-                grid_node_update(sc.g, sc.gp, sc.dt, blade_z, gb[k], l, a[k], nullptr, nullptr);
-            }
+        const int grp = threadIdx.x / kOwnerThreads, gt = threadIdx.x % kOwnerThreads;
+        const int nblk = off[ns];
+        for (int q = grp * gridDim.x + blockIdx.x; q < nblk; q += kOwners * gridDim.x) {
+            const int sidx = find_scene(off, ns, q);
+            const BatchSceneDev &sc = b.scenes[sidx];
+            const StepCtl &st = sc.g.ctl->st[s_epoch[sidx] & 1];
+            const FixScales fs = fix_scales(sc.mass, __ldcg(&st.bound));
+            const double t = b.t0 + (double)b.step * (double)sc.dt;
+            const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
+            owner_block(sc.g, sc.gp, sc.mass, sc.dt, blade_z, fs, __ldcg(&st.n_over),
+                        __ldcg(&sc.g.glist[q - off[sidx]]), sm[grp], gt, 1 + grp, nullptr,
+                        nullptr);
         }
     }
     if (!grid_barrier(b.bar, status)) return;
@@ -624,13 +781,17 @@ k_mpm_batch(MpmBatchArgs b, int *status) {
         g2p_latent_particle(sc.g, sc.gp, sc.residual_g ? sc.X : nullptr, sc.u[b.parity], sc.n_N,
                             sc.n_S, sc.dt, sc.dnext, q - __ldg(&b.s_off[sidx]), status);
     }
-    if (blockIdx.x == 0)
-        for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) {
-            Ctl *c = b.scenes[sc].g.ctl;
-            c->n_g_atomic = 0;                   // read by the grid phase only
-            c->epoch = c->epoch + 1;
-        }
+    // clear every scene's bucket counters
+    block_offsets(ns, off, [&](int sc) {
+        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_p);
+    });
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < off[ns]; q += stride) {
+        const int sidx = find_scene(off, ns, q);
+        const GridWs &g = b.scenes[sidx].g;
+        g.bcount[__ldcg(&g.plist[q - off[sidx]])] = 0;
+    }
 }
+
 
 // CTAs per SM of the latent MPM launch: its phases are separated by grid
 // barriers over a few thousand particles, and one CTA per SM made the stage

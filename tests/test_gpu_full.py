@@ -74,14 +74,15 @@ def _check(sc, out, t0=0.0):
     vg = ompm.grid_update(gmp[..., 0], gmp[..., 1:], sc.dt, og, t0)
     gv = out["grid_v"]
     assert rel(gv[..., :3], vg) < TOL
-    xn, vp, Cp, Gp, ok = ompm.g2p(x0, gv[..., :3], sc.dt, og, full=True)
-    assert np.abs(out["x"] - xn).max() / sc.grid.dx < TOL
-    assert rel(out["v"], vp) < TOL
-    assert rel(out["C"], Cp.reshape(-1, 9)) < TOL
-    Fn = np.einsum("nij,njk->nik", np.eye(3) + sc.dt * Gp, F0)
-    Fe = mat.return_map(Fn)
-    assert rel(out["F"], Fe.reshape(-1, 9)) < TOL
-    return Fn, Fe
+    # G2P, the update of F and the return map of the oracle's full step (§3.3,
+    # App. F), fed the GPU's grid velocities
+    g2 = ompm.g2p_full(x0, F0, gv[..., :3], sc.dt, og, mat)
+    assert g2["in_grid"]
+    assert np.abs(out["x"] - g2["x"]).max() / sc.grid.dx < TOL
+    assert rel(out["v"], g2["v"]) < TOL
+    assert rel(out["C"], g2["C"].reshape(-1, 9)) < TOL
+    assert rel(out["F"], g2["F"].reshape(-1, 9)) < TOL
+    return g2["F_trial"], g2["F"]
 
 
 def test_full_step_small_slab_with_blade(nsf):
@@ -89,6 +90,23 @@ def test_full_step_small_slab_with_blade(nsf):
     sc.grid.blade = dict(x=0.5, z0=0.205, vz=-1.0)
     out = _run(nsf, sc, t0=0.002)
     _check(sc, out, t0=0.002)
+
+
+def test_full_step_end_to_end_matches_oracle_full_step(nsf):
+    # one step from the same state, not teacher-forced: the GPU's x, v, C, F
+    # against oracle.mpm.full_step (§3.3) in float64
+    sc = _perturb(full_scene(77, lattice=(24, 24, 8), n_grid=64), 77)
+    out = _run(nsf, sc)
+    assert out["status"] == 0
+    m = sc.material
+    mat = ocm.Material(m["model"], m["E"], m["nu"])
+    ref = ompm.full_step(sc.x, sc.v, sc.C.reshape(-1, 3, 3), sc.F.reshape(-1, 3, 3), sc.mass,
+                         sc.vol0, sc.dt, oracle_grid(sc.grid), mat)
+    assert ref["in_grid"]
+    assert np.abs(out["x"] - ref["x"]).max() / sc.grid.dx < TOL
+    assert rel(out["v"], ref["v"]) < TOL
+    assert rel(out["C"], ref["C"].reshape(-1, 9)) < TOL
+    assert rel(out["F"], ref["F"].reshape(-1, 9)) < TOL
 
 
 def test_full_step_200k_slab(nsf):

@@ -8,6 +8,23 @@ Each stage is compared with the oracle fed the GPU's own inputs to that stage
   G2P x^{n+1} on S       1e-5 dx
   Gauss-Newton z (§5.3)  1e-4 max(1, |z|_inf)
 and the whole step end to end against the oracle's own step within 1e-4 on z.
+
+BF16 fields (tensor cores) are compared with the oracle's BF16 reading of the
+same networks (bf16 weights and product operands, float64 sums):
+  fields                 2e-3 relative
+  grid, G2P              as above (FP32 MPM)
+  normal equations       every Gauss-Newton iterate equals the float64 solve of
+                         (J^T J + lambda I) dz = -J^T res built from the
+                         library's own g and dg/dz at that iterate, to 1e-9
+  Gauss-Newton result    the objective of Eq. 9 decreases as the oracle's does
+                         to within 1e-3 of that decrease, and the fitted
+                         positions g(X_S, z) agree within 1e-2 dx.
+z itself is not compared value by value on the BF16 path: the random-init
+fields make Eq. 9 ill-conditioned (singular values of J span ~200x at the
+benchmark scene, the damping exceeds the smallest squared one), and bf16
+rounding of the activations moves the minimiser by as much as switching the
+oracle from its BF16 to its FP64 reading does (~5e-3 in z, ~4e-3 dx in the
+fitted positions); z is only checked against gross error (5e-2).
 """
 
 import numpy as np
@@ -22,6 +39,11 @@ pytestmark = pytest.mark.gpu
 GRID_TOL = 1e-5
 FIELD_TOL = 1e-5
 Z_TOL = 1e-4
+BF16_FIELD_TOL = 2e-3
+NORMAL_EQ_TOL = 1e-9
+OBJ_DECREASE_TOL = 1e-3
+POS_TOL_DX = 1e-2
+BF16_Z_GROSS = 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -83,7 +105,8 @@ def _run_step(nsf, sc, z0, zp, nsteps=1, taps=True, t0=0.0, iters=None):
     return out, st
 
 
-def _check_stages(sc, z0, zp, out, t0=0.0, field_tol=FIELD_TOL, z_tol=Z_TOL, z_exact=True):
+def _check_stages(sc, z0, zp, out, t0=0.0, bf16=False):
+    field_tol = BF16_FIELD_TOL if bf16 else FIELD_TOL
     of = oracle_fields(sc.fields)
     og = oracle_grid(sc.grid)
     X = sc.X.astype(np.float64)
@@ -134,20 +157,28 @@ def _check_stages(sc, z0, zp, out, t0=0.0, field_tol=FIELD_TOL, z_tol=Z_TOL, z_e
         dz = np.linalg.solve(A, -Jm.T @ res.reshape(-1))
         expect = z_in + dz
         err = np.abs(out["z_iter"][k] - expect).max() / max(1.0, np.abs(expect).max())
-        assert err < 1e-5, (k, err)
+        # float64 on the FP32 path, float-float (~48-bit) sums and solve on the
+        # BF16 path: both at float64 level for these systems
+        assert err < (NORMAL_EQ_TOL if bf16 else 1e-5), (k, err)
         z_in = out["z_iter"][k]
-    if z_exact:
-        assert np.abs(out["z_iter"] - np.array(hist)).max() < z_tol * scale
-        assert np.abs(out["z"] - z).max() < z_tol * scale
+    if not bf16:
+        assert np.abs(out["z_iter"] - np.array(hist)).max() < Z_TOL * scale
+        assert np.abs(out["z"] - z).max() < Z_TOL * scale
     else:
-        # BF16 fields: weakly determined latent directions amplify bf16 rounding
-        # differences, so z itself is reported; the GPU's z must be as good a
-        # minimiser of Eq. 9 as the oracle's (objective within 1e-3 relative)
+        # Eq. 9 on the step's own target: the GPU's 5 iterations must take the
+        # objective down as far as the oracle's do, and fit the same positions
         target = X[:nS] + out["u_next_S"].T
-        f_gpu = ((of.g.value(X[:nS], out["z"]) - target) ** 2).sum()
-        f_ora = ((of.g.value(X[:nS], z) - target) ** 2).sum()
-        print(f"objective gpu {f_gpu:.6e} oracle {f_ora:.6e}")
-        assert f_gpu <= f_ora * (1 + z_tol) + 1e-18
+        g_gpu, g_ora = of.g.value(X[:nS], out["z"]), of.g.value(X[:nS], z)
+        f_gpu = ((g_gpu - target) ** 2).sum()
+        f_ora = ((g_ora - target) ** 2).sum()
+        f_0 = ((of.g.value(X[:nS], z0) - target) ** 2).sum()
+        pos_dx = np.abs(g_gpu - g_ora).max() / sc.grid.dx
+        print(f"objective start {f_0:.6e} oracle {f_ora:.6e} gpu {f_gpu:.6e}; fitted positions "
+              f"{pos_dx:.3e} dx; |z_gpu - z_oracle| {np.abs(out['z'] - z).max():.3e}")
+        assert f_0 > 10 * f_ora          # a step the fit resolves (not BF16 noise)
+        assert f_gpu - f_ora <= OBJ_DECREASE_TOL * (f_0 - f_ora)
+        assert pos_dx < POS_TOL_DX
+        assert np.abs(out["z"] - z).max() < BF16_Z_GROSS * scale
     np.testing.assert_array_equal(out["z_prev"], z0)
     return z
 
@@ -205,9 +236,11 @@ def test_latent_step_config3_scale_bf16(nsf, width, depth, r):
         sc = latent_scene(2400 + r, 3000, 300, r, width, depth, "bf16", sc.grid, 5e-5,
                           X=sc.X[:3000], E=2e5, vol_total=sc.vol0 * 200000,
                           n_total=200000)
-    zp = _perturbed_prev(sc, 4, eps=1e-3)
+    # a latent velocity that moves the sample particles ~5e-2 dx in the step,
+    # well above the BF16 resolution of the field (~3e-3 dx)
+    zp = _perturbed_prev(sc, 4, eps=5e-2)
     out, _ = _run_step(nsf, sc, sc.z0, zp)
-    _check_stages(sc, sc.z0, zp, out, field_tol=2e-3, z_tol=0.5, z_exact=False)
+    _check_stages(sc, sc.z0, zp, out, bf16=True)
 
 
 def test_latent_step_bf16_more_sample_tiles_than_ctas(nsf):
@@ -219,9 +252,22 @@ def test_latent_step_bf16_more_sample_tiles_than_ctas(nsf):
     base = latent_config3(precision="bf16", width=64, depth=3)
     sc = latent_scene(2405, 3000, 2500, 6, 64, 3, "bf16", base.grid, 5e-5,
                       X=base.X[:3000], E=2e5, vol_total=base.vol0 * 200000, n_total=200000)
-    zp = _perturbed_prev(sc, 5, eps=1e-3)
+    zp = _perturbed_prev(sc, 5, eps=5e-2)
     out, _ = _run_step(nsf, sc, sc.z0, zp)
-    _check_stages(sc, sc.z0, zp, out, field_tol=2e-3, z_tol=0.5, z_exact=False)
+    _check_stages(sc, sc.z0, zp, out, bf16=True)
+
+
+def test_bf16_steps_are_reproducible_bit_for_bit(nsf):
+    # P2G sums are fixed-point integers (order-free) and the tensor-core
+    # Gauss-Newton combines its CTAs' float-float sums in a fixed order, so
+    # the BF16 step of the benchmark scene gives the same z on every run
+    sc = latent_config3(precision="bf16")
+    zp = _perturbed_prev(sc, 6, eps=5e-2)
+    a, _ = _run_step(nsf, sc, sc.z0, zp, nsteps=2, taps=False)
+    b, _ = _run_step(nsf, sc, sc.z0, zp, nsteps=2, taps=False)
+    assert a["status"] == 0 and b["status"] == 0
+    np.testing.assert_array_equal(a["z"], b["z"])
+    np.testing.assert_array_equal(a["z_prev"], b["z_prev"])
 
 
 def test_multi_step_matches_repeated_single_steps(nsf):
@@ -251,8 +297,8 @@ def test_reuse_prev_flag_continues_a_call(nsf):
     st.step(z, zpv, sc.dt, t0=sc.dt, nsteps=1, reuse_prev=True)
     torch.cuda.synchronize()
     assert st.read_status() == 0
-    # float32 atomics in P2G make two runs differ slightly; weakly determined
-    # latent directions amplify that
+    # the FP32 path's Gauss-Newton adds float64 partials with atomics, whose
+    # order varies from run to run
     assert np.abs(z.cpu().numpy() - a["z"]).max() < Z_TOL
     assert np.abs(zpv.cpu().numpy() - a["z_prev"]).max() < Z_TOL
 

@@ -103,7 +103,11 @@ def test_latent_step_closed_form_translation(rng):
 
 
 def test_latent_mpm_substep_equals_full_order_step(rng):
-    # §5.2: integrating all particles reproduces the full-order x^{n+1} exactly.
+    # §5.2: a latent MPM sub-step on N = P, fed the full-order state (x, v,
+    # tau(F) as the stress field's output, C as the affine field's output),
+    # moves every particle to the x^{n+1} of mpm.full_step on the same state,
+    # whose transfers are pinned against brute force and closed forms in
+    # test_oracle_mpm.py.
     grid = mpm.Grid((16, 16, 16), 1.0 / 16, gravity=(0, 0, -9.8), wall_cells=3)
     n = 150
     x = rng.uniform(0.3, 0.7, size=(n, 3))
@@ -111,14 +115,17 @@ def test_latent_mpm_substep_equals_full_order_step(rng):
     C = rng.normal(size=(n, 3, 3))
     F = np.eye(3) + 0.03 * rng.normal(size=(n, 3, 3))
     mat = constitutive.Material("neo_hookean", 1e4, 0.3)
-    tau = mat.stress(F)
     dt, mass, vol0 = 1e-4, 1e-3, 1e-6
-    m, p, _ = mpm.p2g(x, v, C, tau, mass, vol0, dt, grid)
-    vg = mpm.grid_update(m, p, dt, grid)
-    x_full, _ = mpm.g2p(x, vg, dt, grid)
-    sub = latent.mpm_substep(x, v, fields.sym_to_voigt(tau), C.reshape(n, 9), mass, vol0,
-                             dt, grid, 0.0, n)
-    np.testing.assert_array_equal(sub["x_next_S"], x_full)
+    full = mpm.full_step(x, v, C, F, mass, vol0, dt, grid, mat)
+    sub = latent.mpm_substep(x, v, fields.sym_to_voigt(mat.stress(F)), C.reshape(n, 9), mass,
+                             vol0, dt, grid, 0.0, n)
+    assert full["in_grid"] and sub["in_grid"]
+    np.testing.assert_array_equal(sub["x_next_S"], full["x"])
+    np.testing.assert_array_equal(sub["v_grid"], full["v_grid"])
+    # a prefix S of N gets the same positions (only S is read after G2P)
+    sub_S = latent.mpm_substep(x, v, fields.sym_to_voigt(mat.stress(F)), C.reshape(n, 9), mass,
+                               vol0, dt, grid, 0.0, 40)
+    np.testing.assert_array_equal(sub_S["x_next_S"], full["x"][:40])
 
 
 def test_too_few_sample_particles_is_singular_without_damping(rng):

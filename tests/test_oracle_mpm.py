@@ -220,3 +220,86 @@ def test_full_step_conserves_linear_and_angular_momentum(rng):
     P1, L1 = mpm.momentum(xn, vp, Cp, mass, g.dx)
     np.testing.assert_allclose(P1, P0, rtol=1e-11, atol=1e-13)
     np.testing.assert_allclose(L1, L0, rtol=1e-10, atol=1e-13)
+
+
+def _no_stress():
+    # E = 0: mu = lambda = 0, so tau(F) = 0 for any F (no grid force)
+    return constitutive.Material("neo_hookean", 0.0, 0.3)
+
+
+@pytest.mark.parametrize("grad", ["mls", "bspline"])
+def test_full_step_affine_velocity_updates_F_in_closed_form(grad):
+    # Particles moving with an affine velocity v = A x + b (C_p = A) and no
+    # stress: P2G gives p_i = m_i (A x_i + b) exactly (first moment identity),
+    # so v_i = A x_i + b, G2P returns v_p = A x_p + b and C_p = A (second
+    # moment identity), the B-spline velocity gradient is A as well, and F
+    # advects to the closed form (I + dt A) F for any F.
+    rng = np.random.Generator(np.random.PCG64(601))
+    g = _grid(n=16, dx=1.0 / 16)
+    n = 120
+    x = rng.uniform(0.3, 0.7, size=(n, 3))
+    A = rng.normal(size=(3, 3))                       # not symmetric
+    b = rng.normal(size=3)
+    v = x @ A.T + b
+    C = np.broadcast_to(A, (n, 3, 3)).copy()
+    F = np.eye(3) + 0.2 * rng.normal(size=(n, 3, 3))
+    dt = 1e-3
+    out = mpm.full_step(x, v, C, F, 1e-3, 1e-6, dt, g, _no_stress(), grad=grad)
+    assert out["in_grid"]
+    np.testing.assert_allclose(out["v"], v, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out["x"], x + dt * v, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(out["C"], C, rtol=0, atol=1e-10)
+    expect_F = np.einsum("ij,njk->nik", np.eye(3) + dt * A, F)
+    np.testing.assert_allclose(out["F"], expect_F, rtol=0, atol=1e-13)
+    # a transposed update, F (I + dt A), would be off by dt |A F - F A| ~ 1e-3
+    assert np.abs(np.einsum("nij,jk->nik", F, np.eye(3) + dt * A) - out["F"]).max() > 1e-5
+
+
+def test_full_step_rigid_translation_leaves_F_unchanged():
+    # F = I has zero neo-Hookean stress, a uniform velocity has zero gradient:
+    # every particle translates by dt v and F stays the identity.
+    rng = np.random.Generator(np.random.PCG64(602))
+    g = _grid(n=16, dx=1.0 / 16)
+    n = 90
+    x = rng.uniform(0.3, 0.7, size=(n, 3))
+    b = rng.normal(size=3)
+    v = np.broadcast_to(b, (n, 3)).copy()
+    F = np.broadcast_to(np.eye(3), (n, 3, 3)).copy()
+    mat = constitutive.Material("neo_hookean", 1e5, 0.3)
+    out = mpm.full_step(x, v, np.zeros((n, 3, 3)), F, 1e-3, 1e-6, 1e-4, g, mat)
+    np.testing.assert_allclose(out["x"], x + 1e-4 * b, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(out["F"], F, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(out["C"], 0.0, atol=1e-11)
+
+
+def test_full_step_von_mises_lands_on_the_yield_surface():
+    # App. F.4 inside the step: a particle whose trial strain is past the yield
+    # surface ends with ||dev eps(F^E)|| = tau_y / (2 mu) and the same volume;
+    # one inside keeps F_trial, and F_trial = (I + dt C_p) F (MLS form).
+    rng = np.random.Generator(np.random.PCG64(603))
+    g = _grid(n=16, dx=1.0 / 16)
+    n = 200
+    x = rng.uniform(0.3, 0.7, size=(n, 3))
+    v = 0.05 * rng.normal(size=(n, 3))
+    C = rng.normal(size=(n, 3, 3))
+    F = np.eye(3) + 0.03 * rng.normal(size=(n, 3, 3))
+    mat = constitutive.Material("von_mises", 1e4, 0.3, yield_stress=300.0)
+    dt = 1e-4
+    out = mpm.full_step(x, v, C, F, 1e-3, 1e-6, dt, g, mat)
+    np.testing.assert_allclose(out["F_trial"], np.einsum("nij,njk->nik",
+                                                         np.eye(3) + dt * out["C"], F),
+                               rtol=0, atol=1e-14)
+
+    def dev_norm_and_trace(M):
+        _, s, _ = constitutive.svd3(M)
+        e = np.log(np.abs(s))
+        return np.linalg.norm(e - e.mean(1, keepdims=True), axis=1), e.sum(1)
+
+    d_tr, tr_tr = dev_norm_and_trace(out["F_trial"])
+    d_new, tr_new = dev_norm_and_trace(out["F"])
+    ry = mat.yield_stress / (2 * mat.mu)
+    yielded = d_tr > ry
+    assert 0.1 < yielded.mean() < 0.9
+    np.testing.assert_allclose(d_new[yielded], ry, rtol=1e-9)
+    np.testing.assert_allclose(tr_new, tr_tr, atol=1e-12)
+    np.testing.assert_allclose(out["F"][~yielded], out["F_trial"][~yielded], atol=1e-14)
