@@ -66,15 +66,16 @@ GridParams make_params(const nsf_grid_desc *g) {
 }
 
 // Grid part of a workspace.  The particle buckets hold up to `cap` particle
-// indices per particle block (min(cap_max, n)); particles past that go to the
-// overflow list, which every grid block's P2G scans (correct, but slow if
-// large), so cap_max is set well above the densest expected packing (8
+// indices per particle block (min(cap_max, n)); particles past that go to an
+// overflow list and add their contributions with global atomics (correct,
+// but slower), so cap_max is set well above the densest expected packing (8
 // particles per cell fill a block with 512).
-constexpr int kBucketCapScene = 1024;
+constexpr int kBucketCapScene = kMaxBucketCap;
 constexpr int kBucketCapBatch = 256;
+static_assert(kBucketCapBatch <= kMaxBucketCap, "bucket capacity");
 
 struct GridLayout {
-    size_t vel, gstamp, bcount, bucket, rec, plist, glist, over, ctl;
+    size_t acc, vel, gstamp, bcount, bucket, rec, plist, glist, over, ctl;
     int nblocks, max_pblocks, max_gblocks, cap;
 };
 
@@ -87,6 +88,7 @@ GridLayout carve_grid(Carver &c, const nsf_grid_desc *g, int n, int cap_max) {
     L.max_gblocks = mg < L.nblocks ? (int)mg : L.nblocks;
     L.cap = n < cap_max ? n : cap_max;
     L.ctl = c.take(sizeof(Ctl));
+    L.acc = c.take(nodes * 4 * sizeof(unsigned long long));
     L.vel = c.take(nodes * sizeof(float4));
     L.gstamp = c.take((size_t)L.nblocks * 4);
     L.bcount = c.take((size_t)L.nblocks * 4);
@@ -108,6 +110,7 @@ GridWs grid_ws(char *base, const GridLayout &L, const nsf_grid_desc *g, int n) {
     w.nb1 = w.n1 / 4;
     w.nb2 = w.n2 / 4;
     w.nblocks = L.nblocks;
+    w.acc = reinterpret_cast<unsigned long long *>(base + L.acc);
     w.vel = reinterpret_cast<float4 *>(base + L.vel);
     w.gstamp = reinterpret_cast<int *>(base + L.gstamp);
     w.bcount = reinterpret_cast<int *>(base + L.bcount);

@@ -70,6 +70,8 @@ __host__ __device__ __forceinline__ int tri_index(int i, int j, int r) {
 
 // Quadratic B-spline stencil along one axis (§3.2, b = 2):
 // base = floor(s - 0.5) with s = x / dx, fx = s - base in [0.5, 1.5).
+// s and s - 0.5 are rounded explicitly (no multiply-add contraction), so every
+// kernel that bins, scatters or gathers a particle finds the same base node.
 struct Axis {
     int base;
     float fx;
@@ -78,9 +80,9 @@ struct Axis {
 
 __device__ __forceinline__ Axis bspline_axis(float x, float inv_dx) {
     Axis a;
-    float s = x * inv_dx;
-    a.base = __float2int_rd(s - 0.5f);
-    a.fx = s - (float)a.base;
+    const float s = __fmul_rn(x, inv_dx);
+    a.base = __float2int_rd(__fsub_rn(s, 0.5f));
+    a.fx = __fsub_rn(s, (float)a.base);
     float t0 = 1.5f - a.fx, t1 = a.fx - 1.0f, t2 = a.fx - 0.5f;
     a.w[0] = 0.5f * t0 * t0;
     a.w[1] = 0.75f - t1 * t1;

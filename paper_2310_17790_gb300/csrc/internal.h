@@ -71,11 +71,17 @@ struct Ctl {
 // block-linear: 4x4x4-node blocks, block (bx, by, bz) at
 // ((bx * nb1 + by) * nb2 + bz), node (lx, ly, lz) inside at (lx * 4 + ly) * 4 + lz.
 // A particle belongs to the block of its stencil base node ("particle
-// block"); its stencil reaches that grid block and the next one along each
-// axis.
+// block"); its stencil reaches the 6^3 nodes from that block's first node on,
+// i.e. that grid block and the next one along each axis.
+// Largest bucket capacity per particle block.  The P2G tile of a block sums
+// at most this many contributions per node, which bounds its 32-bit partial
+// sums (mpm.cu).
+constexpr int kMaxBucketCap = 1024;
+
 struct GridWs {
     int n0, n1, n2;
     int nb0, nb1, nb2, nblocks;
+    unsigned long long *acc;   // [nodes][4] fixed-point (m, p) sums; zero between steps
     float4 *vel;        // (v, m) after the grid update; valid on the step's active blocks
     int *gstamp;        // epoch stamp of each grid block
     int *bcount;        // particles binned to each particle block; zero between steps

@@ -10,27 +10,27 @@
 //            particle block (the block of its stencil base node): a warp
 //            aggregates the lanes that share a block (match, popc) into one
 //            counter atomic whose old value gives each lane its slot in the
-//            block's bucket.  The first arrival in a block lists it and
-//            stamps the 8 grid blocks its stencils can reach.
-//   P2G +    each active grid block is owned by one group of threads, which
-//   grid     gathers the particles of the 8 particle blocks that reach it
-//            from their buckets, accumulates their contributions to its 64
-//            nodes in shared memory, then turns each node's (m, p) into
-//            v = p / m + dt g with the walls and the blade, and writes v
-//            once.  No grid value goes through a global atomic.
+//            block's bucket; the first arrival in a block lists it.
+//   P2G      each listed particle block is taken by one group of threads:
+//            its particles' 27 node contributions are summed in the block's
+//            6^3-node tile in shared memory, then every nonzero node of the
+//            tile is added once to the grid (one integer atomic per value),
+//            and the 8 grid blocks the tile covers are activated.
+//   grid     v = p / m + dt g, walls, blade, over the activated grid blocks;
+//            the sums are cleared on the way.
 //   G2P      latent: x^{n+1} on the sample particles, in the same launch;
 //            full-order: a separate launch (its float64 return map needs
 //            far more registers than the other phases).
 //
-// Sums are exact.  Every node contribution is rounded once to a 64-bit fixed
-// point number (mass on a scale from the particle mass, momentum on a scale
-// from this step's largest contribution bound, reduced warp by warp in the
-// bin phase) and added as an integer, so a node's total does not depend on
-// the order of the additions: the step is bit-for-bit reproducible.  A
-// contribution of the bounding size maps to < 2^44, leaving 2^19 such
-// contributions of headroom per node; the resolution is 2^-44 of the largest
-// contribution (a smaller one than float32 rounding of a sum of similar
-// terms gives).
+// Sums are exact.  Every node contribution is rounded once to a fixed-point
+// integer (mass on a scale from the particle mass, momentum on a scale from
+// this step's largest contribution bound, reduced warp by warp in the bin
+// phase) and added as an integer, so a node's total does not depend on the
+// order of the additions: the step is bit-for-bit reproducible.  A
+// contribution of the bounding size maps to < 2^40 (2^23 such contributions
+// of headroom per node in the 64-bit grid sums); the resolution is 2^-40 of
+// the largest contribution, finer than float32 rounding of a sum of similar
+// terms.
 
 #include "constitutive.cuh"
 #include "device_common.cuh"
@@ -134,12 +134,13 @@ __device__ __forceinline__ void load_particle(const P2gFullArgs &a, float stress
 }
 
 // Particle block (4^3 cells, by stencil base node) of position x, or -1 when
-// the 3^3 stencil leaves the grid (status set).
+// the 3^3 stencil leaves the grid (status set).  The base nodes are those of
+// bspline_axis, which the scatter uses too.
 __device__ __forceinline__ int block_key(const GridWs &g, const float x[3], float inv_dx,
                                          int *status) {
-    const int b0 = __float2int_rd(x[0] * inv_dx - 0.5f);
-    const int b1 = __float2int_rd(x[1] * inv_dx - 0.5f);
-    const int b2 = __float2int_rd(x[2] * inv_dx - 0.5f);
+    const int b0 = bspline_axis(x[0], inv_dx).base;
+    const int b1 = bspline_axis(x[1], inv_dx).base;
+    const int b2 = bspline_axis(x[2], inv_dx).base;
     const bool fin = finite3(x[0], x[1], x[2]);
     const bool ok = fin && b0 >= 0 && b1 >= 0 && b2 >= 0 && b0 + 2 <= g.n0 - 1 &&
                     b1 + 2 <= g.n1 - 1 && b2 + 2 <= g.n2 - 1;
@@ -171,7 +172,16 @@ __device__ __forceinline__ float4 node_contribution(const P2gParticle &q, const 
 // ------------------------------------------------------- fixed point ----
 // A contribution of the bounding magnitude maps to < 2^kFixBits (integer
 // sums of up to 2^(63 - kFixBits) of them cannot overflow).
-constexpr int kFixBits = 44;
+constexpr int kFixBits = 40;
+// In a particle block's tile each fixed-point value q is kept as two 32-bit
+// sums, of lo = q mod 2^kLoBits (unsigned) and hi = floor(q / 2^kLoBits)
+// (signed), so that it can use the native 32-bit shared-memory reductions:
+// with at most kMaxTileAdds additions per node (the bucket capacity) neither
+// sum can overflow, and the exact total is hi 2^kLoBits + lo.
+constexpr int kLoBits = 22;
+constexpr int kMaxTileAdds = kMaxBucketCap;
+static_assert((long long)kMaxTileAdds * ((1ll << kLoBits) - 1) < (1ll << 32), "lo sums fit");
+static_assert((long long)kMaxTileAdds << (kFixBits - kLoBits) < (1ll << 31), "hi sums fit");
 
 // 2^(kFixBits - e) for the exponent e with bound < 2^e (a power of two, so
 // scaling by it and by its reciprocal is exact); kept inside the normal range.
@@ -189,6 +199,28 @@ __device__ __forceinline__ unsigned long long to_fix(float v, float scale) {
 
 __device__ __forceinline__ float from_fix(unsigned long long q, float inv_scale) {
     return __ll2float_rn((long long)q) * inv_scale;
+}
+
+// Adds the fixed-point value of v (q = rint(v scale), as to_fix) to the (lo,
+// hi) pair of 32-bit sums at the shared-window addresses lo_addr, hi_addr.
+// The split is formed in float32 arithmetic, all exact: t = rint(v scale) is
+// an integer below 2^kFixBits in magnitude, hi = floor(t / 2^kLoBits) and
+// lo = t - hi 2^kLoBits, an integer in [0, 2^kLoBits) (one fused multiply-add
+// with an exactly representable result).
+__device__ __forceinline__ void red_shared_split(uint32_t lo_addr, uint32_t hi_addr, float v,
+                                                 float scale) {
+    const float t = rintf(v * scale);
+    const float hf = floorf(t * (1.f / (float)(1u << kLoBits)));
+    const float lf = fmaf(-hf, (float)(1u << kLoBits), t);
+    const unsigned lo = (unsigned)__float2int_rn(lf);
+    const int hi = __float2int_rn(hf);
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(lo_addr), "r"(lo) : "memory");
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(hi_addr), "r"(hi) : "memory");
+}
+
+// The fixed-point total of a (lo, hi) pair of sums.
+__device__ __forceinline__ unsigned long long split_total(unsigned lo, int hi) {
+    return (unsigned long long)(((long long)hi << kLoBits) + (long long)lo);
 }
 
 // Largest |component| of any node contribution of q: w <= 1 and
@@ -215,26 +247,24 @@ __device__ __forceinline__ void store_record(float4 *rec, int p, const P2gPartic
 }
 
 // ----------------------------------------------------------- binning ----
-// Stamps the grid blocks (kx..kx+1, ky..ky+1, kz..kz+1) that the stencils of
-// particle block `key` reach; the first stamp of this step lists the block.
-__device__ __forceinline__ void activate_grid_blocks(const GridWs &g, int key, int epoch,
-                                                     StepCtl &st) {
-    const int kz = key % g.nb2, t = key / g.nb2, ky = t % g.nb1, kx = t / g.nb1;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        const int cx = kx + (d >> 2), cy = ky + ((d >> 1) & 1), cz = kz + (d & 1);
-        if (cx >= g.nb0 || cy >= g.nb1 || cz >= g.nb2) continue;
-        const int gb = (cx * g.nb1 + cy) * g.nb2 + cz;
-        if (atomicExch(&g.gstamp[gb], epoch) != epoch) g.glist[atomicAdd(&st.n_g, 1)] = gb;
-    }
+// Grid block (kx, ky, kz) + corner d (d = 0 .. 7 over {0,1}^3), one of the 8
+// that the stencils of particle block (kx, ky, kz) reach: stamped with the
+// step's epoch; the first stamp of the step lists it.
+__device__ __forceinline__ void activate_grid_block(const GridWs &g, int kx, int ky, int kz,
+                                                    int d, int epoch) {
+    const int cx = kx + (d >> 2), cy = ky + ((d >> 1) & 1), cz = kz + (d & 1);
+    if (cx >= g.nb0 || cy >= g.nb1 || cz >= g.nb2) return;
+    const int gb = (cx * g.nb1 + cy) * g.nb2 + cz;
+    if (atomicExch(&g.gstamp[gb], epoch) != epoch)
+        g.glist[atomicAdd(&g.ctl->st[epoch & 1].n_g, 1)] = gb;
 }
 
 // Bin particle p (p < 0: no particle) of scene `tag` (0 for a single scene).
-// Every lane of the warp calls (the match below is warp-wide).  The lanes
+// Every lane of the warp calls (the matches below are warp-wide).  The lanes
 // that share a particle block form a group: one counter atomic for the group
-// (its old value plus the lane's rank in the group is the lane's bucket slot),
-// one atomicMax of the group's largest contribution bound, and the group
-// that finds the block empty lists it and activates its grid blocks.
+// (its old value plus the lane's rank in the group is the lane's bucket
+// slot), and the group that finds the block empty lists it.  The step's
+// contribution bound is reduced over the warp first.
 template <class Args>
 __device__ __forceinline__ void bin_particle(const GridWs &g, const GridParams &gp,
                                              const Args &a, float stress_k, int tag, int p,
@@ -256,21 +286,21 @@ __device__ __forceinline__ void bin_particle(const GridWs &g, const GridParams &
             }
         }
     }
+    StepCtl &st = g.ctl->st[epoch & 1];
+    // the step's contribution bound: one max over the warp's lanes of each
+    // scene, one atomic per scene and warp
+    const unsigned same_scene = __match_any_sync(0xffffffffu, tag);
+    const unsigned bmax = __reduce_max_sync(same_scene, key >= 0 ? __float_as_uint(bnd) : 0u);
+    if (lane == __ffs(same_scene) - 1 && bmax) atomicMax(&st.bound, bmax);
     const unsigned long long gkey =
         key < 0 ? ~0ull : (((unsigned long long)(unsigned)tag << 32) | (unsigned)key);
     const unsigned peers = __match_any_sync(0xffffffffu, gkey);
     if (key < 0) return;
     const int leader = __ffs(peers) - 1;
-    const unsigned bmax = __reduce_max_sync(peers, __float_as_uint(bnd));
-    StepCtl &st = g.ctl->st[epoch & 1];
     int old = 0;
     if (lane == leader) {
         old = atomicAdd(&g.bcount[key], __popc(peers));
-        atomicMax(&st.bound, bmax);
-        if (old == 0) {
-            g.plist[atomicAdd(&st.n_p, 1)] = key;
-            activate_grid_blocks(g, key, epoch, st);
-        }
+        if (old == 0) g.plist[atomicAdd(&st.n_p, 1)] = key;
     }
     old = __shfl_sync(peers, old, leader);
     const int rank = old + __popc(peers & ((1u << lane) - 1u));
@@ -278,23 +308,7 @@ __device__ __forceinline__ void bin_particle(const GridWs &g, const GridParams &
     else g.over[atomicAdd(&st.n_over, 1)] = p;
 }
 
-// --------------------------------------------------- P2G + grid update ----
-// Threads of one grid-block owner (a CTA runs kThreads / kOwnerThreads
-// owners side by side, each on its own named barrier).
-constexpr int kOwnerThreads = 64;      // one thread per node of the grid block
-constexpr int kOwners = kThreads / kOwnerThreads;
-static_assert(kOwnerThreads == 64 && kThreads % kOwnerThreads == 0, "owner layout");
-
-struct OwnerSmem {
-    unsigned long long acc[64 * 4];   // (m, p) of the block's 64 nodes, fixed point
-    int nb[8];                        // the 8 particle blocks that reach it (-1: none)
-    int off[9];                       // prefix of their particle counts
-};
-
-__device__ __forceinline__ void owner_sync(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kOwnerThreads) : "memory");
-}
-
+// --------------------------------------------------------------- P2G ----
 // Scales of one step's fixed-point sums.
 struct FixScales {
     float m, p, inv_m, inv_p;
@@ -309,42 +323,167 @@ __device__ __forceinline__ FixScales fix_scales(float mass, unsigned bound_bits)
     return s;
 }
 
-// Adds particle p's contributions to the nodes of grid block (ox, oy, oz) +
-// [0, 4)^3 (its stencil nodes inside that block) to the owner's sums.
-__device__ __forceinline__ void owner_add_particle(const GridWs &g, const GridParams &gp,
-                                                   float mass, const FixScales &fs, int p,
-                                                   int ox, int oy, int oz,
-                                                   unsigned long long *acc) {
-    const float4 *r = g.rec + 4 * (size_t)p;
-    const float4 r0 = __ldcg(r);
-    const Axis ax = bspline_axis(r0.x, gp.inv_dx), ay = bspline_axis(r0.y, gp.inv_dx),
-               az = bspline_axis(r0.z, gp.inv_dx);
-    const int a0 = max(0, ox - ax.base), a1 = min(2, ox + 3 - ax.base);
-    const int b0 = max(0, oy - ay.base), b1 = min(2, oy + 3 - ay.base);
-    const int c0 = max(0, oz - az.base), c1 = min(2, oz + 3 - az.base);
-    if (a0 > a1 || b0 > b1 || c0 > c1) return;
-    const float4 r1 = __ldcg(r + 1), r2 = __ldcg(r + 2), r3 = __ldcg(r + 3);
-    P2gParticle q;
+__device__ __forceinline__ void unpack_record(const float4 *rec, int p, P2gParticle &q) {
+    const float4 *r = rec + 4 * (size_t)p;
+    const float4 r0 = __ldcg(r), r1 = __ldcg(r + 1), r2 = __ldcg(r + 2), r3 = __ldcg(r + 3);
     q.x[0] = r0.x; q.x[1] = r0.y; q.x[2] = r0.z;
     q.mv[0] = r0.w; q.mv[1] = r1.x; q.mv[2] = r1.y;
     q.Q[0] = r1.z; q.Q[1] = r1.w;
     q.Q[2] = r2.x; q.Q[3] = r2.y; q.Q[4] = r2.z; q.Q[5] = r2.w;
     q.Q[6] = r3.x; q.Q[7] = r3.y; q.Q[8] = r3.z;
-    const Stencil s{ax, ay, az};
-    for (int ia = a0; ia <= a1; ++ia)
-        for (int ib = b0; ib <= b1; ++ib)
-            for (int ic = c0; ic <= c1; ++ic) {
+}
+
+// Tile of a particle block: its 6^3 nodes from the block's first node on,
+// (m, p) as four fixed-point values per node, each a (lo, hi) pair of 32-bit
+// sums.  Word w (0 .. 7: lo m, hi m, lo px, hi px, ...) of node l sits at
+// w * kTileNodes + l: the lanes of one reduction touch the same word of
+// different nodes, which then fall in different banks (node-major words
+// would put all of them in 4 of the 32 banks).
+constexpr int kTileNodes = 216;
+constexpr int kTileWords = 8 * kTileNodes;
+
+// Adds the 27 node contributions of particle p (block origin o, in nodes) to
+// the tile at shared-window address `tile`.
+__device__ __forceinline__ void tile_add_particle(const GridWs &g, const GridParams &gp,
+                                                  float mass, const FixScales &fs, int p,
+                                                  int ox, int oy, int oz, uint32_t tile,
+                                                  int *status) {
+    P2gParticle q;
+    unpack_record(g.rec, p, q);
+    const Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
+                    bspline_axis(q.x[2], gp.inv_dx)};
+    const int lx = s.ax.base - ox, ly = s.ay.base - oy, lz = s.az.base - oz;   // 0 .. 3
+    if ((unsigned)lx > 3u || (unsigned)ly > 3u || (unsigned)lz > 3u) {
+        // binned to another block than its stencil base: never expected (both
+        // come from bspline_axis); recorded and skipped rather than written
+        // outside the tile
+        set_status(status, NSF_ERR_OUT_OF_GRID);
+        return;
+    }
+#pragma unroll
+    for (int ia = 0; ia < 3; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+            for (int ic = 0; ic < 3; ++ic) {
                 const float4 c = node_contribution(q, s, mass, gp.dx, ia, ib, ic);
-                const int l = ((ax.base + ia - ox) * 4 + (ay.base + ib - oy)) * 4 +
-                              (az.base + ic - oz);
-                unsigned long long *n = acc + 4 * l;
-                atomicAdd(n + 0, to_fix(c.x, fs.m));
+                const int l = ((lx + ia) * 6 + (ly + ib)) * 6 + (lz + ic);
+                constexpr uint32_t W = 4u * kTileNodes;          // bytes per word array
+                const uint32_t n = tile + 4u * (uint32_t)l;
+                red_shared_split(n, n + W, c.x, fs.m);
+                red_shared_split(n + 2u * W, n + 3u * W, c.y, fs.p);
+                red_shared_split(n + 4u * W, n + 5u * W, c.z, fs.p);
+                red_shared_split(n + 6u * W, n + 7u * W, c.w, fs.p);
+            }
+}
+
+// Particle p's 27 contributions straight into the grid's fixed-point sums
+// (particles past their block's bucket capacity).
+__device__ __forceinline__ void grid_add_particle(const GridWs &g, const GridParams &gp,
+                                                  float mass, const FixScales &fs, int p) {
+    P2gParticle q;
+    unpack_record(g.rec, p, q);
+    const Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
+                    bspline_axis(q.x[2], gp.inv_dx)};
+#pragma unroll
+    for (int ia = 0; ia < 3; ++ia)
+#pragma unroll
+        for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+            for (int ic = 0; ic < 3; ++ic) {
+                const float4 c = node_contribution(q, s, mass, gp.dx, ia, ib, ic);
+                unsigned long long *n =
+                    g.acc + 4 * (size_t)node_addr(g, s.ax.base + ia, s.ay.base + ib, s.az.base + ic);
+                atomicAdd(n, to_fix(c.x, fs.m));
                 atomicAdd(n + 1, to_fix(c.y, fs.p));
                 atomicAdd(n + 2, to_fix(c.z, fs.p));
                 atomicAdd(n + 3, to_fix(c.w, fs.p));
             }
 }
 
+// Group of TT threads (TT = 32: a warp; otherwise a named barrier) that runs
+// the tile of one particle block at a time.
+template <int TT>
+__device__ __forceinline__ void group_sync(int bar_id) {
+    if constexpr (TT == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(TT) : "memory");
+}
+
+// P2G of particle block `key`: its particles' contributions summed in the
+// tile (shared memory, exact integer sums), then every node of the tile with
+// a nonzero sum added once to the grid (integer atomics, so the order in
+// which tiles meet on their shared halo nodes does not matter).
+template <int TT>
+__device__ __forceinline__ void tile_block(const GridWs &g, const GridParams &gp, float mass,
+                                           const FixScales &fs, int key, int epoch,
+                                           unsigned long long *tile, int gt, int bar_id,
+                                           int *status) {
+    const int kz = key % g.nb2, t = key / g.nb2, ky = t % g.nb1, kx = t / g.nb1;
+    const int ox = kx * 4, oy = ky * 4, oz = kz * 4;
+    for (int i = gt; i < kTileWords / 2; i += TT) tile[i] = 0ull;
+    group_sync<TT>(bar_id);
+    const int np = min(__ldcg(&g.bcount[key]), g.cap);
+    const int *bk = g.bucket + (size_t)key * g.cap;
+    const uint32_t ts = (uint32_t)__cvta_generic_to_shared(tile);
+    for (int k = gt; k < np; k += TT)
+        tile_add_particle(g, gp, mass, fs, __ldcg(&bk[k]), ox, oy, oz, ts, status);
+    group_sync<TT>(bar_id);
+    if (gt < 8) activate_grid_block(g, kx, ky, kz, gt, epoch);
+    const unsigned *tw = reinterpret_cast<const unsigned *>(tile);
+    for (int l = gt; l < kTileNodes; l += TT) {
+        unsigned h[8];
+        unsigned any = 0u;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            h[w] = tw[w * kTileNodes + l];
+            any |= h[w];
+        }
+        if (any == 0u) continue;
+        const ulonglong2 v0 = make_ulonglong2(split_total(h[0], (int)h[1]),
+                                              split_total(h[2], (int)h[3]));
+        const ulonglong2 v1 = make_ulonglong2(split_total(h[4], (int)h[5]),
+                                              split_total(h[6], (int)h[7]));
+        // a nonzero sum lies in some particle's stencil, inside the grid
+        const int i = ox + l / 36, j = oy + (l / 6) % 6, kk = oz + l % 6;
+        if (i >= g.n0 || j >= g.n1 || kk >= g.n2) {
+            set_status(status, NSF_ERR_OUT_OF_GRID);
+            continue;
+        }
+        unsigned long long *n = g.acc + 4 * (size_t)node_addr(g, i, j, kk);
+        if (v0.x) atomicAdd(n, v0.x);
+        if (v0.y) atomicAdd(n + 1, v0.y);
+        if (v1.x) atomicAdd(n + 2, v1.x);
+        if (v1.y) atomicAdd(n + 3, v1.y);
+    }
+    group_sync<TT>(bar_id);
+}
+
+// Tiles of one CTA: kThreads / TT groups, each with its own tile.
+template <int TT>
+struct __align__(16) TileSmem {
+    unsigned long long tile[kThreads / TT][kTileWords / 2];   // 8 word arrays per tile
+};
+
+// P2G phase of a single scene: every listed particle block's tile, then the
+// overflow particles.
+template <int TT>
+__device__ void phase_p2g(const GridWs &g, const GridParams &gp, float mass, int epoch,
+                          TileSmem<TT> &sm, int *status) {
+    const StepCtl &st = g.ctl->st[epoch & 1];
+    constexpr int kGroups = kThreads / TT;
+    const int grp = threadIdx.x / TT, gt = threadIdx.x % TT;
+    const int n_p = __ldcg(&st.n_p), n_over = __ldcg(&st.n_over);
+    const FixScales fs = fix_scales(mass, __ldcg(&st.bound));
+    // group w of CTA c takes blocks w * gridDim.x + c, + all groups: a short
+    // list still spreads over every SM
+    for (int q = grp * gridDim.x + blockIdx.x; q < n_p; q += kGroups * gridDim.x)
+        tile_block<TT>(g, gp, mass, fs, __ldcg(&g.plist[q]), epoch, sm.tile[grp], gt, 1 + grp,
+                       status);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_over; u += gridDim.x * blockDim.x)
+        grid_add_particle(g, gp, mass, fs, __ldcg(&g.over[u]));
+}
+
+// --------------------------------------------------------------- grid ----
 // Grid update of node l (0 .. 63) of grid block gb from its (m, p) = a:
 // v = p / m + dt g, walls, blade, written with m to g.vel (§3.3).  Nodes
 // with m = 0 get v = 0 and no boundary condition.
@@ -382,66 +521,48 @@ __device__ __forceinline__ void grid_node_update(const GridWs &g, const GridPara
     if (tap_v) *reinterpret_cast<float4 *>(tap_v + nat) = v;
 }
 
-// One grid block gb owned by this thread group (gt: thread in the group):
-// gather, accumulate, grid update.  Every thread of the group calls.
-__device__ void owner_block(const GridWs &g, const GridParams &gp, float mass, float dt,
-                            double blade_z, const FixScales &fs, int n_over, int gb,
-                            OwnerSmem &sm, int gt, int bar_id, float *tap_mp, float *tap_v) {
-    const int bz = gb % g.nb2, t = gb / g.nb2, by = t % g.nb1, bx = t / g.nb1;
-    for (int i = gt; i < 64 * 4; i += kOwnerThreads) sm.acc[i] = 0ull;
-    if (gt < 8) {
-        const int kx = bx - (gt >> 2), ky = by - ((gt >> 1) & 1), kz = bz - (gt & 1);
-        int key = -1, c = 0;
-        if (kx >= 0 && ky >= 0 && kz >= 0) {
-            key = (kx * g.nb1 + ky) * g.nb2 + kz;
-            c = min(__ldcg(&g.bcount[key]), g.cap);
-        }
-        int v = c;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const int y = __shfl_up_sync(0xffu, v, o, 8);
-            if (gt >= o) v += y;
-        }
-        sm.nb[gt] = key;
-        sm.off[gt + 1] = v;
-        if (gt == 0) sm.off[0] = 0;
+// The fixed-point sums of node l of grid block gb as floats; the sums are
+// cleared for the next step on the way.
+__device__ __forceinline__ float4 take_node_sums(const GridWs &g, const FixScales &fs, int gb,
+                                                 int l) {
+    ulonglong2 *n = reinterpret_cast<ulonglong2 *>(g.acc + 4 * ((size_t)gb * 64 + l));
+    const ulonglong2 v0 = __ldcg(n), v1 = __ldcg(n + 1);
+    if ((v0.x | v0.y | v1.x | v1.y) != 0ull) {
+        n[0] = make_ulonglong2(0ull, 0ull);
+        n[1] = make_ulonglong2(0ull, 0ull);
     }
-    owner_sync(bar_id);
-    const int total = sm.off[8];
-    const int ox = bx * 4, oy = by * 4, oz = bz * 4;
-    for (int u = gt; u < total; u += kOwnerThreads) {
-        int d = 0;
-        while (u >= sm.off[d + 1]) ++d;
-        const int p = __ldcg(&g.bucket[(size_t)sm.nb[d] * g.cap + (u - sm.off[d])]);
-        owner_add_particle(g, gp, mass, fs, p, ox, oy, oz, sm.acc);
-    }
-    // particles that did not fit in their block's bucket (rare)
-    for (int u = gt; u < n_over; u += kOwnerThreads)
-        owner_add_particle(g, gp, mass, fs, __ldcg(&g.over[u]), ox, oy, oz, sm.acc);
-    owner_sync(bar_id);
-    {
-        const int l = gt;                          // kOwnerThreads == 64 nodes
-        const unsigned long long *n = sm.acc + 4 * l;
-        const float4 a = make_float4(from_fix(n[0], fs.inv_m), from_fix(n[1], fs.inv_p),
-                                     from_fix(n[2], fs.inv_p), from_fix(n[3], fs.inv_p));
-        grid_node_update(g, gp, dt, blade_z, gb, l, a, tap_mp, tap_v);
-    }
-    owner_sync(bar_id);
+    return make_float4(from_fix(v0.x, fs.inv_m), from_fix(v0.y, fs.inv_p),
+                       from_fix(v1.x, fs.inv_p), from_fix(v1.y, fs.inv_p));
 }
 
-// Owner loop of a single scene: grid blocks q = owner index, + all owners.
-__device__ void phase_p2g_grid(const GridWs &g, const GridParams &gp, float mass, float dt,
-                               double t, const StepCtl &st, float *tap_mp, float *tap_v) {
-    __shared__ OwnerSmem sm[kOwners];
-    const int grp = threadIdx.x / kOwnerThreads, gt = threadIdx.x % kOwnerThreads;
-    const int n_g = __ldcg(&st.n_g), n_over = __ldcg(&st.n_over);
+// Grid blocks a thread updates per pass: their index and node loads are
+// issued together, so a thread has kGridUnroll memory chains in flight
+// instead of one.
+constexpr int kGridUnroll = 4;
+
+__device__ void phase_grid(const GridWs &g, const GridParams &gp, float mass, float dt, double t,
+                           const StepCtl &st, float *tap_mp, float *tap_v) {
+    const int ngb = __ldcg(&st.n_g);
     const FixScales fs = fix_scales(mass, __ldcg(&st.bound));
+    const int per = blockDim.x >> 6;                 // grid blocks per CTA pass
+    const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+    const int stride = gridDim.x * per;
     const double blade_z = (double)gp.blade_z0 + (double)gp.blade_vz * t;
-    // owner w of CTA c is global owner w * gridDim.x + c: a short list still
-    // spreads over every SM
-    for (int q = grp * gridDim.x + blockIdx.x; q < n_g; q += kOwners * gridDim.x)
-        owner_block(g, gp, mass, dt, blade_z, fs, n_over, __ldcg(&g.glist[q]), sm[grp], gt,
-                    1 + grp, tap_mp, tap_v);
+    for (int i0 = sub * gridDim.x + blockIdx.x; i0 < ngb; i0 += kGridUnroll * stride) {
+        int gb[kGridUnroll];
+        float4 a[kGridUnroll];
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u) {
+            const int idx = i0 + u * stride;
+            gb[u] = idx < ngb ? __ldcg(&g.glist[idx]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u)
+            if (gb[u] >= 0) a[u] = take_node_sums(g, fs, gb[u], l);
+#pragma unroll
+        for (int u = 0; u < kGridUnroll; ++u)
+            if (gb[u] >= 0) grid_node_update(g, gp, dt, blade_z, gb[u], l, a[u], tap_mp, tap_v);
+    }
 }
 
 // Bin phase of a single scene.
@@ -473,17 +594,22 @@ __device__ __forceinline__ int begin_step(const GridWs &g) {
     return epoch;
 }
 
-// bin | barrier | P2G + grid update.  Returns false if the barrier timed out.
-// After the barrier (every CTA has read the old epoch) CTA 0 publishes the
-// step's epoch, which later launches of the step read.
-template <class Args>
+// bin | barrier | P2G tiles | barrier | grid update.  Returns false if a
+// barrier timed out.  After the first barrier (every CTA has read the old
+// epoch) CTA 0 publishes the step's epoch, which later launches of the step
+// read.
+template <int TT, class Args>
 __device__ bool bin_p2g_grid(const GridWs &g, const GridParams &gp, const Args &a, double t,
                              int epoch, float *tap_mp, float *tap_v, int *status) {
+    __shared__ TileSmem<TT> sm;
     const float stress_k = -a.dt * a.vol0 * 4.f * gp.inv_dx * gp.inv_dx;
     phase_bin(g, gp, a, stress_k, epoch, status);
     if (!grid_barrier(&g.ctl->bar, status)) return false;
     if (cta0_thread0()) g.ctl->epoch = epoch;
-    phase_p2g_grid(g, gp, a.mass, a.dt, t, g.ctl->st[epoch & 1], tap_mp, tap_v);
+    const StepCtl &st = g.ctl->st[epoch & 1];
+    phase_p2g<TT>(g, gp, a.mass, epoch, sm, status);
+    if (!grid_barrier(&g.ctl->bar, status)) return false;
+    phase_grid(g, gp, a.mass, a.dt, t, st, tap_mp, tap_v);
     return true;
 }
 
@@ -614,11 +740,18 @@ __device__ void phase_g2p_full(const GridWs &g, const GridParams &gp, const G2pF
 }
 
 // ------------------------------------------------------------- kernels ---
+// Threads per tile group: 64 for the sparse latent sets (a few particles per
+// block: four small tiles in flight per CTA), 128 for the dense full-order
+// slab (up to 512 particles per block).  Each tile takes 6.9 KB of shared
+// memory.
+constexpr int kTileThreadsLatent = 64;
+constexpr int kTileThreadsFull = 128;
+
 __global__ void __launch_bounds__(kThreads)
 k_mpm_latent(GridWs g, GridParams gp, P2gLatentArgs a, int n_S, double t, float *d_next,
              float *tap_mp, float *tap_v, int *status) {
     const int epoch = begin_step(g);
-    if (!bin_p2g_grid(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
+    if (!bin_p2g_grid<kTileThreadsLatent>(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
     if (!grid_barrier(&g.ctl->bar, status)) return;
     phase_g2p_latent(g, gp, a.X, a.u, a.n, n_S, a.dt, d_next, status);
     clear_bins(g, g.ctl->st[epoch & 1]);
@@ -628,7 +761,7 @@ __global__ void __launch_bounds__(kThreads)
 k_mpm_full(GridWs g, GridParams gp, P2gFullArgs a, double t, float *tap_mp, float *tap_v,
            int *status) {
     const int epoch = begin_step(g);
-    bin_p2g_grid(g, gp, a, t, epoch, tap_mp, tap_v, status);
+    bin_p2g_grid<kTileThreadsFull>(g, gp, a, t, epoch, tap_mp, tap_v, status);
 }
 
 // Full-order G2P, one thread per particle; it also clears the step's bucket
@@ -721,22 +854,23 @@ __device__ __forceinline__ P2gLatentArgs latent_args(const BatchSceneDev &sc, in
 
 
 // The MPM part of a batched latent step: every phase runs over all scenes at
-// once (a flat index over the scenes' particles, active grid blocks and
-// sample particles), with one grid barrier between phases for the whole
-// batch.  Each scene keeps its own counters, epoch and buckets.
+// once (a flat index over the scenes' particles, listed particle blocks,
+// active grid blocks and sample particles), with one grid barrier between
+// phases for the whole batch.  Each scene keeps its own counters, epoch,
+// buckets and fixed-point scales.
 __global__ void __launch_bounds__(kThreads, 4)
 k_mpm_batch(MpmBatchArgs b, int *status) {
     __shared__ int off[kMaxBatchScenes + 1];
     __shared__ int s_epoch[kMaxBatchScenes];
-    __shared__ OwnerSmem sm[kOwners];
+    __shared__ TileSmem<kTileThreadsLatent> sm;
+    constexpr int TT = kTileThreadsLatent, kGroups = kThreads / TT;
     const int ns = b.nscenes;
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     // every scene's step epoch, read before the first barrier; block 0 clears
     // each scene's other counter set
     for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) {
-        const Ctl *c = b.scenes[sc].g.ctl;
-        s_epoch[sc] = __ldcg(&c->epoch) + 1;
+        s_epoch[sc] = __ldcg(&b.scenes[sc].g.ctl->epoch) + 1;
         if (blockIdx.x == 0) b.scenes[sc].g.ctl->st[(s_epoch[sc] & 1) ^ 1] = StepCtl{0, 0, 0, 0u};
     }
     __syncthreads();
@@ -753,23 +887,68 @@ k_mpm_batch(MpmBatchArgs b, int *status) {
     if (!grid_barrier(b.bar, status)) return;
     if (blockIdx.x == 0)                         // every CTA has read them
         for (int sc = threadIdx.x; sc < ns; sc += blockDim.x) b.scenes[sc].g.ctl->epoch = s_epoch[sc];
-    // P2G + grid update over every scene's active grid blocks
+    // P2G: tiles of every scene's listed particle blocks, then overflow particles
     block_offsets(ns, off, [&](int sc) {
-        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_g);
+        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_p);
     });
     {
-        const int grp = threadIdx.x / kOwnerThreads, gt = threadIdx.x % kOwnerThreads;
+        const int grp = threadIdx.x / TT, gt = threadIdx.x % TT;
         const int nblk = off[ns];
-        for (int q = grp * gridDim.x + blockIdx.x; q < nblk; q += kOwners * gridDim.x) {
+        for (int q = grp * gridDim.x + blockIdx.x; q < nblk; q += kGroups * gridDim.x) {
             const int sidx = find_scene(off, ns, q);
             const BatchSceneDev &sc = b.scenes[sidx];
             const StepCtl &st = sc.g.ctl->st[s_epoch[sidx] & 1];
             const FixScales fs = fix_scales(sc.mass, __ldcg(&st.bound));
-            const double t = b.t0 + (double)b.step * (double)sc.dt;
-            const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
-            owner_block(sc.g, sc.gp, sc.mass, sc.dt, blade_z, fs, __ldcg(&st.n_over),
-                        __ldcg(&sc.g.glist[q - off[sidx]]), sm[grp], gt, 1 + grp, nullptr,
-                        nullptr);
+            tile_block<TT>(sc.g, sc.gp, sc.mass, fs, __ldcg(&sc.g.plist[q - off[sidx]]),
+                           s_epoch[sidx], sm.tile[grp], gt, 1 + grp, status);
+        }
+    }
+    block_offsets(ns, off, [&](int sc) {
+        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_over);
+    });
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < off[ns]; q += stride) {
+        const int sidx = find_scene(off, ns, q);
+        const BatchSceneDev &sc = b.scenes[sidx];
+        const FixScales fs = fix_scales(sc.mass, __ldcg(&sc.g.ctl->st[s_epoch[sidx] & 1].bound));
+        grid_add_particle(sc.g, sc.gp, sc.mass, fs, __ldcg(&sc.g.over[q - off[sidx]]));
+    }
+    if (!grid_barrier(b.bar, status)) return;
+    // grid update
+    block_offsets(ns, off, [&](int sc) {
+        return __ldcg(&b.scenes[sc].g.ctl->st[s_epoch[sc] & 1].n_g);
+    });
+    {
+        const int per = blockDim.x >> 6;
+        const int sub = threadIdx.x >> 6, l = threadIdx.x & 63;
+        const int nblk = off[ns], gstride = gridDim.x * per;
+        for (int u0 = sub * gridDim.x + blockIdx.x; u0 < nblk; u0 += kGridUnroll * gstride) {
+            int sidx[kGridUnroll], gb[kGridUnroll];
+            float4 a[kGridUnroll];
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k) {
+                const int u = u0 + k * gstride;
+                sidx[k] = -1;
+                if (u < nblk) {
+                    sidx[k] = find_scene(off, ns, u);
+                    gb[k] = __ldcg(&b.scenes[sidx[k]].g.glist[u - off[sidx[k]]]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k)
+                if (sidx[k] >= 0) {
+                    const BatchSceneDev &sc = b.scenes[sidx[k]];
+                    const FixScales fs =
+                        fix_scales(sc.mass, __ldcg(&sc.g.ctl->st[s_epoch[sidx[k]] & 1].bound));
+                    a[k] = take_node_sums(sc.g, fs, gb[k], l);
+                }
+#pragma unroll
+            for (int k = 0; k < kGridUnroll; ++k) {
+                if (sidx[k] < 0) continue;
+                const BatchSceneDev &sc = b.scenes[sidx[k]];
+                const double t = b.t0 + (double)b.step * (double)sc.dt;
+                const double blade_z = (double)sc.gp.blade_z0 + (double)sc.gp.blade_vz * t;
+                grid_node_update(sc.g, sc.gp, sc.dt, blade_z, gb[k], l, a[k], nullptr, nullptr);
+            }
         }
     }
     if (!grid_barrier(b.bar, status)) return;
@@ -791,7 +970,6 @@ k_mpm_batch(MpmBatchArgs b, int *status) {
         g.bcount[__ldcg(&g.plist[q - off[sidx]])] = 0;
     }
 }
-
 
 // CTAs per SM of the latent MPM launch: its phases are separated by grid
 // barriers over a few thousand particles, and one CTA per SM made the stage

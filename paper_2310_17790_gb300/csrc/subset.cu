@@ -30,12 +30,14 @@ __device__ __forceinline__ bool position(const SubsetArgs &a, int p, float x[3])
     return finite3(x[0], x[1], x[2]);
 }
 
-// Stencil base of x, false if the stencil leaves the grid.
+// Stencil base of x (the base node of the MPM kernels' bspline_axis, with
+// x / dx and the shift by 0.5 each rounded to float32), false if the stencil
+// leaves the grid.
 __device__ __forceinline__ bool stencil_base(const SubsetArgs &a, const float x[3], int b[3]) {
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        b[d] = __float2int_rd(x[d] * a.inv_dx - 0.5f);
+        b[d] = bspline_axis(x[d], a.inv_dx).base;
         ok &= b[d] >= 0 && b[d] + 2 <= a.dims[d] - 1;
     }
     return ok;
