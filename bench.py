@@ -633,6 +633,10 @@ def run_part(args):
                               peaks, peak_src)
     if args.only == "training":
         return run_training(args, nsf, dev, peaks, peak_src)
+    if args.only == "full":
+        from scenes.synthetic import full_config2
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        return run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     return run_batched(args, nsf, dev, flush, peaks, peak_src)
 
@@ -686,8 +690,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--only", default="all",
-                    choices=["all", "latent", "batched", "mlp", "training"],
-                    help="batched / mlp: run that part alone (profiling runs) and print its JSON")
+                    choices=["all", "latent", "batched", "mlp", "training", "full"],
+                    help="latent / batched / mlp / training / full: run that part alone "
+                         "(profiling runs) and print its JSON")
     ap.add_argument("--batch-scenes", type=int, default=256)
     args = ap.parse_args()
     rank, world, local = dist_env()

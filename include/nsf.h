@@ -222,8 +222,9 @@ nsf_status nsf_latent_workspace_size(const nsf_fields *fields,
  *     tau^n = h(X, z_n), C^n = l(X, z_n) on all integration particles;
  *  2. one MLS-MPM step (§3.3, §5.2) on N: particles binned by 4^3 grid block,
  *     P2G of mass, APIC momentum and the stress force of the node force balance
- *     (Eq. 5, MLS gradient w_ip (4/dx^2)(x_i - x_p)), grid update with gravity
- *     and boundary conditions, G2P of x^{n+1} = x^n + dt sum_i w_ip v_i on S;
+ *     (Eq. 5, MLS gradient w_ip (4/dx^2)(x_i - x_p)) summed per block in shared
+ *     memory, grid update with gravity and boundary conditions, G2P of
+ *     x^{n+1} = x^n + dt sum_i w_ip v_i on S;
  *  3. network inversion (§5.3, Eq. 9): opts->iters Gauss-Newton iterations from
  *     z_n on the sample particles.
  * In/out: d_z holds z_n on entry and z_{n+nsteps} on return; d_z_prev holds
@@ -234,6 +235,11 @@ nsf_status nsf_latent_workspace_size(const nsf_fields *fields,
  * returned z_prev in the workspace for a following NSF_LATENT_REUSE_PREV call.
  * t0 is the time at the start of the first step (moves the blade).
  * taps may be NULL.
+ * Reproducible: the P2G node sums are exact sums of contributions rounded
+ * once to fixed point (2^-40 of the step's largest contribution bound), and
+ * the BF16 path combines its Gauss-Newton sums in a fixed order, so the same
+ * inputs give the same z bit for bit (the FP32 path adds float64 partials
+ * with atomics, whose order may vary).
  */
 nsf_status nsf_latent_step(const nsf_fields *fields,
                            const nsf_latent_scene *scene, double dt, double t0,
@@ -273,9 +279,12 @@ nsf_status nsf_project(const nsf_fields *fields, const float *d_X_S,
  * call allocates nothing: it clears the part of the array it uses on the
  * caller's stream and then runs nsf_project there.  Its first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one array, so calls that can overlap on the GPU (unordered streams) race
- * with each other: order them.
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call it after cudaDeviceReset (or
+ * anything else that destroys and recreates the device's primary context):
+ * the kept address would then be stale.  All calls share the one array, so
+ * calls that can overlap on the GPU (unordered streams) race with each other:
+ * order them.
  */
 #define NSF_PROJECT_STATIC_MAX_S 2048
 #define NSF_PROJECT_STATIC_BYTES (1 << 20)
@@ -459,9 +468,11 @@ nsf_status nsf_full_workspace_size(const nsf_grid_desc *grid, int n,
 
 /*
  * nsteps full-order explicit MLS-MPM steps (paper §3.3): stress tau(F_p), P2G
- * (mass, APIC momentum, MLS stress force), grid update, G2P of v, x,
- * C = (4/dx^2) sum_i w_ip v_i (x_i - x_p)^T, F <- (I + dt C) F, then the
- * material's return map.  Updates particles in place.  taps may be NULL.
+ * (mass, APIC momentum, MLS stress force; particles binned by 4^3 block and
+ * summed per block in shared memory, exact fixed-point sums as in
+ * nsf_latent_step), grid update, G2P of v, x, C = (4/dx^2) sum_i w_ip v_i
+ * (x_i - x_p)^T, F <- (I + dt C) F, then the material's return map.  Updates
+ * particles in place.  taps may be NULL.
  */
 nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
                          const nsf_particles *particles, double dt, double t0,

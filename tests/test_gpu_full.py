@@ -109,6 +109,33 @@ def test_full_step_end_to_end_matches_oracle_full_step(nsf):
     assert rel(out["F"], ref["F"].reshape(-1, 9)) < TOL
 
 
+def test_full_step_dense_block_overflows_its_bucket(nsf):
+    # 3,000 particles whose stencil bases all lie in one 4^3-cell block, more
+    # than the 1,024 its bucket holds: the particles past the bucket add their
+    # contributions to the grid directly, and the grid must still be the
+    # oracle's P2G of all of them (and the step reproducible bit for bit)
+    from scenes.synthetic import FullScene
+    rng = np.random.Generator(np.random.PCG64(78))
+    n, dx = 3000, 1.0 / 32
+    # x / dx in [16.5, 20.5): stencil bases 16 .. 19, the block starting at cell 16
+    x = ((16.5 + rng.uniform(0.01, 3.99, size=(n, 3))) * dx).astype(np.float32)
+    vol0 = (4 * dx) ** 3 / n
+    sc = FullScene(x=x, v=np.zeros((n, 3), np.float32), C=np.zeros((n, 9), np.float32),
+                   F=np.tile(np.eye(3, dtype=np.float32).ravel(), (n, 1)), mass=1000.0 * vol0,
+                   vol0=vol0, grid=GridSpec(n=(32, 32, 32), dx=dx, gravity=(0.0, 0.0, -9.8),
+                                            wall_cells=0),
+                   dt=1e-5, material=dict(model="neo_hookean", E=1e4, nu=0.3,
+                                          yield_stress=0.0, friction_deg=30.0))
+    sc = _perturb(sc, 78, v=0.05, c=1.0, f=0.01)
+    base = np.floor(sc.x.astype(np.float64) / dx - 0.5)
+    assert base.min() >= 16 and base.max() <= 19
+    out = _run(nsf, sc)
+    _check(sc, out)
+    again = _run(nsf, sc)
+    for k in ("x", "v", "C", "F", "grid_mp", "grid_v"):
+        np.testing.assert_array_equal(out[k], again[k])
+
+
 def test_full_step_200k_slab(nsf):
     # the 200,000-particle slab on the 128^3 grid (one step, teacher-forced)
     sc = _perturb(full_scene(72), 72)
