@@ -10,6 +10,10 @@ write) between timed steps and the flush is outside the timed events.
 
 The full-order MLS-MPM step on the same 200,000-particle slab (neo-Hookean,
 sticky blade) is timed the same way and reported as "full_order".
+"matched_error" fits the fields to a full-order run of that slab with the
+library's training path and compares the latent step's speed and sample
+particle error (dx units) with the full-order step's, for 1, 2, 3 and 5
+Gauss-Newton iterations.  "config1" is the 1,024-particle FP32 latent scene.
 
 --impl reference times the FP64 CPU oracle instead (the reference arm of this
 benchmark): the same workload and metric on the host cores.
@@ -285,6 +289,8 @@ def run_gpu(args, rank, world, local):
     full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
     full_plastic = run_full(args, nsf, full_config2(model="von_mises", steps=args.steps), dev,
                             flush)
+    matched = run_matched(args, nsf, dev, flush, full["steps_per_s"]) if args.precision == "bf16" else None
+    config1 = run_config1(args, nsf, dev, flush)
 
     # kernels per step: fields 1, MPM 1 (binning, P2G, grid update and G2P in
     # one cooperative launch), Gauss-Newton 1 (all iterations in one
@@ -308,6 +314,8 @@ def run_gpu(args, rank, world, local):
         "training": training,
         "full_order": full,
         "full_order_plastic": full_plastic,
+        "matched_error": matched,
+        "config1": config1,
         "gpu_launches": launches_per_step * K,
         "status": status,
     }
@@ -420,6 +428,48 @@ def run_e2e(args, nsf, sc, F, gd, dev):
     return {"value": Kh / dt, "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(out.numel() * 8), "steps": Kh,
             "note": "eager API call per step (no graph), host wall clock"}
+
+
+def run_config1(args, nsf, dev, flush):
+    """The 1,024-particle latent scene with FP32 fields (4 x 64 on the CUDA
+    cores, r = 6, 32^3 grid, 5 Gauss-Newton iterations), one graph replay per
+    step, L2 flushed between steps.  Latency-bound (~1 GFLOP and ~0.1 MB per
+    step): reported as steps/s, not against a roofline."""
+    import torch
+    from scenes.synthetic import latent_config1
+    sc = latent_config1(steps=args.steps)
+    F = nsf.Fields.from_spec(sc.fields)
+    X = torch.from_numpy(np.ascontiguousarray(sc.X.T)).to(dev)
+    gd = nsf.grid_desc(sc.grid.n, sc.grid.dx, sc.grid.gravity, sc.grid.wall_cells)
+    stp = nsf.LatentStepper(F, X, sc.n_S, sc.mass, sc.vol0, gd)
+    z = torch.tensor(sc.z0, dtype=torch.float64, device=dev)
+    zp = z.clone()
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        stp.step(z, zp, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping, stream=stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        stp.step(z, zp, sc.dt, nsteps=1, iters=sc.gn_iters, damping=sc.damping, stream=stream,
+                 reuse_prev=True)
+    for _ in range(max(3, args.warmup)):
+        graph.replay()
+    torch.cuda.synchronize()
+    K = min(args.steps, 200)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / K
+    return {"workload": sc.name, "steps_per_s": 1e3 / ms, "ms_per_step": ms, "steps": K,
+            "status": stp.read_status(), "dtype": "fp32",
+            "launches_per_step": 2 + sc.gn_iters,
+            "note": "FP32 fields on CUDA cores; Gauss-Newton one launch per iteration"}
 
 
 def run_full(args, nsf, fc, dev, flush):
@@ -620,6 +670,151 @@ def run_training(args, nsf, dev, peaks, peak_src):
                     "weight re-pack"}
 
 
+def run_matched(args, nsf, dev, flush, full_steps_per_s, steps=400, every=10,
+                train_steps=4000, lr=1e-3, iters_list=(1, 2, 3, 5)):
+    """The latent step against the full-order step on the same scene at
+    matched particle-position error (§6; App. D training).
+
+    1. Full-order run of the 200,000-particle slab (neo-Hookean, sticky blade),
+       `steps` steps, a snapshot of x, C and tau(F) every `every` steps.
+    2. Fields g, h, l (5 x 128, BF16, r = 6) fitted to the snapshots with the
+       library's training path (Adam, hand-written backward): outputs
+       normalised by the snapshots' per-component mean and std (App. D), one
+       latent code per snapshot learned with g, h and l fitted on those codes.
+    3. Latent runs from snapshot 0's code (zero initial velocity) on a seeded
+       5 % integration set (10,000 particles) with 700 sample particles, for
+       each Gauss-Newton iteration count (1 = the first-order Taylor
+       projection of §5.3), and one graph-replayed step of each timed with L2
+       flushed between steps.
+    4. Error of the sample particles' fitted positions g(X_S, z_n) against the
+       full-order positions, in dx units (max and rms over S), at the end and
+       over the run; delta of Eq. 10 over S and all snapshots."""
+    import torch
+    from scenes.synthetic import full_config2, make_fields
+    fc = full_config2(steps=1)
+    soa = lambda a: torch.from_numpy(np.ascontiguousarray(a.T)).to(dev)
+    x, v, Cm, Fm = soa(fc.x), soa(fc.v), soa(fc.C), soa(fc.F)
+    X_ref = x.clone()
+    gd = nsf.grid_desc(fc.grid.n, fc.grid.dx, fc.grid.gravity, fc.grid.wall_cells, fc.grid.blade)
+    mat = nsf.material(**fc.material)
+    st = nsf.FullStepper(gd, mat, x, v, Cm, Fm, fc.mass, fc.vol0)
+    n = x.shape[1]
+    snaps = {"g": [], "h": [], "l": []}
+
+    def record():
+        tau = torch.empty(6, n, device=dev)
+        nsf.nsf_material_stress(mat, Fm, tau)
+        snaps["g"].append(x.clone())
+        snaps["h"].append(tau)
+        snaps["l"].append(Cm.clone())
+    record()
+    for k in range(steps // every):
+        st.step(fc.dt, t0=k * every * fc.dt, nsteps=every)
+        record()
+    torch.cuda.synchronize()
+    assert st.read_status() == 0, nsf.status_string(st.read_status())
+    S = {k: torch.stack(a) for k, a in snaps.items()}             # [T, comps, n]
+    T = S["g"].shape[0]
+    rng = np.random.Generator(np.random.PCG64(2318))
+    spec = make_fields(rng, 6, 128, 5, "bf16", {"g": 1.0, "h": 1.0, "l": 1.0})
+    for k in "ghl":
+        A = S[k] - X_ref[None] if k == "g" else S[k]               # g is residual: x = X + y
+        flat = A.permute(1, 0, 2).reshape(A.shape[1], -1)
+        spec.out_shift[k] = flat.mean(1).cpu().numpy().astype(np.float32)
+        spec.out_scale[k] = flat.std(1).clamp_min(1e-12).cpu().numpy().astype(np.float32)
+    F = nsf.Fields.from_spec(spec)
+    B = 65536
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2318)
+
+    def batch(target):
+        p = torch.randint(0, n, (B,), device=dev, generator=gen)
+        t = torch.randint(0, T, (B,), device=dev, generator=gen)
+        return X_ref[:, p].contiguous(), t.to(torch.int32).contiguous(), target[t, :, p].T.contiguous()
+    codes0 = torch.from_numpy(rng.normal(0, 0.1, size=(T, 6)).astype(np.float32)).to(dev)
+    trainers, losses = {}, {}
+    t_train = time.perf_counter()
+    for k in "ghl":
+        w0 = torch.from_numpy(np.asarray(spec.weights[k], np.float32)).to(dev)
+        tr = nsf.FieldTrainer(F, k, w0, codes0 if k == "g" else trainers["g"].z, B, lr=lr,
+                              train_codes=(k == "g"))
+        for it in range(train_steps):
+            tr.lr = lr * (1.0 if it < train_steps // 2 else 0.3 if it < 3 * train_steps // 4 else 0.1)
+            tr.step(*batch(S[k]))
+        torch.cuda.synchronize()
+        trainers[k], losses[k] = tr, float(tr.loss.item())
+    t_train = time.perf_counter() - t_train
+    codes = trainers["g"].z.double()
+    r2 = np.random.Generator(np.random.PCG64(2319))
+    sub = r2.choice(n, size=10000, replace=False)
+    sub = torch.from_numpy(sub[r2.permutation(sub.size)]).to(dev)
+    nS, dx = 700, fc.grid.dx
+    X_N = X_ref[:, sub].contiguous()
+    XS = X_N[:, :nS].contiguous()
+    ref = S["g"][:, :, sub[:nS]]                                     # [T, 3, nS]
+
+    def fitted(zz):
+        out = torch.empty(3, nS, device=dev)
+        nsf.nsf_eval_fields(F, XS, zz.contiguous(), x=out)
+        return out
+    fit_max = max(float((fitted(codes[t]) - ref[t]).abs().max()) / dx for t in range(T))
+    disp_max = float((ref[-1] - XS).abs().max()) / dx
+    runs = []
+    for iters in iters_list:
+        lat = nsf.LatentStepper(F, X_N, nS, fc.mass, fc.vol0, gd)
+        z, zp = codes[0].clone().contiguous(), codes[0].clone().contiguous()
+        err_max, err_rms, num, den = [], [], 0.0, 0.0
+        for t in range(T):
+            if t > 0:
+                lat.step(z, zp, fc.dt, t0=(t - 1) * every * fc.dt, nsteps=every, iters=iters,
+                         damping=1e-6)
+            d = fitted(z) - ref[t]
+            err_max.append(float(d.abs().max()) / dx)
+            err_rms.append(float(d.pow(2).sum(0).mean().sqrt()) / dx)
+            num += float(d.pow(2).sum())
+            den += float(ref[t].pow(2).sum())
+        torch.cuda.synchronize()
+        status = lat.read_status()
+        stream = torch.cuda.Stream(device=dev)
+        zt, zpt = z.clone(), zp.clone()
+        with torch.cuda.stream(stream):
+            lat.step(zt, zpt, fc.dt, nsteps=1, iters=iters, damping=1e-6, stream=stream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            lat.step(zt, zpt, fc.dt, nsteps=1, iters=iters, damping=1e-6, stream=stream,
+                     reuse_prev=True)
+        for _ in range(5):
+            graph.replay()
+        torch.cuda.synchronize()
+        K = 100
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                graph.replay()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        runs.append({"gn_iters": iters, "latent_steps_per_s": 1e3 / ms, "status": status,
+                     "final_max_dx": err_max[-1], "final_rms_dx": err_rms[-1],
+                     "run_max_dx": max(err_max), "delta_eq10": (num / den) ** 0.5})
+    ok = [r for r in runs if r["status"] == 0]
+    best = max(ok, key=lambda r: r["latent_steps_per_s"]) if ok else None
+    return {"workload": f"full-order slab 200k neo-Hookean + blade, {steps} steps, snapshots every "
+                        f"{every}; latent 10,000 N / 700 S, r = 6, fields 5 x 128 BF16 fitted to "
+                        f"the snapshots ({train_steps} Adam steps per field, batch {B})",
+            "full_order_steps_per_s": full_steps_per_s, "runs": runs,
+            "fastest_latent": best,
+            "speedup_fastest_vs_full": (best["latent_steps_per_s"] / full_steps_per_s) if best else None,
+            "fit_max_dx": fit_max, "sample_displacement_max_dx": disp_max,
+            "training_s": t_train, "final_losses": losses,
+            "note": "errors of the sample particles' positions g(X_S, z_n) against the full-order "
+                    "run, dx units; gn_iters 1 is the first-order Taylor projection (§5.3)"}
+
+
 def run_part(args):
     """One part of the benchmark alone (for profiling captures)."""
     import torch
@@ -633,6 +828,11 @@ def run_part(args):
                               peaks, peak_src)
     if args.only == "training":
         return run_training(args, nsf, dev, peaks, peak_src)
+    if args.only == "matched":
+        from scenes.synthetic import full_config2
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        full = run_full(args, nsf, full_config2(steps=args.steps), dev, flush)
+        return run_matched(args, nsf, dev, flush, full["steps_per_s"])
     if args.only == "full":
         from scenes.synthetic import full_config2
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -690,9 +890,9 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--only", default="all",
-                    choices=["all", "latent", "batched", "mlp", "training", "full"],
-                    help="latent / batched / mlp / training / full: run that part alone "
-                         "(profiling runs) and print its JSON")
+                    choices=["all", "latent", "batched", "mlp", "training", "full", "matched"],
+                    help="latent / batched / mlp / training / full / matched: run that part "
+                         "alone (profiling runs) and print its JSON")
     ap.add_argument("--batch-scenes", type=int, default=256)
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -480,6 +480,18 @@ nsf_status nsf_full_step(const nsf_grid_desc *grid, const nsf_material *mat,
                          int *d_status, const nsf_full_taps *taps,
                          void *stream);
 
+/*
+ * Kirchhoff stress tau(F) of material `mat` at n deformation gradients (App. F
+ * for the SVD-based models, the textbook neo-Hookean form for NSF_NEO_HOOKEAN),
+ * with no return map: the stress the full-order step applies to a particle
+ * whose (elastic) deformation gradient is F.  d_F [9][n] row-major per
+ * particle, d_tau6 [6][n] in the Voigt order of this header.  The stress
+ * field h is fitted to these values of full-order snapshots (App. D).
+ * neo-Hookean in FP32, the SVD-based models in float64 (as the full step).
+ */
+nsf_status nsf_material_stress(const nsf_material *mat, const float *d_F, int n, float *d_tau6,
+                               void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *nsf_status_string(int status);
 /* Library ABI version (major * 10000 + minor * 100 + patch). */

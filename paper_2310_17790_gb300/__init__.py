@@ -261,10 +261,12 @@ class FieldTrainer:
     """Adam on one field's FP32 master weights and a table of per-snapshot
     latent codes, every step in the library: loss and gradients
     (nsf_field_loss_grad), Adam (nsf_adam_step), re-pack of the new weights
-    into the fields object (nsf_fields_set_weights)."""
+    into the fields object (nsf_fields_set_weights).  train_codes=False keeps
+    the codes fixed (a field fitted on the codes another field learned)."""
 
-    def __init__(self, fields, field, weights, z_table, batch, lr=1e-4):
+    def __init__(self, fields, field, weights, z_table, batch, lr=1e-4, train_codes=True):
         torch = _torch()
+        self.train_codes = train_codes
         self.fields, self.field = fields, FIELD_INDEX.get(field, field)
         self.w = weights.detach().clone().float().contiguous()
         self.z = z_table.detach().clone().float().contiguous()
@@ -281,9 +283,10 @@ class FieldTrainer:
     def step(self, X, code, target, stream=None):
         self.t += 1
         nsf_field_loss_grad(self.fields, self.field, X, code, target, self.z, self.loss, self.gw,
-                            self.gz, self.ws, self.status, stream)
+                            self.gz if self.train_codes else None, self.ws, self.status, stream)
         nsf_adam_step(self.w, self.gw, self.mw, self.vw, self.t, self.lr, stream=stream)
-        nsf_adam_step(self.z, self.gz, self.mz, self.vz, self.t, self.lr, stream=stream)
+        if self.train_codes:
+            nsf_adam_step(self.z, self.gz, self.mz, self.vz, self.t, self.lr, stream=stream)
         nsf_fields_set_weights(self.fields, self.field, self.w, stream)
         return self.loss
 
@@ -377,6 +380,12 @@ def particles(x, v, Cm, F, mass, vol0):
     p.d_x, p.d_v, p.d_C, p.d_F = _ptr(x), _ptr(v), _ptr(Cm), _ptr(F)
     p.mass, p.vol0 = float(mass), float(vol0)
     return p
+
+
+def nsf_material_stress(mat, F, tau6, stream=None):
+    """Kirchhoff stress tau(F) of material `mat` (F [9, n], tau6 [6, n])."""
+    check(N.lib.nsf_material_stress(C.byref(mat), _ptr(F), int(F.shape[1]), _ptr(tau6),
+                                    _stream(stream)), "nsf_material_stress")
 
 
 def nsf_full_step(grid, mat, parts, dt, t0, nsteps, workspace, status, taps=None,

@@ -124,6 +124,7 @@ SIGNATURES = [
     ("nsf_full_step", _ST, [C.POINTER(nsf_grid_desc), C.POINTER(nsf_material),
                             C.POINTER(nsf_particles), _D, _D, _I, _P, _S, _P,
                             C.POINTER(nsf_full_taps), _P]),
+    ("nsf_material_stress", _ST, [C.POINTER(nsf_material), _P, _I, _P, _P]),
     ("nsf_status_string", C.c_char_p, [_I]),
     ("nsf_version", _I, []),
 ]

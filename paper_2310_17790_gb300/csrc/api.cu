@@ -713,6 +713,18 @@ nsf_status nsf_integration_set(const nsf_fields *f, const nsf_grid_desc *grid, c
     return NSF_OK;
 }
 
+nsf_status nsf_material_stress(const nsf_material *mat, const float *d_F, int n, float *d_tau6,
+                               void *stream) {
+    if (!mat || n < 0 || (n > 0 && (!d_F || !d_tau6)) || !(mat->E > 0.f) || !(mat->nu > -1.f) ||
+        !(mat->nu < 0.5f) || mat->model < NSF_NEO_HOOKEAN || mat->model > NSF_DRUCKER_PRAGER)
+        return NSF_ERR_INVALID_ARG;
+    const float mu = mat->E / (2.f * (1.f + mat->nu));
+    const float lam = mat->E * mat->nu / ((1.f + mat->nu) * (1.f - 2.f * mat->nu));
+    NSF_CUDA_TRY(launch_stress(d_F, d_tau6, n, mat->model, mu, lam,
+                               static_cast<cudaStream_t>(stream)));
+    return NSF_OK;
+}
+
 nsf_status nsf_full_workspace_size(const nsf_grid_desc *g, int n, size_t *bytes) {
     if (!valid_grid(g) || n < 1 || !bytes) return NSF_ERR_INVALID_ARG;
     *bytes = full_layout(g, n).total;

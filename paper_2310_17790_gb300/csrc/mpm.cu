@@ -1004,10 +1004,28 @@ cudaError_t launch_coop(K kernel, int grid, cudaStream_t s, A... args) {
 
 }  // namespace
 
+// Kirchhoff stress of F for the neo-Hookean model, FP32 (as P2G computes it).
+__global__ void __launch_bounds__(256)
+k_stress_neo_hookean(const float *__restrict__ F, float *tau6, int n, float mu, float lam) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float Fp[9], T[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Fp[c] = F[(size_t)c * n + p];
+    neo_hookean_tau(Fp, mu, lam, T);
+    const float t6[6] = {T[0], T[4], T[8], T[5], T[2], T[1]};   // xx yy zz yz xz xy
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tau6[(size_t)c * n + p] = t6[c];
+}
+
 // ------------------------------------------------------------ launchers ---
 cudaError_t launch_stress(const float *F, float *tau6, int n, int model, float mu, float lam,
                           cudaStream_t s) {
-    k_stress<<<(n + 255) / 256, 256, 0, s>>>(F, tau6, n, model, mu, lam);
+    if (n <= 0) return cudaSuccess;
+    if (model == NSF_NEO_HOOKEAN)
+        k_stress_neo_hookean<<<(n + 255) / 256, 256, 0, s>>>(F, tau6, n, mu, lam);
+    else
+        k_stress<<<(n + 255) / 256, 256, 0, s>>>(F, tau6, n, model, mu, lam);
     return cudaGetLastError();
 }
 

@@ -185,3 +185,21 @@ def test_full_step_plastic_slab_multi_step(nsf):
     out = _run(nsf, sc, nsteps=10)
     assert out["status"] == 0
     assert np.isfinite(out["x"]).all() and np.isfinite(out["F"]).all()
+
+
+@pytest.mark.parametrize("model", ["neo_hookean", "fixed_corotated", "von_mises", "drucker_prager"])
+def test_material_stress_matches_oracle(nsf, model):
+    # tau(F) of every model (App. F; textbook neo-Hookean) against the oracle
+    import torch
+    rng = np.random.Generator(np.random.PCG64(79))
+    n = 5000
+    F = (np.eye(3) + 0.05 * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    mat = ocm.Material(model, 2e5, 0.3, 1e4, 30.0)
+    ref = mat.stress(F.astype(np.float64))
+    Fd = soa(F.reshape(n, 9))
+    tau = torch.zeros(6, n, device="cuda")
+    nsf.nsf_material_stress(nsf.material(model, 2e5, 0.3, 1e4, 30.0), Fd, tau)
+    torch.cuda.synchronize()
+    from oracle import fields as ofields
+    got = ofields.voigt_to_sym(tau.cpu().numpy().T.astype(np.float64))
+    assert rel(got, ref) < (1e-5 if model == "neo_hookean" else 1e-6)
