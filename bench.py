@@ -610,8 +610,8 @@ def run_training(args, nsf, dev, peaks, peak_src):
     """One training step of the deformation field on full-order snapshots
     (App. D): 64 snapshots of the 200,000-particle slab from the library's
     full-order step (5 steps apart), minibatches of 65,536 (particle,
-    snapshot) pairs, field g of 5 hidden layers x 256 (BF16 forward, TF32
-    backward products, FP32 master weights), per-snapshot latent codes r = 6 learned
+    snapshot) pairs, field g of 5 hidden layers x 256 (BF16 forward, backward
+    products with the cotangent split into bf16 hi + lo, FP32 master weights), per-snapshot latent codes r = 6 learned
     jointly, Adam lr 1e-4.  A step = loss and gradients + Adam on weights and
     codes + re-pack of the weights, all through the C ABI."""
     import torch
@@ -661,13 +661,13 @@ def run_training(args, nsf, dev, peaks, peak_src):
     last = float(tr.loss.item())
     mac = mlp_macs(6, 256, 5, 3)
     flops = 6.0 * B * mac        # forward 2 n MAC, backward 4 n MAC
-    return {"workload": "train-g-w256d5-r6-bf16fwd-tf32bwd-batch65536-64snapshots-200k",
+    return {"workload": "train-g-w256d5-r6-bf16fwd-splitbf16bwd-batch65536-64snapshots-200k",
             "ms_per_step": ms, "steps": K, "points_per_s": B / (ms / 1e3),
             "tflops": flops / (ms / 1e3) / 1e12, "flops_per_step": flops,
             "loss_first": first, "loss_last": last,
-            "note": "loss and gradients (forward BF16 GEMMs, backward TF32 GEMMs via cuBLAS "
-                    "with FP32 accumulation, chain-rule kernels), Adam on weights and codes, "
-                    "weight re-pack"}
+            "note": "loss and gradients (the library's tcgen05 GEMMs: BF16 forward, backward "
+                    "with hi/lo-split bf16 cotangents, FP32 accumulation; fused bias/ELU/ELU' "
+                    "epilogues), Adam on weights and codes, weight re-pack"}
 
 
 def run_matched(args, nsf, dev, flush, full_steps_per_s, steps=400, every=10,

@@ -311,9 +311,11 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
  * forward pass runs in the fields' precision (BF16: every product with bf16
  * operands and FP32 accumulation on the tensor cores, the input layer in
  * FP32); the backward pass is FP32 on the forward's activations, which the
- * workspace keeps (nsf_train_workspace_size bytes), with its products in TF32
- * (FP32 accumulation) for BF16 fields.  Dense products go to
- * cuBLAS; the first training call on a device creates its cuBLAS handle.
+ * workspace keeps (nsf_train_workspace_size bytes).  For BF16 fields the
+ * backward products of the hidden layers multiply the bf16 weights and
+ * activations by the cotangent split into two bf16 parts (hi + lo, ~16
+ * significant bits) on the tensor cores, FP32 accumulation.  Every product is
+ * one of the library's own kernels (no BLAS library).
  * A negative code[p] sets NSF_ERR_INVALID_ARG in *d_status.
  *
  * nsf_adam_step: one Adam step (Kingma and Ba 2014; App. D) on count float32

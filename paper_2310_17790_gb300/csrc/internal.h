@@ -180,11 +180,58 @@ struct SubsetArgs {
 cudaError_t launch_subset(const SubsetArgs &a, int *count_out, float *X_out, int ld_out,
                           int *status, cudaStream_t s);
 
+// ------------------------------------------------------------------ GEMM ---
+// Dense products of training (gemm.cu): D(m, n) = sum_k A(m, k) B(n, k) for
+// m < M, n < N, k < K, the operands read through strided views.
+struct MatView {
+    const void *ptr;       // element (row, k) at ptr[row * s_row + k * s_k]
+    long long s_row, s_k;
+    int bf16;              // element type: 1 bf16, 0 float
+    const void *lo;        // bf16 views of a split operand: the lo parts (same strides)
+};
+enum { kEpiStore = 0, kEpiBiasElu = 1, kEpiEluGrad = 2, kEpiSlab = 3 };
+struct GemmEpilogue {
+    int mode;
+    float *out;            // Store, EluGrad: out[n * ld + m]; Slab: out[z M N + m N + n]
+    long long ld;
+    const float *bias;     // BiasElu: pre = D + bias[m] -> pre[n ld + m]
+    float *pre;
+    float *h32;            // BiasElu: ELU(pre) (rounded to bf16 when round_bf16)
+    __nv_bfloat16 *h16;    // BiasElu: its bf16 copy (may be null)
+    int round_bf16;
+    const float *apre;     // EluGrad: out = D * ELU'(apre[n ld + m])
+    float *colsum;         // EluGrad on the tensor cores (may be null): per-CTA sums of out
+                           // over its columns, colsum[(blockIdx.x * 2 + half) * M + m]
+    __nv_bfloat16 *dhi, *dlo;   // EluGrad (may be null): out as hi = bf16(v), lo = bf16(v - hi)
+};
+// FP32 product on the CUDA cores; K split over `kslices` slices (only with
+// the Slab epilogue, which writes one M x N slab per slice).
+cudaError_t gemm_simt(int M, int N, int K, const MatView &A, const MatView &B,
+                      const GemmEpilogue &e, int kslices, cudaStream_t s);
+// BF16 product on the tcgen05 tensor cores with FP32 accumulation in tensor
+// memory.  Both operands bf16, each either with contiguous k (s_k = 1) or
+// with contiguous rows (s_row = 1), strides multiples of 8 elements; split =
+// 1 (2) adds the product of operand A's (B's) lo parts (view.lo), so that an
+// operand kept as hi + lo pairs counts with ~16 significant bits.
+cudaError_t gemm_tc(int M, int N, int K, const MatView &A, const MatView &B, int split,
+                    const GemmEpilogue &e, int kslices, int *status, cudaStream_t s);
+// Thin shapes.  thin_outer: out(a, c) = sum_k U(a, k) V(c, k) for A <= 32,
+// k split into `slices` slabs summed in a fixed order, out row-major [A][C]
+// (or [C][A] when transposed).  thin_m: D(m, n) = sum_k A(m, k) B(n, k) for
+// M <= 32, K <= 256, out[n * ld + m].
+cudaError_t thin_outer(int A, int C, int K, const MatView &U, const MatView &V, float *slab,
+                       int slices, float *out, bool transposed, cudaStream_t s);
+cudaError_t thin_m(int M, int N, int K, const MatView &A, const MatView &B, float *out,
+                   long long ld, cudaStream_t s);
+// out[i] = sum over z < slices of slab[z * count + i] (fixed order).
+cudaError_t reduce_slabs(const float *slab, int slices, long long count, float *out,
+                         cudaStream_t s);
+
 // --------------------------------------------------------------- training ---
 // Workspace of one loss/gradient evaluation (train.cu).
 struct TrainLayout {
-    size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, w16, ones,
-        total;
+    size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, ones, slab,
+        dh[2], dl[2], Wb[kMaxDepth], WTb[kMaxDepth], total;
 };
 TrainLayout train_layout(int r, int W, int D, int od, int n);
 cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const int *code,

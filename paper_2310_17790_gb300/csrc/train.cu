@@ -4,22 +4,23 @@
 //
 // Activations are column-major per point (column p = point p).  Forward, per
 // linear layer l:  A_l = W_l H_{l-1} + b_l,  H_l = ELU(A_l), with H_{-1} =
-// [X; z] and the input layer in FP32; the other products in the fields'
-// precision (BF16 fields: bf16 operands, FP32 accumulation on the tensor
-// cores; the activations entering a product are rounded to bf16).  Loss: the
-// mean squared normalised error L = sum ((y - y*) / scale)^2 / (n out_dim).
-// Backward in FP32 (TF32 products for BF16 fields) on the forward's
+// [X; z].  Loss: the mean squared normalised error
+// L = sum ((y - y*) / scale)^2 / (n out_dim).  Backward on the forward's
 // activations:
 //   delta_out = dL/draw = 2 (y - y*) / (scale n out_dim)
 //   dW_l = delta_l H_{l-1}^T,  db_l = delta_l x ones (row sums),
 //   delta_{l-1} = (W_l^T delta_l) * ELU'(A_{l-1}),
 //   dz_t += (W_0^T delta_0)[3:, p] over the points p of snapshot t.
-// The dense products go to cuBLAS (plain GEMMs); the chain rule around them
-// runs in the kernels below.
-#include <mutex>
+// Every product is the library's own (gemm.cu), its elementwise step fused
+// into the product's epilogue (bias + ELU, or * ELU').  BF16 fields: the
+// width x width products on the tcgen05 tensor cores -- forward with bf16
+// operands (the activations entering a product rounded to bf16), backward
+// with the FP32 cotangent split into two bf16 parts against the exact bf16
+// weights or activations (~16 significant bits) -- and the thin input and
+// output layers in FP32 on the CUDA cores; FP32 fields: every product in FP32
+// on the CUDA cores.  Weight gradients split the sum over points into K
+// slices (one slab each), summed in a fixed order.
 #include <vector>
-
-#include <cublas_v2.h>
 
 #include "tc_common.cuh"
 
@@ -52,57 +53,52 @@ __global__ void k_inputs(const float *__restrict__ X, const int *__restrict__ co
     for (int k = 0; k < r; ++k) col[3 + k] = z_table[(size_t)c * r + k];
 }
 
-// H = ELU(A + b) over a rows x n block (CTA y = a group of points, thread x a
-// row); H32 gets the value entering the next product (bf16-rounded when
-// round_bf16), H16 (optional) its bf16 copy.
-__global__ void k_bias_elu(float *A, const float *__restrict__ b, int rows, int n, float *H32,
-                           __nv_bfloat16 *H16, int round_bf16) {
-    const int o = threadIdx.x;
-    if (o >= rows) return;
-    const float bo = b[o];
-    for (int p = blockIdx.x; p < n; p += gridDim.x) {
-    const size_t i = (size_t)p * rows + o;
-    const float a = A[i] + bo;
-    A[i] = a;
-    float h = a > 0.f ? a : expm1f(a);
-    const __nv_bfloat16 hb = __float2bfloat16_rn(h);
-    if (round_bf16) h = __bfloat162float(hb);
-    H32[i] = h;
-    if (H16) H16[i] = hb;
-    }
-}
-
 // Outputs, loss and dL/draw.  raw: od x n (column-major), target [od][n].
+// Also this CTA's sums of dL/draw over its points (the output bias gradient's
+// partials) into dbias_part[blockIdx.x][od].
 __global__ void k_loss(const float *__restrict__ raw, const float *__restrict__ bout,
                        const float *__restrict__ X, const float *__restrict__ target, int n,
-                       int od, FieldDev F, int residual, float *delta, float *loss) {
+                       int od, FieldDev F, int residual, float *delta, float *loss,
+                       float *dbias_part) {
     __shared__ float part[kT];
+    __shared__ float dsum[kT / 32][9];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float acc = 0.f;
+    float d[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) d[a] = 0.f;
     if (p < n) {
-        for (int a = 0; a < od; ++a) {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            if (a >= od) break;
             float y = fmaf(F.scale[a], raw[(size_t)p * od + a] + bout[a], F.shift[a]);
             if (residual) y += X[(size_t)a * n + p];
             const float e = (y - target[(size_t)a * n + p]) / F.scale[a];
             acc = fmaf(e, e, acc);
-            delta[(size_t)p * od + a] = 2.f * e / ((float)n * (float)od);
+            d[a] = 2.f * e / ((float)n * (float)od);
+            delta[(size_t)p * od + a] = d[a];
         }
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        float v = d[a];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) dsum[warp][a] = v;
     }
     part[threadIdx.x] = acc;
     __syncthreads();
+    if (threadIdx.x < od) {
+        float v = 0.f;
+        for (int w = 0; w < kT / 32; ++w) v += dsum[w][threadIdx.x];
+        dbias_part[(size_t)blockIdx.x * od + threadIdx.x] = v;
+    }
     for (int s = kT / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
         __syncthreads();
     }
     if (threadIdx.x == 0) atomicAdd(loss, part[0] / ((float)n * (float)od));
-}
-
-// delta *= ELU'(A)
-__global__ void k_elu_grad(float *delta, const float *__restrict__ A, long long count) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const float a = A[i];
-    delta[i] *= a > 0.f ? 1.f : expf(a);
 }
 
 __global__ void k_fill(float *a, float v, int count) {
@@ -135,9 +131,17 @@ __global__ void k_scatter_dz(const float *__restrict__ dinp, const int *__restri
         if (tab[i] != 0.f) atomicAdd(&gz[i], tab[i]);
 }
 
-__global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *b, long long count) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) b[i] = __float2bfloat16_rn(a[i]);
+// bf16 copies of a hidden layer's weights from its transposed FP32 copy
+// Wt [in][out]: Wb [out][in] and WTb [in][out] (the values are bf16 already
+// for a BF16 field).
+__global__ void k_weights_bf16(const float *__restrict__ Wt, int W, __nv_bfloat16 *Wb,
+                               __nv_bfloat16 *WTb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * W) return;
+    const int c = i / W, o = i % W;
+    const __nv_bfloat16 v = __float2bfloat16_rn(Wt[i]);
+    WTb[i] = v;
+    Wb[(size_t)o * W + c] = v;
 }
 
 // Adam (Kingma and Ba 2014), bias-corrected, in place.
@@ -200,39 +204,39 @@ __global__ void k_repack(const float *__restrict__ flat, long long total, int r,
     }
 }
 
-std::mutex g_mu;
-cublasHandle_t g_handle[64] = {};
-
-cublasHandle_t handle_for_current_device() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_handle[dev]) {
-        cublasHandle_t h;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-        cublasSetPointerMode(h, CUBLAS_POINTER_MODE_HOST);
-        cublasSetMathMode(h, CUBLAS_DEFAULT_MATH);
-        g_handle[dev] = h;
-    }
-    return g_handle[dev];
+// K slices of a weight-gradient product over n points whose output has
+// `tiles` tiles: enough CTAs to cover the SMs, at least 256 points a slice.
+constexpr int kMaxSlices = 48;
+// K slices of a thin product (one 256-thread CTA per slice): 256 points a
+// slice, at most kMaxThinSlices.
+constexpr int kMaxThinSlices = 256;
+int thin_slices(int n) {
+    const int k = n / 256;
+    return k < 1 ? 1 : (k > kMaxThinSlices ? kMaxThinSlices : k);
+}
+int weight_slices(int n, int tiles) {
+    int k = (2 * tc::sm_count() + tiles - 1) / tiles;
+    k = k > kMaxSlices ? kMaxSlices : k;
+    const int by_n = (n + 255) / 256;
+    k = k > by_n ? by_n : k;
+    return k < 1 ? 1 : k;
 }
 
-// C (m x n, ld ldc) = op(A) op(B), all column-major FP32.
-cublasStatus_t sgemm(cublasHandle_t h, bool ta, bool tb, int m, int n, int k, const float *A,
-                     int lda, const float *B, int ldb, float *C, int ldc) {
-    const float one = 1.f, zero = 0.f;
-    return cublasSgemm(h, ta ? CUBLAS_OP_T : CUBLAS_OP_N, tb ? CUBLAS_OP_T : CUBLAS_OP_N, m, n, k,
-                       &one, A, lda, B, ldb, &zero, C, ldc);
+MatView view(const void *p, long long s_row, long long s_k, int bf16) {
+    MatView v;
+    v.ptr = p;
+    v.s_row = s_row;
+    v.s_k = s_k;
+    v.bf16 = bf16;
+    return v;
 }
 
-// The same with bf16 operands and FP32 accumulation and result.
-cublasStatus_t gemm_bf16(cublasHandle_t h, bool ta, bool tb, int m, int n, int k,
-                         const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb,
-                         float *C, int ldc) {
-    const float one = 1.f, zero = 0.f;
-    return cublasGemmEx(h, ta ? CUBLAS_OP_T : CUBLAS_OP_N, tb ? CUBLAS_OP_T : CUBLAS_OP_N, m, n,
-                        k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &zero, C, CUDA_R_32F,
-                        ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+GemmEpilogue epi(int mode, float *out = nullptr, long long ld = 0) {
+    GemmEpilogue e{};
+    e.mode = mode;
+    e.out = out;
+    e.ld = ld;
+    return e;
 }
 
 }  // namespace
@@ -258,8 +262,26 @@ TrainLayout train_layout(int r, int W, int D, int od, int n) {
     L.dout = take((size_t)od * nn * 4);
     L.d1 = take((size_t)W * nn * 4);
     L.d2 = take((size_t)W * nn * 4);
-    L.w16 = take((size_t)W * W * 2);
-    L.ones = take(nn * 4);
+    for (int i = 0; i < 2; ++i) {       // the cotangents as bf16 hi / lo pairs
+        L.dh[i] = take((size_t)W * nn * 2);
+        L.dl[i] = take((size_t)W * nn * 2);
+    }
+    for (int l = 1; l < D; ++l) {       // bf16 W_l [out][in] and W_l^T [in][out]
+        L.Wb[l] = take((size_t)W * W * 2);
+        L.WTb[l] = take((size_t)W * W * 2);
+    }
+    L.ones = take(16);
+    // slabs of the split sums: tensor-core weight gradients (W x W per
+    // slice), thin products (at most max(3 + r, od) x W per slice), the loss
+    // kernel's per-CTA output-bias sums
+    const size_t thin_a = (size_t)(3 + r > od ? 3 + r : od);
+    size_t slab = (size_t)kMaxSlices * W * W;
+    slab = slab > (size_t)kMaxThinSlices * thin_a * W ? slab : (size_t)kMaxThinSlices * thin_a * W;
+    const size_t loss_parts = (nn + kT - 1) / kT * (size_t)od;
+    const size_t col_parts = 2 * ((nn + 127) / 128) * (size_t)W;    // bias column sums
+    slab = slab > loss_parts ? slab : loss_parts;
+    slab = slab > col_parts ? slab : col_parts;
+    L.slab = take(slab * 4);
     L.total = o;
     return L;
 }
@@ -270,54 +292,79 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
                           cudaStream_t s) {
     const FieldDev &F = fd.f[field];
     const int r = fd.r, W = F.width, D = F.depth, od = F.out_dim, K0 = 3 + r;
-    const bool bf16 = fd.precision == NSF_PREC_BF16;
+    const int b16 = fd.precision == NSF_PREC_BF16 ? 1 : 0;
     const bool residual = field == NSF_FIELD_G && fd.residual_g;
     const TrainLayout L = train_layout(r, W, D, od, n);
-    cublasHandle_t h = handle_for_current_device();
-    if (!h) return cudaErrorNotReady;
-    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorNotReady;
     auto P = [&](size_t off) { return reinterpret_cast<float *>(ws + off); };
     auto P16 = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
-    const long long nW = (long long)W * n;
-#define NSF_CB(x) do { if ((x) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown; } while (0)
+    float *slab = P(L.slab);
+    const MatView ones = view(P(L.ones), 0, 0, 0);
+    const int ks_thin = thin_slices(n);
+#define NSF_GT(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return e_; } while (0)
+    // a hidden W x W product: tensor cores for BF16 fields, CUDA cores for FP32
+    auto hidden = [&](int M, int N, int K, const MatView &A, const MatView &B, int split,
+                      const GemmEpilogue &e, int slices) {
+        return b16 ? gemm_tc(M, N, K, A, B, split, e, slices, status, s)
+                   : gemm_simt(M, N, K, A, B, e, slices, s);
+    };
+    // sum over all n points (K) of an M x N product into dst, by K slices
+    auto summed = [&](int M, int N, const MatView &A, const MatView &B, bool tc, int split,
+                      float *dst) -> cudaError_t {
+        const int tiles = tc ? ((M + 127) / 128) * ((N + 127) / 128)
+                             : ((M + 63) / 64) * ((N + 63) / 64);
+        const int k = weight_slices(n, tiles);
+        const GemmEpilogue e = epi(kEpiSlab, slab);
+        cudaError_t err = tc ? gemm_tc(M, N, n, A, B, split, e, k, status, s)
+                             : gemm_simt(M, N, n, A, B, e, k, s);
+        if (err != cudaSuccess) return err;
+        return reduce_slabs(slab, k, (long long)M * N, dst, s);
+    };
+    auto bias_elu = [&](int l) {
+        GemmEpilogue e = epi(kEpiBiasElu);
+        e.ld = W;
+        e.bias = F.b[l];
+        e.pre = P(L.A[l]);
+        e.h32 = b16 ? nullptr : P(L.H[l]);         // BF16 fields read the bf16 copy
+        e.h16 = b16 ? P16(L.H16[l]) : nullptr;
+        e.round_bf16 = b16;
+        return e;
+    };
+    auto elu_grad = [&](float *out, int l, int pair, float *colsum = nullptr) {
+        GemmEpilogue e = epi(kEpiEluGrad, out, W);
+        e.apre = P(L.A[l]);
+        e.colsum = colsum;
+        if (b16) {
+            e.dhi = P16(L.dh[pair]);
+            e.dlo = P16(L.dl[pair]);
+        }
+        return e;
+    };
+    // the last hidden activation as the thin products read it
+    const MatView Hlast_rows = b16 ? view(P16(L.H16[D - 1]), W, 1, 1) : view(P(L.H[D - 1]), W, 1, 0);
+    const MatView Hlast_cols = b16 ? view(P16(L.H16[D - 1]), 1, W, 1) : view(P(L.H[D - 1]), 1, W, 0);
     // ---- forward
     k_inputs<<<blocks(n), kT, 0, s>>>(X, code, z_table, n, r, P(L.inp), status);
-    NSF_CB(sgemm(h, true, false, W, n, K0, F.W0, K0, P(L.inp), K0, P(L.A[0]), W));
-    const int ecta = n < 4 * 152 * 8 ? n : 4 * 152 * 8;      // CTAs of the row-wise kernels
-    k_bias_elu<<<ecta, W, 0, s>>>(P(L.A[0]), F.b[0], W, n, P(L.H[0]),
-                                  bf16 ? P16(L.H16[0]) : nullptr, bf16 ? 1 : 0);
+    NSF_GT(gemm_simt(W, n, K0, view(F.W0, K0, 1, 0), view(P(L.inp), K0, 1, 0), bias_elu(0), 1, s));
+    if (b16)
+        for (int l = 1; l < D; ++l)
+            k_weights_bf16<<<blocks((long long)W * W), kT, 0, s>>>(F.Wt[l], W, P16(L.Wb[l]),
+                                                                  P16(L.WTb[l]));
     for (int l = 1; l < D; ++l) {
-        if (bf16) {
-            k_to_bf16<<<blocks((long long)W * W), kT, 0, s>>>(F.Wt[l], P16(L.w16), (long long)W * W);
-            NSF_CB(gemm_bf16(h, false, false, W, n, W, P16(L.w16), W, P16(L.H16[l - 1]), W,
-                             P(L.A[l]), W));
-        } else {
-            NSF_CB(sgemm(h, false, false, W, n, W, F.Wt[l], W, P(L.H[l - 1]), W, P(L.A[l]), W));
-        }
-        k_bias_elu<<<ecta, W, 0, s>>>(P(L.A[l]), F.b[l], W, n, P(L.H[l]),
-                                      bf16 ? P16(L.H16[l]) : nullptr, bf16 ? 1 : 0);
+        // A_l(o, p) = sum_c W_l[o][c] H_{l-1}(c, p), W_l[o][c] = Wt[l][c W + o]
+        if (b16)
+            NSF_GT(gemm_tc(W, n, W, view(P16(L.Wb[l]), W, 1, 1), view(P16(L.H16[l - 1]), W, 1, 1),
+                           0, bias_elu(l), 1, status, s));
+        else
+            NSF_GT(gemm_simt(W, n, W, view(F.Wt[l], 1, W, 0), view(P(L.H[l - 1]), W, 1, 0),
+                             bias_elu(l), 1, s));
     }
-    if (bf16) {
-        k_to_bf16<<<blocks((long long)od * W), kT, 0, s>>>(F.Wout, P16(L.w16), (long long)od * W);
-        NSF_CB(gemm_bf16(h, true, false, od, n, W, P16(L.w16), W, P16(L.H16[D - 1]), W, P(L.raw),
-                         od));
-    } else {
-        NSF_CB(sgemm(h, true, false, od, n, W, F.Wout, W, P(L.H[D - 1]), W, P(L.raw), od));
-    }
-    // ---- loss and dL/draw
-    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
-    if (e != cudaSuccess) return e;
+    NSF_GT(thin_m(od, n, W, view(F.Wout, W, 1, 0), Hlast_rows, P(L.raw), od, s));
+    // ---- loss, dL/draw and the output bias gradient
+    NSF_GT(cudaMemsetAsync(loss, 0, sizeof(float), s));
     k_loss<<<blocks(n), kT, 0, s>>>(P(L.raw), F.b[D], X, target, n, od, F, residual ? 1 : 0,
-                                    P(L.dout), loss);
-    // ---- backward; gradient offsets in the flat layout.  BF16 fields take
-    // their backward products in TF32 on the tensor cores (10-bit mantissa
-    // operands, FP32 accumulation: well inside the bf16 forward's rounding);
-    // FP32 fields keep FP32 products.
-    if (bf16) NSF_CB(cublasSetMathMode(h, CUBLAS_TF32_TENSOR_OP_MATH));
-    struct MathReset {
-        cublasHandle_t h;
-        ~MathReset() { cublasSetMathMode(h, CUBLAS_DEFAULT_MATH); }
-    } reset{h};
+                                    P(L.dout), loss, slab);
+    k_fill<<<1, 32, 0, s>>>(P(L.ones), 1.f, 4);
+    // ---- backward; gradient offsets in the flat layout
     std::vector<size_t> goff(D + 1);
     {
         size_t o = 0;
@@ -327,37 +374,67 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
             o += (size_t)in * out + out;
         }
     }
-    // output layer: dWout (row-major od x W) = H_{D-1} dout^T as a W x od column-major
-    NSF_CB(sgemm(h, false, true, W, od, n, P(L.H[D - 1]), W, P(L.dout), od, grad_w + goff[D], W));
-    // bias gradients: row sums of delta = delta x ones
-    k_fill<<<blocks(n), kT, 0, s>>>(P(L.ones), 1.f, n);
-    const float one = 1.f, zero = 0.f;
-    NSF_CB(cublasSgemv(h, CUBLAS_OP_N, od, n, &one, P(L.dout), od, P(L.ones), 1, &zero,
-                       grad_w + goff[D] + (size_t)od * W, 1));
+    // output layer: dbout[a] = sum_p dout(a, p) from k_loss's per-CTA sums,
+    // dWout[a][c] = sum_p dout(a, p) H_{D-1}(c, p)
+    NSF_GT(reduce_slabs(slab, blocks(n), od, grad_w + goff[D] + (size_t)od * W, s));
+    NSF_GT(thin_outer(od, W, n, view(P(L.dout), 1, od, 0), Hlast_cols, slab, ks_thin,
+                      grad_w + goff[D], false, s));
     float *dcur = P(L.d1), *dnext = P(L.d2);
-    NSF_CB(sgemm(h, false, false, W, n, od, F.Wout, W, P(L.dout), od, dcur, W));
+    // flat offset of layer l's bias gradient
+    auto boff = [&](int l) { return goff[l] + (size_t)(l == 0 ? K0 : W) * W; };
+    // delta_{D-1}(c, p) = sum_a Wout[a][c] dout(a, p) * ELU'(A_{D-1}(c, p)), db_{D-1}
+    int pair = 0;                       // the hi / lo buffers of dcur
+    NSF_GT(gemm_simt(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
+                     elu_grad(dcur, D - 1, pair), 1, s));
+    NSF_GT(thin_outer(1, W, n, ones, view(dcur, 1, W, 0), slab, ks_thin, grad_w + boff(D - 1),
+                      false, s));
     for (int l = D - 1; l >= 1; --l) {
-        k_elu_grad<<<blocks(nW), kT, 0, s>>>(dcur, P(L.A[l]), nW);
-        NSF_CB(sgemm(h, false, true, W, W, n, P(L.H[l - 1]), W, dcur, W, grad_w + goff[l], W));
-        NSF_CB(cublasSgemv(h, CUBLAS_OP_N, W, n, &one, dcur, W, P(L.ones), 1, &zero,
-                           grad_w + goff[l] + (size_t)W * W, 1));
-        NSF_CB(sgemm(h, true, false, W, n, W, F.Wt[l], W, dcur, W, dnext, W));
+        // dW_l[o][c] = sum_p delta_l(o, p) H_{l-1}(c, p); BF16 fields: the cotangent
+        // as its hi / lo pairs, both operands with contiguous rows
+        if (b16) {
+            MatView dpair = view(P16(L.dh[pair]), 1, W, 1);
+            dpair.lo = P16(L.dl[pair]);
+            NSF_GT(summed(W, W, dpair, view(P16(L.H16[l - 1]), 1, W, 1), true, 1,
+                          grad_w + goff[l]));
+        } else {
+            NSF_GT(summed(W, W, view(dcur, 1, W, 0), view(P(L.H[l - 1]), 1, W, 0), false, 0,
+                          grad_w + goff[l]));
+        }
+        // delta_{l-1}(c, p) = sum_o W_l[o][c] delta_l(o, p) * ELU'(A_{l-1}(c, p)) and
+        // db_{l-1}[c] = sum_p delta_{l-1}(c, p): on the tensor cores the product's
+        // epilogue sums its columns, otherwise a thin reduction
+        if (b16) {
+            MatView dpair = view(P16(L.dh[pair]), W, 1, 1);
+            dpair.lo = P16(L.dl[pair]);
+            // the FP32 cotangent is read only at the input layer (l - 1 = 0)
+            NSF_GT(gemm_tc(W, n, W, view(P16(L.WTb[l]), W, 1, 1), dpair, 2,
+                           elu_grad(l - 1 == 0 ? dnext : nullptr, l - 1, pair ^ 1, slab), 1,
+                           status, s));
+            NSF_GT(reduce_slabs(slab, 2 * ((n + 127) / 128), W, grad_w + boff(l - 1), s));
+        } else {
+            NSF_GT(gemm_simt(W, n, W, view(F.Wt[l], W, 1, 0), view(dcur, W, 1, 0),
+                             elu_grad(dnext, l - 1, pair ^ 1), 1, s));
+            NSF_GT(thin_outer(1, W, n, ones, view(dnext, 1, W, 0), slab, ks_thin,
+                              grad_w + boff(l - 1), false, s));
+        }
         float *t = dcur;
         dcur = dnext;
         dnext = t;
+        pair ^= 1;
     }
-    k_elu_grad<<<blocks(nW), kT, 0, s>>>(dcur, P(L.A[0]), nW);
-    NSF_CB(sgemm(h, false, true, K0, W, n, P(L.inp), K0, dcur, W, grad_w + goff[0], K0));
-    NSF_CB(cublasSgemv(h, CUBLAS_OP_N, W, n, &one, dcur, W, P(L.ones), 1, &zero,
-                       grad_w + goff[0] + (size_t)K0 * W, 1));
+    // input layer: dW_0[o][j] = sum_p delta_0(o, p) inp(j, p) (computed as [j][o],
+    // stored transposed)
+    const MatView d0 = view(dcur, 1, W, 0);
+    NSF_GT(thin_outer(K0, W, n, view(P(L.inp), 1, K0, 0), d0, slab, ks_thin, grad_w + goff[0],
+                      true, s));
     if (grad_z) {
-        e = cudaMemsetAsync(grad_z, 0, (size_t)n_codes * r * sizeof(float), s);
-        if (e != cudaSuccess) return e;
-        NSF_CB(sgemm(h, false, false, K0, n, W, F.W0, K0, dcur, W, P(L.dinp), K0));
+        NSF_GT(cudaMemsetAsync(grad_z, 0, (size_t)n_codes * r * sizeof(float), s));
+        // dinp(j, p) = sum_o W0[o][j] delta_0(o, p)
+        NSF_GT(thin_m(K0, n, W, view(F.W0, 1, K0, 0), view(dcur, W, 1, 0), P(L.dinp), K0, s));
         k_scatter_dz<<<blocks(n) < 304 ? blocks(n) : 304, kT, 0, s>>>(P(L.dinp), code, n, r,
                                                                    n_codes, grad_z);
     }
-#undef NSF_CB
+#undef NSF_GT
     return cudaGetLastError();
 }
 
