@@ -26,6 +26,9 @@
 //
 // k_gemm_simt (FP32 fields, and the thin input and output layers of every
 // field): 64 x 64 tiles, 4 x 4 outputs per thread, FP32 FMA.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "tc_common.cuh"
 
 namespace nsf {
@@ -45,6 +48,37 @@ __device__ __forceinline__ float view_at(const MatView &v, long long row, long l
 __device__ __forceinline__ float elu_f(float a) { return a > 0.f ? a : expm1f(a); }
 __device__ __forceinline__ float elu_grad_f(float a) { return a > 0.f ? 1.f : expf(a); }
 
+// ELU and ELU' on the BF16 path, where the activation is rounded to bf16 right
+// after: e = 2^(a log2 e) on the special-function unit, ELU = e - 1, except
+// for -1/32 < a <= 0, where the series a (1 + a/2 (1 + a/3)) (relative error
+// < 1.3e-6) keeps small activations accurate.  Both stay far inside half a
+// bf16 ulp of the exact value.  Large a gives e = inf, unused.
+__device__ __forceinline__ float elu_bf16_path(float a, float &grad) {
+    const float e = ex2_approx(a * 1.4426950408889634f);
+    grad = a > 0.f ? 1.f : e;
+    const float series = a * fmaf(a, fmaf(a, 0.16666667f, 0.5f), 1.f);
+    return a > 0.f ? a : (a > -0.03125f ? series : e - 1.f);
+}
+
+// ELU' on the BF16 path is kept as a 16-bit fixed-point code q = rint(ELU'
+// 2^15) (ELU' lies in (0, 1], and 1 codes as 32768 exactly; absolute error
+// <= 2^-16), two bytes a value instead of the four of the pre-activation.
+// Encoding: the low 16 bits of the float ELU' 2^15 + 2^23 (the addition
+// rounds to the nearest integer); decoding: 0x4B000000 | q read as a float is
+// 2^23 + q.
+__device__ __forceinline__ unsigned short dact_code(float g) {
+    return (unsigned short)(__float_as_uint(fmaf(g, 32768.f, 8388608.f)) & 0xFFFFu);
+}
+__device__ __forceinline__ float dact_value(unsigned q) {
+    return (__uint_as_float(0x4B000000u | q) - 8388608.f) * 3.0517578125e-05f;
+}
+
+// The split of a cotangent value into bf16 hi + lo.
+__device__ __forceinline__ void split_bf16(float o, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(o);
+    lo = __float2bfloat16_rn(o - __bfloat162float(hi));
+}
+
 // The epilogue of output (m, n) of K-slice z with accumulated value d.
 __device__ __forceinline__ void epilogue(const GemmEpilogue &e, int M, int N, int z, int m, int n,
                                          float d) {
@@ -53,25 +87,26 @@ __device__ __forceinline__ void epilogue(const GemmEpilogue &e, int M, int N, in
         case kEpiStore: e.out[i] = d; break;
         case kEpiBiasElu: {
             const float a = d + e.bias[m];
+            if (e.dact) {                      // BF16 path
+                float g;
+                const float h = elu_bf16_path(a, g);
+                e.dact[i] = dact_code(g);
+                e.h16[i] = __float2bfloat16_rn(h);
+                break;
+            }
             e.pre[i] = a;
-            float h = elu_f(a);
-            const __nv_bfloat16 hb = __float2bfloat16_rn(h);
-            if (e.round_bf16) h = __bfloat162float(hb);
+            const float h = elu_f(a);
             if (e.h32) e.h32[i] = h;
-            if (e.h16) e.h16[i] = hb;
+            if (e.h16) e.h16[i] = __float2bfloat16_rn(h);
             break;
         }
         case kEpiEluGrad: {
-            const float o = d * elu_grad_f(e.apre[i]);
-            e.out[i] = o;
-            if (e.dhi) {
-                const __nv_bfloat16 hb = __float2bfloat16_rn(o);
-                e.dhi[i] = hb;
-                e.dlo[i] = __float2bfloat16_rn(o - __bfloat162float(hb));
-            }
+            const float o = d * (e.dact ? dact_value(e.dact[i]) : elu_grad_f(e.apre[i]));
+            if (e.out) e.out[i] = o;
+            if (e.dhi) split_bf16(o, e.dhi[i], e.dlo[i]);
             break;
         }
-        default: e.out[(size_t)z * M * N + (size_t)m * N + n] = d; break;
+        default: e.out[(size_t)z * M * N + (size_t)n * M + m] = d; break;
     }
 }
 
@@ -122,84 +157,50 @@ k_gemm_simt(int M, int N, int K, int kper, const MatView A, const MatView B,
 }
 
 // ------------------------------------------------------------ tcgen05 ----
-constexpr int kTM = 128, kTN = 128, kTK = 64, kTThreads = 256, kMaxStages = 3;
-// Copy stages: three without a split operand (96 KB of tiles), two with one
-// (also 96 KB): two CTAs share an SM either way.
-__host__ __device__ constexpr int tc_stages(bool split) { return split ? 2 : 3; }
+// Persistent, warp-specialised: one CTA per SM walks the work units (a
+// 128 x 128 output tile and a K-slice) u = blockIdx.x, + gridDim.x, ...;
+// units with the same output columns and K-slice are adjacent, so the CTAs
+// that share an operand tile fetch it at about the same time (one HBM read,
+// the rest from L2).
+//   warp 0      one thread issues the TMA copies of each K-chunk (64) of
+//               both operands (and the lo parts of a split operand) into a
+//               ring of shared-memory stages, each completing on the stage's
+//               `full` barrier;
+//   warp 1      owns the tensor memory; one thread issues the tcgen05.mma of
+//               each chunk (four M = 128, N = 128, K = 16 products, eight with
+//               a split operand) into one of two FP32 accumulators and commits
+//               them to the stage's `empty` barrier, and after a unit's last
+//               chunk to the accumulator's `tfull` barrier;
+//   warps 2-9   the epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
+//               output rows) and 64 of the 128 columns, hands the accumulator
+//               back (`tempty`), then applies the epilogue and stores.
+// So the copies of the next chunks, the products of the next unit and the
+// epilogue of this one overlap.  Every wait is bounded in time.
+constexpr int kTM = 128, kTN = 128, kTK = 64;
+constexpr int kWsThreads = 320, kWsEpiWarps = 8;
 constexpr int kTileBytes = kTM * kTK * 2;           // one bf16 operand tile: 16 KB
+// Stages of the copy ring: 6 x 32 KB, or 4 x 48 KB with a split operand.
+__host__ __device__ constexpr int ws_stages(bool split) { return split ? 4 : 6; }
+__host__ __device__ constexpr int ws_stage_bytes(bool split) {
+    return (split ? 3 : 2) * kTileBytes;
+}
+// After the stages: the barriers, the TMEM holder, then (1024-aligned) a
+// 16 x 64 tile of bf16 ones, the B operand of the column sums.
+__host__ __device__ constexpr int ws_ones_offset(bool split) {
+    return (ws_stages(split) * ws_stage_bytes(split) + (2 * ws_stages(split) + 5) * 8 + 16 + 1023) /
+           1024 * 1024;
+}
+__host__ __device__ constexpr int ws_smem_bytes(bool split) {
+    return ws_ones_offset(split) + 2048 + 1024;
+}
+// MN-major operand tiles as the TMA writes them: two 64-row blocks (8 KB
+// apart, the leading byte offset), each 64 k-rows of 128 bytes in 8-row
+// atoms 1024 bytes apart (the stride byte offset).
+constexpr uint32_t kMnLbo = 8192, kMnSbo = 1024;
 
-// Shared-memory carve (offsets from a 1024-aligned base): per stage s the A
-// tile, the B tile and, with a split operand, the tile of its lo parts; then
-// the stages' barriers and the tensor-memory address.
-struct TcGemmLayout {
-    int tile[kMaxStages][3];
-    int bars, tmem, total;
+struct WsShape {
+    int M, N, K, kper, tiles_m, tiles_n, units;
 };
-__host__ __device__ inline TcGemmLayout tc_gemm_layout(bool split) {
-    TcGemmLayout L;
-    int o = 0;
-    for (int st = 0; st < kMaxStages; ++st)
-        for (int t = 0; t < 3; ++t) {
-            L.tile[st][t] = o;
-            if (st < tc_stages(split) && (t < 2 || split)) o += kTileBytes;
-        }
-    L.bars = o;
-    o += kMaxStages * 8;
-    L.tmem = align_to(o, 16);
-    o = L.tmem + 16;
-    L.total = o + 1024;
-    return L;
-}
-
-// Byte offset of the 16-byte chunk holding rows r .. r + 7 (r % 8 == 0) at k
-// of an MN-major, 128-byte-swizzled tile of 128 rows: two 64-row atoms 1024
-// bytes apart (leading byte offset), 8-k-row groups 2048 bytes apart (stride
-// byte offset).
-constexpr uint32_t kMnSbo = 2048;
-__device__ __forceinline__ int mn_chunk(int k, int r) {
-    return (k >> 3) * (int)kMnSbo + (r >> 6) * 1024 + (k & 7) * 128 +
-           ((((r >> 3) & 7) ^ (k & 7)) << 4);
-}
-
-// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Issues the copies of rows [r0, r0 + 128) x k-chunk [k0, k0 + 64) of a bf16
-// view into its swizzled tile at `hi` (and the lo parts at `lo`).  A unit is
-// one 16-byte chunk: 8 consecutive k of one row (K-major, MN = false) or 8
-// consecutive rows at one k (MN-major); out-of-range units are zero-filled.
-template <bool MN>
-__device__ __forceinline__ void load_tile(const MatView &V, int rows, int K, int r0, int k0,
-                                          uint32_t hi, uint32_t lo, bool with_lo) {
-    const __nv_bfloat16 *ph = reinterpret_cast<const __nv_bfloat16 *>(V.ptr);
-    const __nv_bfloat16 *pl = reinterpret_cast<const __nv_bfloat16 *>(V.lo);
-#pragma unroll
-    for (int u = 0; u < (kTM * kTK / 8) / kTThreads; ++u) {
-        const int q = threadIdx.x + u * kTThreads;
-        int r, kk;
-        if (MN) { r = 8 * (q % (kTM / 8)); kk = q / (kTM / 8); }
-        else { r = q % kTM; kk = 8 * (q / kTM); }
-        const int row = r0 + r, k = k0 + kk;
-        // the whole chunk is in range or none of it: rows and K are multiples
-        // of 8 where it matters (checked by the launcher)
-        const bool in = MN ? (row < rows && k < K) : (row < rows && k < K);
-        const size_t e0 = in ? (size_t)row * V.s_row + (size_t)k * V.s_k : 0;
-        const uint32_t off = MN ? (uint32_t)mn_chunk(kk, r) : (uint32_t)sw128_kmajor_offset(r, kk, kTM);
-        cp_async16(hi + off, ph + e0, in ? 16 : 0);
-        if (with_lo) cp_async16(lo + off, pl + e0, in ? 16 : 0);
-    }
-}
 
 // Tile products of one K-chunk from the tiles at a_addr and b_addr.
 template <bool AMN, bool BMN>
@@ -207,194 +208,647 @@ __device__ __forceinline__ void chunk_mma(uint32_t tmem, uint32_t a_addr, uint32
                                           uint32_t idesc, bool first) {
 #pragma unroll
     for (int ks = 0; ks < kTK / 16; ++ks) {
-        const uint64_t ad = AMN ? sw128_desc(a_addr + 2u * ks * kMnSbo, 1024u, kMnSbo)
+        const uint64_t ad = AMN ? sw128_desc(a_addr + 2048u * ks, kMnLbo, kMnSbo)
                                 : sw128_desc(a_addr + 32u * ks);
-        const uint64_t bd = BMN ? sw128_desc(b_addr + 2u * ks * kMnSbo, 1024u, kMnSbo)
+        const uint64_t bd = BMN ? sw128_desc(b_addr + 2048u * ks, kMnLbo, kMnSbo)
                                 : sw128_desc(b_addr + 32u * ks);
         mma_bf16(tmem, ad, bd, idesc, (!first || ks > 0) ? 1u : 0u);
     }
 }
 
-// D = A B^T over the CTA's K-slice for a 128 x 128 output tile, then the
-// epilogue EPI.  AMN / BMN: operand with contiguous rows (staged MN-major)
-// instead of contiguous k (K-major); SPLIT: 1 (2) also multiplies A's (B's)
-// lo parts.  kStages stages of copies in flight: the copies of chunk c + 2
-// overlap the products of chunk c.
-template <bool AMN, bool BMN, int SPLIT, int EPI>
-__global__ void __launch_bounds__(kTThreads)
-k_gemm_tc(int M, int N, int K, int kper, const MatView A, const MatView B,
-          const GemmEpilogue e, int *status) {
-    extern __shared__ uint8_t smem_dyn[];
-    uint8_t *base = aligned_smem(smem_dyn);
-    constexpr bool split_a = SPLIT == 1, split_b = SPLIT == 2;
-    const TcGemmLayout L = tc_gemm_layout(SPLIT != 0);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(base + L.bars);
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + L.tmem);
-    __shared__ int s_ok;
-    const int tid = threadIdx.x;
-    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN, z = blockIdx.z;
-    const int k_beg = z * kper, k_end = min(K, k_beg + kper);
-    const int nchunks = k_end > k_beg ? (k_end - k_beg + kTK - 1) / kTK : 0;
-    constexpr int kStages = tc_stages(SPLIT != 0);
-
-    if (tid == 0) {
-        s_ok = 1;
-        for (int st = 0; st < kStages; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (tid < 32) tmem_alloc(tmem_holder, kTN);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_holder;
-    const uint32_t idesc = idesc_bf16(kTM, kTN, BMN) | (AMN ? (1u << 15) : 0u);
-    const uint32_t sb = smem_u32(base);
-    auto issue = [&](int c) {           // the copies of chunk c into stage c % kStages
-        const int st = c % kStages, k0 = k_beg + c * kTK;
-        load_tile<AMN>(A, M, k_end, m0, k0, sb + L.tile[st][0], sb + L.tile[st][2], split_a);
-        load_tile<BMN>(B, N, k_end, n0, k0, sb + L.tile[st][1], sb + L.tile[st][2], split_b);
-    };
-    for (int c = 0; c < kStages - 1; ++c) {
-        if (c < nchunks) issue(c);
-        cp_async_commit();
-    }
-    uint32_t phase_bits = 0u;          // bit st: parity of stage st's next product completion
-    for (int c = 0; c < nchunks; ++c) {
-        // stage (c + kStages - 1) % kStages last held chunk c - 1: its products
-        // must be done before the copies of chunk c + kStages - 1 land there
-        const int cn = c + kStages - 1;
-        if (cn < nchunks) {
-            if (c >= 1) {
-                const int st = (c - 1) % kStages;
-                if (!mbar_wait(&bar[st], (phase_bits >> st) & 1u)) s_ok = 0;
-                phase_bits ^= 1u << st;
-            }
-            issue(cn);
-        }
-        cp_async_commit();
-        cp_async_wait<kStages - 1>();   // this thread's copies of chunk c have landed
-        fence_proxy_async();
-        __syncthreads();                // ... and every thread's
-        if (!s_ok) break;
-        if (tid == 0) {
-            tc_fence_after();
-            const int st = c % kStages;
-            const uint32_t a_hi = sb + L.tile[st][0], b_hi = sb + L.tile[st][1];
-            const uint32_t lo = sb + L.tile[st][2];
-            chunk_mma<AMN, BMN>(tmem, a_hi, b_hi, idesc, c == 0);
-            if (split_a) chunk_mma<AMN, BMN>(tmem, lo, b_hi, idesc, false);
-            if (split_b) chunk_mma<AMN, BMN>(tmem, a_hi, lo, idesc, false);
-            mma_commit(&bar[st]);
-        }
-    }
-    cp_async_wait<0>();
-    // the products of the last chunks (those not yet waited for)
-    for (int c = nchunks - kStages + 1 > 1 ? nchunks - kStages + 1 : 1; c <= nchunks; ++c) {
-        const int st = (c - 1) % kStages;
-        if (c - 1 < 0 || c - 1 >= nchunks) continue;
-        // chunk c - 1 was waited for in-loop only if a later chunk reused its stage
-        if (c - 1 + kStages < nchunks) continue;
-        if (!mbar_wait(&bar[st], (phase_bits >> st) & 1u)) s_ok = 0;
-        phase_bits ^= 1u << st;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const int w = tid >> 5, lane = tid & 31, half = w >> 2;
-    const int m = m0 + (w & 3) * 32 + lane;
-    const uint32_t tq = tmem + ((uint32_t)((w & 3) * 32) << 16);
-    float csum = 0.f;
-    if (!s_ok) {
-        if (tid == 0) set_status(status, NSF_ERR_ITER_CAP);
+// The copies of rows [r0, r0 + 128) x k [k0, k0 + 64) of one operand: one box
+// of 64 k x 128 rows (K-major) or two of 64 rows x 64 k (MN-major).
+template <bool MN>
+__device__ __forceinline__ void load_operand(const CUtensorMap *map, uint32_t dst, int r0, int k0,
+                                             uint64_t *bar) {
+    if (MN) {
+        tma_load_2d(dst, map, r0, k0, bar);
+        tma_load_2d(dst + kMnLbo, map, r0 + 64, k0, bar);
     } else {
-        // warp w reads lanes 32 (w % 4) .. + 31 (rows m) and columns
-        // 64 (w / 4) .. + 63 (n), 16 at a time
-#pragma unroll 1
-        for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 16) {
-            float v[16];
-            tmem_ld16(tq + (uint32_t)c0, v);
-            tmem_wait_ld();
-            if (nchunks == 0)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = 0.f;
-            if (m >= M) continue;
-            const int nb = n0 + c0;
-            if (EPI == kEpiBiasElu) {
-                const float bm = e.bias[m];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (nb + j >= N) break;
-                    const size_t i = (size_t)(nb + j) * e.ld + m;
-                    const float a = v[j] + bm;
-                    e.pre[i] = a;
-                    float h = elu_f(a);
-                    const __nv_bfloat16 hb = __float2bfloat16_rn(h);
-                    if (e.round_bf16) h = __bfloat162float(hb);
-                    if (e.h32) e.h32[i] = h;
-                    if (e.h16) e.h16[i] = hb;
-                }
-            } else if (EPI == kEpiEluGrad) {
-                float ap[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j)       // all the loads first
-                    ap[j] = nb + j < N ? __ldg(e.apre + (size_t)(nb + j) * e.ld + m) : 0.f;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (nb + j >= N) break;
-                    const size_t i = (size_t)(nb + j) * e.ld + m;
-                    const float o = v[j] * elu_grad_f(ap[j]);
-                    if (e.out) e.out[i] = o;
-                    if (e.dhi) {
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(o);
-                        e.dhi[i] = hb;
-                        e.dlo[i] = __float2bfloat16_rn(o - __bfloat162float(hb));
-                    }
-                    csum += o;
-                }
-            } else if (EPI == kEpiSlab) {
-                float *o = e.out + (size_t)z * M * N + (size_t)m * N + nb;
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (nb + j < N) o[j] = v[j];
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (nb + j < N) e.out[(size_t)(nb + j) * e.ld + m] = v[j];
-            }
-        }
-        if (EPI == kEpiEluGrad && e.colsum && m < M)
-            e.colsum[((size_t)blockIdx.x * 2 + half) * M + m] = csum;
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid < 32) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTN);
+        tma_load_2d(dst, map, k0, r0, bar);
     }
 }
 
-__global__ void k_reduce_slabs(const float *__restrict__ slab, int slices, long long count,
-                               float *out) {
-    // 32 outputs a CTA, 8 groups of slices per output, then a shared sum
+__device__ __forceinline__ void unit_coords(const WsShape &g, int u, int &m0, int &n0, int &tn,
+                                            int &z, int &k_beg, int &nch) {
+    const int tm = u % g.tiles_m, r = u / g.tiles_m;
+    tn = r % g.tiles_n;
+    z = r / g.tiles_n;
+    m0 = tm * kTM;
+    n0 = tn * kTN;
+    k_beg = z * g.kper;
+    const int k_end = min(g.K, k_beg + g.kper);
+    nch = k_end > k_beg ? (k_end - k_beg + kTK - 1) / kTK : 0;
+}
+
+// D = A B^T by units, then the epilogue EPI.  AMN / BMN: operand with
+// contiguous rows (MN-major) instead of contiguous k (K-major); SPLIT: 1 (2)
+// also multiplies A's (B's) lo parts, whose tensor map is mLo.  K-slices are
+// whole chunks (kper % 64 == 0): a chunk past K reads the TMA's zero fill.
+template <bool AMN, bool BMN, int SPLIT, int EPI>
+__global__ void __launch_bounds__(kWsThreads, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+          const __grid_constant__ CUtensorMap mLo, const WsShape g, const GemmEpilogue e,
+          int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    uint8_t *base = aligned_smem(smem_dyn);
+    constexpr bool split = SPLIT != 0;
+    constexpr int S = ws_stages(split), SB = ws_stage_bytes(split);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + S * SB);
+    uint64_t *empty = full + S, *tfull = empty + S, *tempty = tfull + 2, *done = tempty + 2;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kWsEpiWarps);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // With colsum: TMEM columns 256 + 16 acc hold the sums of A's rows over the
+    // unit's k (A times a tile of ones), computed by the units of column tile 0.
+    const bool sums = e.colsum != nullptr;
+    const uint32_t tcols = sums ? 4 * kTN : 2 * kTN;
+    if (sums) {
+        uint4 *ones = reinterpret_cast<uint4 *>(base + ws_ones_offset(split));
+        for (int i = threadIdx.x; i < 2048 / 16; i += kWsThreads)
+            ones[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        fence_proxy_async();         // visible to the tensor cores
+    }
+    if (warp == 1) tmem_alloc(holder, tcols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    const uint32_t sb = smem_u32(base);
+    int m0, n0, tn, z, k_beg, nch;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0, filled = 0, last_ph = 0;   // per stage: ever filled, parity
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                unit_coords(g, u, m0, n0, tn, z, k_beg, nch);
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
+                    const uint32_t dst = sb + (uint32_t)(st * SB);
+                    const int k0 = k_beg + c * kTK;
+                    mbar_expect_tx(&full[st], (uint32_t)SB);
+                    load_operand<AMN>(&mA, dst, m0, k0, &full[st]);
+                    load_operand<BMN>(&mB, dst + kTileBytes, n0, k0, &full[st]);
+                    if (SPLIT == 1) load_operand<AMN>(&mLo, dst + 2 * kTileBytes, m0, k0, &full[st]);
+                    if (SPLIT == 2) load_operand<BMN>(&mLo, dst + 2 * kTileBytes, n0, k0, &full[st]);
+                    filled |= 1u << st;
+                    last_ph = (last_ph & ~(1u << st)) | (ph << st);
+                    if (++st == S) { st = 0; ph ^= 1u; }
+                }
+            }
+            if (!ok) {
+                set_status(status, NSF_ERR_ITER_CAP);
+                // the copies already issued land before the CTA ends
+                for (int i = 0; i < S; ++i)
+                    if (filled >> i & 1u) mbar_wait(&full[i], (last_ph >> i) & 1u);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kTM, kTN, BMN) | (AMN ? (1u << 15) : 0u);
+            const uint32_t idesc1 = idesc_bf16(kTM, 16, false) | (AMN ? (1u << 15) : 0u);
+            const uint32_t ones = sb + (uint32_t)ws_ones_offset(split);
+            int st = 0, it = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                unit_coords(g, u, m0, n0, tn, z, k_beg, nch);
+                if (nch == 0) continue;
+                const int acc = it & 1;
+                if (!mbar_wait(&tempty[acc], ((it >> 1) & 1) ^ 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * kTN);
+                for (int c = 0; c < nch; ++c) {
+                    if (!mbar_wait(&full[st], ph)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a_hi = sb + (uint32_t)(st * SB), b_hi = a_hi + kTileBytes;
+                    const uint32_t lo = a_hi + 2 * kTileBytes;
+                    chunk_mma<AMN, BMN>(d, a_hi, b_hi, idesc, c == 0);
+                    if (SPLIT == 1) chunk_mma<AMN, BMN>(d, lo, b_hi, idesc, false);
+                    if (SPLIT == 2) chunk_mma<AMN, BMN>(d, a_hi, lo, idesc, false);
+                    if (sums && tn == 0) {
+                        const uint32_t d1 = tmem + (uint32_t)(2 * kTN + 16 * acc);
+                        chunk_mma<AMN, false>(d1, a_hi, ones, idesc1, c == 0);
+                        if (SPLIT == 1) chunk_mma<AMN, false>(d1, lo, ones, idesc1, false);
+                    }
+                    mma_commit(&empty[st]);
+                    if (++st == S) { st = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+                ++it;
+            }
+            if (!ok) set_status(status, NSF_ERR_ITER_CAP);
+            // every product issued has completed before the tensor memory is freed
+            mma_commit(done);
+            mbar_wait(done, 0);
+        }
+    } else {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        int it = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
+            unit_coords(g, u, m0, n0, tn, z, k_beg, nch);
+            const int m = m0 + q * 32 + lane, nb = n0 + half * 64;
+            const bool row_in = m < g.M;
+            float v[64];
+            if (nch > 0) {
+                const int acc = it & 1;
+                if (!mbar_wait(&tfull[acc], (it >> 1) & 1)) {
+                    set_status(status, NSF_ERR_ITER_CAP);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem + (uint32_t)(acc * kTN + half * 64) + lane_off;
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + 32, v + 32);
+                if (sums && tn == 0 && half == 0) {
+                    float r[8];
+                    tmem_ld8(tmem + (uint32_t)(2 * kTN + 16 * acc) + lane_off, r);
+                    tmem_wait_ld();
+                    if (row_in) e.colsum[(size_t)z * g.M + m] = r[0];
+                }
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+                ++it;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] = 0.f;
+                if (sums && tn == 0 && half == 0 && row_in) e.colsum[(size_t)z * g.M + m] = 0.f;
+            }
+            if (!row_in) continue;
+            if (EPI == kEpiSlab) {
+                float *o = e.out + (size_t)z * g.M * g.N + m;
+#pragma unroll
+                for (int j = 0; j < 64; ++j)
+                    if (nb + j < g.N) o[(size_t)(nb + j) * g.M] = v[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j)
+                    if (nb + j < g.N) e.out[(size_t)(nb + j) * e.ld + m] = v[j];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+}
+
+// ------------------------------------------------ hidden-layer products ----
+// The W x W products of the hidden layers with the points as the M dimension:
+//   Y(p, c) = sum_k X(p, k) Wt(c, k),
+// forward: X = H_{l-1} (bf16 [p][k]), Wt = W_l ([c][k]), epilogue bias + ELU
+// -> ELU' code and bf16 activation; backward: X = delta_l as hi + lo pairs,
+// Wt = W_l^T ([c][o]), epilogue * ELU' -> delta_{l-1} as hi + lo pairs (and
+// FP32 when asked), with the column sums (the bias gradient) when asked.
+// A unit is 128 points x 128 output channels (column tile tn of the
+// ceil(W / 128)).  The grid is a multiple of the column-tile count, so a CTA
+// always has the same tn and keeps those 128 rows of Wt in shared memory for
+// the whole launch (ceil(K / 64) K-atoms of 16 KB); only X streams through
+// the stage ring (the CTAs of one point tile fetch it at the same time: one
+// HBM read).  TMEM: two 128 x 128 FP32 accumulators.  Roles as in k_gemm_tc,
+// with 16 epilogue warps: warp w holds points 32 (w % 4) .. + 31 (TMEM lanes)
+// and channels 32 ((w - 2) / 4) .. + 31 of the unit, one point per lane.
+// Rows of an [p][c] array are 2 W bytes apart, so a lane's own row is a poor
+// access pattern: every global load and store goes through a 32 x 64-byte
+// staging block of the warp (rows 80 bytes apart: no bank conflicts when a
+// lane writes its row), read back and written as 8 rows x 64 bytes per
+// instruction.
+constexpr int kLP = 128, kLN = 128;
+constexpr int kLStagesMax = 8, kLEpiWarps = 16, kLThreads = 32 * (2 + kLEpiWarps);
+constexpr int kLRow = 80, kLStaging = 32 * kLRow;   // staging block of one warp
+struct LayerShape {
+    int n, W, K, tiles_n, units, stages;
+    long long ld;
+};
+__host__ __device__ inline int layer_katoms(int K) { return (K + kTK - 1) / kTK; }
+__host__ __device__ inline int layer_stage_bytes(bool split) { return (split ? 2 : 1) * kTileBytes; }
+// weights, stages, staging blocks, bias (128 floats), barriers, TMEM holder,
+// 1024 alignment slack
+__host__ __device__ inline int layer_smem_bytes(int K, bool split, int stages) {
+    return layer_katoms(K) * kLN * 128 + stages * layer_stage_bytes(split) +
+           kLEpiWarps * kLStaging + kLN * 4 + (2 * kLStagesMax + 6) * 8 + 16 + 1024;
+}
+
+// Sum over the warp's lanes of each of 32 values, lane l ending with the sum
+// of x[l]: five exchange steps, each halving the values a lane keeps (a fixed
+// order, so the result is reproducible).
+__device__ __forceinline__ float lane_column_sum(float (&x)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = upper ? x[i] : x[i + s];
+            const float keep = upper ? x[i + s] : x[i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return x[0];
+}
+
+// Two channels of the forward epilogue with packed f32x2 arithmetic: a = acc
+// + bias, e = 2^(a log2 e) on the special-function unit, ELU = a (a > 0) or
+// e - 1 (absolute error ~1e-7: below half a bf16 ulp of every activation
+// larger than 2^-14 in magnitude, negligible below), ELU' = 1 or e.  Returns
+// the two ELU' codes (low half: the first channel) and the two bf16 values.
+__device__ __forceinline__ void elu2_codes(float2 acc, float2 bias, uint32_t &codes,
+                                           uint32_t &hb) {
+    const float2 a = __fadd2_rn(acc, bias);
+    const float2 t = __fmul2_rn(a, make_float2(1.4426950408889634f, 1.4426950408889634f));
+    const float2 e = make_float2(ex2_approx(t.x), ex2_approx(t.y));
+    const float2 em1 = __fadd2_rn(e, make_float2(-1.f, -1.f));
+    const bool px = a.x > 0.f, py = a.y > 0.f;
+    const float2 g = make_float2(px ? 1.f : e.x, py ? 1.f : e.y);
+    const float2 c = __ffma2_rn(g, make_float2(32768.f, 32768.f), make_float2(8388608.f, 8388608.f));
+    codes = __byte_perm(__float_as_uint(c.x), __float_as_uint(c.y), 0x5410);
+    hb = pack_bf16x2(px ? a.x : em1.x, py ? a.y : em1.y);
+}
+
+// Two channels of the backward epilogue: o = acc * ELU' from the two codes
+// of `codes` (the same decoding as dact_value, packed).
+__device__ __forceinline__ float2 mul_codes2(float2 acc, uint32_t codes) {
+    const float2 q = make_float2(__uint_as_float(__byte_perm(codes, 0x4B000000u, 0x7610)),
+                                 __uint_as_float(__byte_perm(codes, 0x4B000000u, 0x7632)));
+    const float2 d = __fadd2_rn(q, make_float2(-8388608.f, -8388608.f));
+    return __fmul2_rn(__fmul2_rn(acc, d), make_float2(3.0517578125e-05f, 3.0517578125e-05f));
+}
+
+// The staging block: lane l's own row (four 16-byte chunks) and the chunk of
+// instruction i of a coalesced pass (row 8 i + l / 4, chunk l % 4).
+__device__ __forceinline__ void stage_own_row(uint8_t *st, const uint32_t (&w)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4 *>(st + lane * kLRow + 16 * c) =
+            make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+}
+__device__ __forceinline__ uint4 staged_chunk(const uint8_t *st, int i) {
+    const int lane = threadIdx.x & 31;
+    return *reinterpret_cast<const uint4 *>(st + (8 * i + (lane >> 2)) * kLRow + 16 * (lane & 3));
+}
+
+// Writes the warp's 32 rows x 32 16-bit values (lane l: row l in w) to
+// dst[(row0 + r) ld + 8 chunk ...]: through the staging block, 8 rows a store.
+__device__ __forceinline__ void store_rows16(uint8_t *st, const uint32_t (&w)[16], uint16_t *dst,
+                                             long long ld, int row0, int n, int cw) {
+    const int lane = threadIdx.x & 31;
+    stage_own_row(st, w);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 8 * i + (lane >> 2), ck = lane & 3;
+        const uint4 v = staged_chunk(st, i);
+        if (row0 + r < n && 8 * ck < cw)
+            *reinterpret_cast<uint4 *>(dst + (size_t)(row0 + r) * ld + 8 * ck) = v;
+    }
+    __syncwarp();
+}
+
+template <bool SPLIT, int EPI>
+__global__ void __launch_bounds__(kLThreads, 1)
+k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mXlo,
+           const __grid_constant__ CUtensorMap mW, const LayerShape g, const GemmEpilogue e,
+           int *status) {
+    extern __shared__ uint8_t smem_dyn[];
+    uint8_t *base = aligned_smem(smem_dyn);
+    const int katoms = layer_katoms(g.K), S = g.stages, SB = layer_stage_bytes(SPLIT);
+    const int tn = blockIdx.x % g.tiles_n;          // this CTA's column tile
+    const uint32_t sb = smem_u32(base);
+    const uint32_t sW = sb, sX = sb + (uint32_t)(katoms * kLN * 128);
+    uint8_t *staging = base + katoms * kLN * 128 + S * SB;
+    float *sbias = reinterpret_cast<float *>(staging + kLEpiWarps * kLStaging);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sbias + kLN);
+    uint64_t *empty = full + kLStagesMax, *tfull = empty + kLStagesMax, *tempty = tfull + 2;
+    uint64_t *wbar = tempty + 2, *done = wbar + 1;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kLEpiWarps);
+        }
+        mbar_init(wbar, 1);
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (EPI == kEpiBiasElu)
+        for (int c = threadIdx.x; c < kLN; c += kLThreads)
+            sbias[c] = tn * kLN + c < g.W ? e.bias[tn * kLN + c] : 0.f;
+    if (warp == 1) tmem_alloc(holder, 2 * kLN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(wbar, (uint32_t)(katoms * kLN * 128));
+            for (int a = 0; a < katoms; ++a)
+                tma_load_2d(sW + (uint32_t)(a * kLN * 128), &mW, a * kTK, tn * kLN, wbar);
+            int st = 0;
+            uint32_t ph = 0, filled = 0, last_ph = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                const int p0 = (u / g.tiles_n) * kLP;
+                for (int c = 0; c < katoms; ++c) {
+                    if (!mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
+                    const uint32_t dst = sX + (uint32_t)(st * SB);
+                    mbar_expect_tx(&full[st], (uint32_t)SB);
+                    tma_load_2d(dst, &mX, c * kTK, p0, &full[st]);
+                    if (SPLIT) tma_load_2d(dst + kTileBytes, &mXlo, c * kTK, p0, &full[st]);
+                    filled |= 1u << st;
+                    last_ph = (last_ph & ~(1u << st)) | (ph << st);
+                    if (++st == S) { st = 0; ph ^= 1u; }
+                }
+            }
+            if (!ok) {
+                set_status(status, NSF_ERR_ITER_CAP);
+                for (int i = 0; i < S; ++i)
+                    if (filled >> i & 1u) mbar_wait(&full[i], (last_ph >> i) & 1u);
+            }
+            mbar_wait(wbar, 0);          // the weights have landed before the CTA ends
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kLP, kLN);
+            int st = 0, it = 0;
+            uint32_t ph = 0;
+            bool ok = mbar_wait(wbar, 0);
+            for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+                const int acc = it & 1;
+                if (!mbar_wait(&tempty[acc], ((it >> 1) & 1) ^ 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * kLN);
+                for (int c = 0; c < katoms; ++c) {
+                    if (!mbar_wait(&full[st], ph)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t x = sX + (uint32_t)(st * SB), w = sW + (uint32_t)(c * kLN * 128);
+#pragma unroll
+                    for (int ks = 0; ks < kTK / 16; ++ks) {
+                        const uint64_t bd = sw128_desc(w + 32u * ks);
+                        mma_bf16(d, sw128_desc(x + 32u * ks), bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        if (SPLIT) mma_bf16(d, sw128_desc(x + kTileBytes + 32u * ks), bd, idesc, 1u);
+                    }
+                    mma_commit(&empty[st]);
+                    if (++st == S) { st = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+                ++it;
+            }
+            if (!ok) set_status(status, NSF_ERR_ITER_CAP);
+            mma_commit(done);
+            mbar_wait(done, 0);
+        }
+    } else {
+        const int q = warp & 3, bt = (warp - 2) >> 2;
+        const int c_loc = 32 * bt, chan0 = tn * kLN + c_loc;
+        const int cw = g.W - chan0;                  // valid channels of this warp (may be <= 0)
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        uint8_t *st = staging + (warp - 2) * kLStaging;
+        float csum = 0.f;
+        int it = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
+            const int row0 = (u / g.tiles_n) * kLP + q * 32;   // the warp's first point
+            uint4 pf[EPI == kEpiEluGrad ? 4 : 1];
+            if (EPI == kEpiEluGrad) {
+                // the ELU' codes, coalesced, before the accumulator is ready
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = 8 * i + (lane >> 2), ck = lane & 3;
+                    pf[i] = (row0 + r < g.n && 8 * ck < cw)
+                                ? __ldg(reinterpret_cast<const uint4 *>(
+                                      e.dact + (size_t)(row0 + r) * g.ld + chan0 + 8 * ck))
+                                : make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+            const int acc = it & 1;
+            if (!mbar_wait(&tfull[acc], (it >> 1) & 1)) {
+                set_status(status, NSF_ERR_ITER_CAP);
+                break;
+            }
+            tc_fence_after();
+            float v[32];
+            tmem_ld32(tmem + (uint32_t)(acc * kLN + c_loc) + lane_off, v);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);   // free for the unit after next
+            ++it;
+            if (EPI == kEpiBiasElu) {
+                uint32_t code[16], hb[16];
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 b4 = *reinterpret_cast<const float4 *>(sbias + c_loc + j);
+                    elu2_codes(make_float2(v[j], v[j + 1]), make_float2(b4.x, b4.y), code[j / 2],
+                               hb[j / 2]);
+                    elu2_codes(make_float2(v[j + 2], v[j + 3]), make_float2(b4.z, b4.w),
+                               code[j / 2 + 1], hb[j / 2 + 1]);
+                }
+                store_rows16(st, code, e.dact + chan0, g.ld, row0, g.n, cw);
+                store_rows16(st, hb, reinterpret_cast<uint16_t *>(e.h16) + chan0, g.ld, row0, g.n,
+                             cw);
+            } else {
+                // the codes of this lane's row, from the coalesced loads
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<uint4 *>(st + (8 * i + (lane >> 2)) * kLRow + 16 * (lane & 3)) =
+                        pf[i];
+                __syncwarp();
+                uint32_t code[16];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint4 w4 = *reinterpret_cast<const uint4 *>(st + lane * kLRow + 16 * c);
+                    code[4 * c] = w4.x;
+                    code[4 * c + 1] = w4.y;
+                    code[4 * c + 2] = w4.z;
+                    code[4 * c + 3] = w4.w;
+                }
+                __syncwarp();
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const float2 o = mul_codes2(make_float2(v[2 * t], v[2 * t + 1]), code[t]);
+                    v[2 * t] = o.x;
+                    v[2 * t + 1] = o.y;
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(o.x, o.y);
+                    hi[t] = *reinterpret_cast<const uint32_t *>(&h2);
+                    const float2 r = __fadd2_rn(o, make_float2(-__low2float(h2), -__high2float(h2)));
+                    lo[t] = pack_bf16x2(r.x, r.y);
+                }
+                store_rows16(st, hi, reinterpret_cast<uint16_t *>(e.dhi) + chan0, g.ld, row0, g.n,
+                             cw);
+                store_rows16(st, lo, reinterpret_cast<uint16_t *>(e.dlo) + chan0, g.ld, row0, g.n,
+                             cw);
+                const int p = row0 + lane;
+                if (e.out && p < g.n)
+#pragma unroll
+                    for (int k4 = 0; k4 < 8; ++k4)
+                        if (4 * k4 < cw)
+                            *reinterpret_cast<float4 *>(e.out + (size_t)p * g.ld + chan0 + 4 * k4) =
+                                make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
+                // points past n have zero products and zero codes: o = 0
+                if (e.colsum) csum += lane_column_sum(v);
+            }
+        }
+        if (EPI == kEpiEluGrad && e.colsum && lane < cw)
+            e.colsum[((size_t)(blockIdx.x / g.tiles_n) * 4 + q) * g.W + chan0 + lane] = csum;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * kLN);
+    }
+}
+
+// Sums rows z in [y per, min(slices, (y + 1) per)) of the slabs (row z at
+// slab + z step) for y = blockIdx.y into out + y out_step: 32 outputs a CTA,
+// 8 groups of rows per output, then a shared sum, all in a fixed order.
+// With out = slab and out_step = per step, a CTA overwrites only the first
+// row of its own range, after all its reads: the first pass of a two-pass sum.
+__global__ void k_reduce_slabs(const float *slab, int slices, int per, long long step,
+                               long long count, float *out, long long out_step) {
     __shared__ float part[8][33];
     const int ix = threadIdx.x & 31, g = threadIdx.x >> 5;
     const long long i = (long long)blockIdx.x * 32 + ix;
+    const int z0 = blockIdx.y * per, z1 = min(slices, z0 + per);
     float s = 0.f;
-    if (i < count)
-        for (int z = g; z < slices; z += 8) s += slab[(size_t)z * count + i];
+    if (i < count) {
+        int z = z0 + g;
+        // four independent loads in flight per thread, summed in row order
+        for (; z + 24 < z1; z += 32) {
+            const float a = slab[(size_t)z * step + i], b = slab[(size_t)(z + 8) * step + i];
+            const float c = slab[(size_t)(z + 16) * step + i], d = slab[(size_t)(z + 24) * step + i];
+            s += a;
+            s += b;
+            s += c;
+            s += d;
+        }
+        for (; z < z1; z += 8) s += slab[(size_t)z * step + i];
+    }
     part[g][ix] = s;
     __syncthreads();
     if (g == 0 && i < count) {
         float t = 0.f;
 #pragma unroll
         for (int q = 0; q < 8; ++q) t += part[q][ix];
-        out[i] = t;
+        out[(size_t)blockIdx.y * out_step + i] = t;
     }
 }
 
 int slice_len(int K, int slices, int multiple) {
     const int per = (K + slices - 1) / slices;
     return (per + multiple - 1) / multiple * multiple;
+}
+
+// ----------------------------------------------------------- thin K ----
+// out(m, n) = sum_{k < K} A(m, k) B(n, k) for K <= 20 (the input layer's
+// forward product, the output layer's backward product) with the BiasElu /
+// EluGrad epilogues of the BF16 path.  M % 4 == 0: thread (m4, point)
+// computes rows 4 m4 .. 4 m4 + 3 of one column, so every store is a vector
+// (8 bytes of codes or bf16, 16 bytes of float).  A sits in shared memory as
+// [k][m]; B's K values of a point are read by all the point's threads (one
+// broadcast).  EluGrad's colsum: each CTA's sums of out over its columns,
+// colsum[blockIdx.x * M + m], in a fixed order.
+constexpr int kThinKMax = 20, kTkThreads = 256, kTkPoints = 64;
+
+__device__ __forceinline__ uint2 pack_codes4(const float *g) {
+    return make_uint2((unsigned)dact_code(g[0]) | ((unsigned)dact_code(g[1]) << 16),
+                      (unsigned)dact_code(g[2]) | ((unsigned)dact_code(g[3]) << 16));
+}
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+    return make_uint2(pack_bf16x2(a, b), pack_bf16x2(c, d));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kTkThreads)
+k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilogue e) {
+    extern __shared__ float tk_smem[];
+    float *As = tk_smem;                          // [K][M]
+    const int q = M / 4, ppass = kTkThreads / q;  // threads per column, columns per pass
+    for (int t = threadIdx.x; t < K * M; t += kTkThreads) As[t] = view_at(A, t % M, t / M);
+    __syncthreads();
+    const int pofs = threadIdx.x / q, m = 4 * (threadIdx.x % q);
+    const bool active = pofs < ppass;
+    float bias[4] = {0.f, 0.f, 0.f, 0.f};
+    if (EPI == kEpiBiasElu && active)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bias[u] = e.bias[m + u];
+    float cs[4] = {0.f, 0.f, 0.f, 0.f};
+    const int p_end = min(N, (blockIdx.x + 1) * kTkPoints);
+    if (active)
+        for (int p = blockIdx.x * kTkPoints + pofs; p < p_end; p += ppass) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < kThinKMax; ++k) {
+                if (k >= K) break;
+                const float b = view_at(B, p, k);
+                const float4 a = *reinterpret_cast<const float4 *>(As + k * M + m);
+                acc[0] = fmaf(a.x, b, acc[0]);
+                acc[1] = fmaf(a.y, b, acc[1]);
+                acc[2] = fmaf(a.z, b, acc[2]);
+                acc[3] = fmaf(a.w, b, acc[3]);
+            }
+            const size_t i = (size_t)p * e.ld + m;
+            if (EPI == kEpiBiasElu) {
+                float h[4], g[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) h[u] = elu_bf16_path(acc[u] + bias[u], g[u]);
+                *reinterpret_cast<uint2 *>(e.dact + i) = pack_codes4(g);
+                *reinterpret_cast<uint2 *>(e.h16 + i) = pack_bf16x4(h[0], h[1], h[2], h[3]);
+            } else {
+                const uint2 c = *reinterpret_cast<const uint2 *>(e.dact + i);
+                const float o[4] = {acc[0] * dact_value(c.x & 0xFFFFu), acc[1] * dact_value(c.x >> 16),
+                                    acc[2] * dact_value(c.y & 0xFFFFu), acc[3] * dact_value(c.y >> 16)};
+                if (e.out) *reinterpret_cast<float4 *>(e.out + i) = make_float4(o[0], o[1], o[2], o[3]);
+                float hi[4], lo[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    hi[u] = __bfloat162float(__float2bfloat16_rn(o[u]));
+                    lo[u] = o[u] - hi[u];
+                    cs[u] += o[u];
+                }
+                *reinterpret_cast<uint2 *>(e.dhi + i) = pack_bf16x4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint2 *>(e.dlo + i) = pack_bf16x4(lo[0], lo[1], lo[2], lo[3]);
+            }
+        }
+    if (EPI == kEpiEluGrad && e.colsum) {
+        float *part = As + K * M;                 // [ppass][M]
+        if (active)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) part[pofs * M + m + u] = cs[u];
+        __syncthreads();
+        for (int mm = threadIdx.x; mm < M; mm += kTkThreads) {
+            float t = 0.f;
+            for (int u = 0; u < ppass; ++u) t += part[u * M + mm];
+            e.colsum[(size_t)blockIdx.x * M + mm] = t;
+        }
+    }
 }
 
 // ------------------------------------------------------- thin shapes ----
@@ -527,45 +981,152 @@ cudaError_t gemm_simt(int M, int N, int K, const MatView &A, const MatView &B,
 }
 
 namespace {
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// The tensor map of a bf16 operand with `rows` rows and K columns, stride
+// `stride` elements along its strided dimension, 128-byte swizzle: boxes of
+// 64 k x 128 rows (K-major) or 64 rows x 64 k (MN-major); out-of-range
+// elements read as zero.
+bool operand_map(CUtensorMap *map, const void *ptr, bool mn, int rows, int K, long long stride,
+                 int box_rows = 128) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return false;
+    cuuint64_t dims[2], strides[1] = {(cuuint64_t)stride * 2};
+    cuuint32_t box[2], es[2] = {1, 1};
+    if (mn) {
+        dims[0] = (cuuint64_t)rows; dims[1] = (cuuint64_t)K;
+        box[0] = 64; box[1] = 64;
+    } else {
+        dims[0] = (cuuint64_t)K; dims[1] = (cuuint64_t)rows;
+        box[0] = 64; box[1] = (cuuint32_t)box_rows;
+    }
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 template <bool AMN, bool BMN, int SPLIT, int EPI>
-cudaError_t launch_tc(int M, int N, int K, int kper, dim3 grid, const MatView &A,
-                      const MatView &B, const GemmEpilogue &e, int *status, cudaStream_t s) {
+cudaError_t launch_tc(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mLo,
+                      const WsShape &g, const GemmEpilogue &e, int *status, cudaStream_t s) {
     static bool attr = false;
     set_max_dynamic_smem(k_gemm_tc<AMN, BMN, SPLIT, EPI>, attr);
-    k_gemm_tc<AMN, BMN, SPLIT, EPI><<<grid, kTThreads, tc_gemm_layout(SPLIT != 0).total, s>>>(
-        M, N, K, kper, A, B, e, status);
+    const int grid = g.units < sm_count() ? g.units : sm_count();
+    k_gemm_tc<AMN, BMN, SPLIT, EPI><<<grid, kWsThreads, ws_smem_bytes(SPLIT != 0), s>>>(
+        mA, mB, mLo, g, e, status);
     return cudaGetLastError();
 }
 }  // namespace
 
-// The three product shapes of training: forward (bf16 weights and
-// activations, both with contiguous k, bias + ELU), backward data (weights
-// transposed and the cotangent's hi/lo pairs, both with contiguous k,
-// * ELU'), weight gradient (cotangent pairs and activations, both with
-// contiguous rows, slabs).
+namespace {
+// One CTA per SM at most, a multiple of the column-tile count.
+int layer_grid(int units, int tiles_n) {
+    int grid = units < sm_count() ? units : sm_count();
+    grid -= grid % tiles_n;
+    return grid < tiles_n ? tiles_n : grid;
+}
+
+template <bool SPLIT, int EPI>
+cudaError_t launch_layer(const CUtensorMap &mX, const CUtensorMap &mXlo, const CUtensorMap &mW,
+                         const LayerShape &g, const GemmEpilogue &e, int *status, cudaStream_t s) {
+    static bool attr = false;
+    set_max_dynamic_smem(k_layer_tc<SPLIT, EPI>, attr);
+    k_layer_tc<SPLIT, EPI><<<layer_grid(g.units, g.tiles_n), kLThreads,
+                             layer_smem_bytes(g.K, SPLIT, g.stages), s>>>(mX, mXlo, mW, g, e, status);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int layer_tc_parts(int n, int W) {
+    const int tiles_n = (W + kLN - 1) / kLN;
+    return 4 * layer_grid(((n + kLP - 1) / kLP) * tiles_n, tiles_n) / tiles_n;
+}
+
+cudaError_t layer_tc(int n, int W, int K, const MatView &X, const MatView &Wt,
+                     const GemmEpilogue &e, int *status, cudaStream_t s) {
+    if (n <= 0 || W <= 0) return cudaSuccess;
+    const bool split = X.lo != nullptr;
+    if (W > NSF_MAX_WIDTH || W % 16 || K <= 0 || K > NSF_MAX_WIDTH || e.ld % 8 || !e.dact)
+        return cudaErrorInvalidValue;
+    if (!X.bf16 || !Wt.bf16 || X.s_k != 1 || Wt.s_k != 1 || X.s_row % 8 || Wt.s_row % 8)
+        return cudaErrorInvalidValue;
+    auto al16 = [](const void *p) { return p == nullptr || ((size_t)p & 15) == 0; };
+    if (!al16(X.ptr) || !al16(X.lo) || !al16(Wt.ptr) || !al16(e.dact)) return cudaErrorInvalidValue;
+    if (e.mode == kEpiBiasElu) {
+        if (split || !e.h16 || !al16(e.h16)) return cudaErrorInvalidValue;
+    } else if (e.mode == kEpiEluGrad) {
+        if (!split || !e.dhi || !e.dlo || !al16(e.dhi) || !al16(e.dlo) || !al16(e.out))
+            return cudaErrorInvalidValue;
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    LayerShape g;
+    g.n = n;
+    g.W = W;
+    g.K = K;
+    g.ld = e.ld;
+    g.tiles_n = (W + kLN - 1) / kLN;
+    g.units = ((n + kLP - 1) / kLP) * g.tiles_n;
+    const int fixed = layer_smem_bytes(K, split, 0);
+    g.stages = (kMaxSmem - fixed) / layer_stage_bytes(split);
+    if (g.stages > kLStagesMax) g.stages = kLStagesMax;
+    if (g.stages < 2) return cudaErrorInvalidValue;
+    CUtensorMap mX, mXlo, mW;
+    if (!operand_map(&mX, X.ptr, false, n, K, X.s_row)) return cudaErrorInvalidValue;
+    mXlo = mX;
+    if (split && !operand_map(&mXlo, X.lo, false, n, K, X.s_row)) return cudaErrorInvalidValue;
+    if (!operand_map(&mW, Wt.ptr, false, W, K, Wt.s_row)) return cudaErrorInvalidValue;
+    if (e.mode == kEpiBiasElu) return launch_layer<false, kEpiBiasElu>(mX, mXlo, mW, g, e, status, s);
+    return launch_layer<true, kEpiEluGrad>(mX, mXlo, mW, g, e, status, s);
+}
+
+// The weight-gradient shape of training: the cotangent's hi/lo pairs and the
+// activations, both with contiguous rows, K-slices into slabs.
 cudaError_t gemm_tc(int M, int N, int K, const MatView &A, const MatView &B, int split,
                     const GemmEpilogue &e, int kslices, int *status, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (kslices < 1 || (kslices > 1 && e.mode != kEpiSlab)) return cudaErrorInvalidValue;
-    const int kper = slice_len(K, kslices, kTK);
-    dim3 grid((N + kTN - 1) / kTN, (M + kTM - 1) / kTM, e.mode == kEpiSlab ? kslices : 1);
+    WsShape g;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kper = slice_len(K, kslices, kTK);
+    g.tiles_m = (M + kTM - 1) / kTM;
+    g.tiles_n = (N + kTN - 1) / kTN;
+    g.units = g.tiles_m * g.tiles_n * (e.mode == kEpiSlab ? kslices : 1);
     const bool a_mn = A.s_row == 1 && A.s_k != 1, b_mn = B.s_row == 1 && B.s_k != 1;
-    // bf16 operands whose 16-byte chunks are aligned and lie wholly in or out
-    // of range
-    auto ok = [&](const MatView &V, bool mn, int rows, bool lo) {
+    // bf16 operands, 16-byte aligned, strides multiples of 16 bytes
+    auto ok = [&](const MatView &V, bool mn, bool lo) {
         if (!V.bf16 || (lo && !V.lo)) return false;
         const long long stride = mn ? V.s_k : V.s_row;
-        if ((mn ? V.s_row : V.s_k) != 1 || stride % 8) return false;
-        if ((((size_t)V.ptr) & 15) || (lo && (((size_t)V.lo) & 15))) return false;
-        return mn ? rows % 8 == 0 : K % 8 == 0;
+        if ((mn ? V.s_row : V.s_k) != 1 || stride % 8 || stride <= 0) return false;
+        return !((((size_t)V.ptr) & 15) || (lo && (((size_t)V.lo) & 15)));
     };
-    if (!ok(A, a_mn, M, split == 1) || !ok(B, b_mn, N, split == 2)) return cudaErrorInvalidValue;
-    if (!a_mn && !b_mn && split == 0 && e.mode == kEpiBiasElu)
-        return launch_tc<false, false, 0, kEpiBiasElu>(M, N, K, kper, grid, A, B, e, status, s);
-    if (!a_mn && !b_mn && split == 2 && e.mode == kEpiEluGrad)
-        return launch_tc<false, false, 2, kEpiEluGrad>(M, N, K, kper, grid, A, B, e, status, s);
+    if (!ok(A, a_mn, split == 1) || !ok(B, b_mn, split == 2)) return cudaErrorInvalidValue;
+    CUtensorMap mA, mB, mLo;
+    if (!operand_map(&mA, A.ptr, a_mn, M, K, a_mn ? A.s_k : A.s_row) ||
+        !operand_map(&mB, B.ptr, b_mn, N, K, b_mn ? B.s_k : B.s_row))
+        return cudaErrorInvalidValue;
+    mLo = mA;
+    if (split == 1 && !operand_map(&mLo, A.lo, a_mn, M, K, a_mn ? A.s_k : A.s_row))
+        return cudaErrorInvalidValue;
+    if (split == 2 && !operand_map(&mLo, B.lo, b_mn, N, K, b_mn ? B.s_k : B.s_row))
+        return cudaErrorInvalidValue;
     if (a_mn && b_mn && split == 1 && e.mode == kEpiSlab)
-        return launch_tc<true, true, 1, kEpiSlab>(M, N, K, kper, grid, A, B, e, status, s);
+        return launch_tc<true, true, 1, kEpiSlab>(mA, mB, mLo, g, e, status, s);
     return cudaErrorInvalidValue;   // a shape training does not use
 }
 
@@ -585,7 +1146,7 @@ cudaError_t thin_outer(int A, int C, int K, const MatView &U, const MatView &V, 
     if (transposed)
         k_reduce_slabs_t<<<(int)((count + 31) / 32), 256, 0, s>>>(slab, slices, A, C, out);
     else
-        k_reduce_slabs<<<(int)((count + 31) / 32), 256, 0, s>>>(slab, slices, count, out);
+        return reduce_slabs(slab, slices, count, out, s);
     return cudaGetLastError();
 }
 
@@ -600,10 +1161,62 @@ cudaError_t thin_m(int M, int N, int K, const MatView &A, const MatView &B, floa
     return cudaGetLastError();
 }
 
-cudaError_t reduce_slabs(const float *slab, int slices, long long count, float *out,
-                         cudaStream_t s) {
+int thin_k_parts(int N) { return (N + kTkPoints - 1) / kTkPoints; }
+
+cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
+                   const GemmEpilogue &e, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K < 1 || K > kThinKMax || M % 4 || M > NSF_MAX_WIDTH || e.ld % 4 || !e.dact)
+        return cudaErrorInvalidValue;
+    auto al = [](const void *p, int a) { return (((size_t)p) % a) == 0; };
+    if (!al(e.dact, 8)) return cudaErrorInvalidValue;
+    if (e.mode == kEpiBiasElu && (!e.h16 || !al(e.h16, 8))) return cudaErrorInvalidValue;
+    if (e.mode == kEpiEluGrad &&
+        (!e.dhi || !e.dlo || !al(e.dhi, 8) || !al(e.dlo, 8) || (e.out && !al(e.out, 16))))
+        return cudaErrorInvalidValue;
+    const int ppass = kTkThreads / (M / 4);
+    const size_t smem = (size_t)(K + ppass) * M * sizeof(float);
+    const int grid = thin_k_parts(N);
+    if (e.mode == kEpiBiasElu)
+        k_thin_k<kEpiBiasElu><<<grid, kTkThreads, smem, s>>>(M, N, K, A, B, e);
+    else if (e.mode == kEpiEluGrad)
+        k_thin_k<kEpiEluGrad><<<grid, kTkThreads, smem, s>>>(M, N, K, A, B, e);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_slabs_t(const float *slab, int slices, int A, int C, float *out,
+                           cudaStream_t s) {
+    const long long count = (long long)A * C;
     if (count <= 0) return cudaSuccess;
-    k_reduce_slabs<<<(int)((count + 31) / 32), 256, 0, s>>>(slab, slices, count, out);
+    k_reduce_slabs_t<<<(int)((count + 31) / 32), 256, 0, s>>>(slab, slices, A, C, out);
+    return cudaGetLastError();
+}
+
+// Few outputs over many slabs (the bias column sums): first sums of groups of
+// rows in place, one CTA per group, then the sum of the groups' results.
+// The slab is overwritten.
+cudaError_t reduce_slabs(float *slab, int slices, long long count, float *out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int cx = (int)((count + 31) / 32);
+    int groups = 1;
+    if (slices >= 64 && cx < sm_count()) {
+        groups = (2 * sm_count() + cx - 1) / cx;
+        if (groups > slices / 16) groups = slices / 16;
+    }
+    if (groups > 1) {
+        const int per = (slices + groups - 1) / groups;
+        groups = (slices + per - 1) / per;
+        k_reduce_slabs<<<dim3(cx, groups), 256, 0, s>>>(slab, slices, per, count, count, slab,
+                                                         (long long)per * count);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_slabs<<<dim3(cx, 1), 256, 0, s>>>(slab, groups, groups, (long long)per * count,
+                                                    count, out, 0);
+        return cudaGetLastError();
+    }
+    k_reduce_slabs<<<dim3(cx, 1), 256, 0, s>>>(slab, slices, slices, count, count, out, 0);
     return cudaGetLastError();
 }
 

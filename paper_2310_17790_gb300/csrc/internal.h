@@ -192,27 +192,31 @@ struct MatView {
 enum { kEpiStore = 0, kEpiBiasElu = 1, kEpiEluGrad = 2, kEpiSlab = 3 };
 struct GemmEpilogue {
     int mode;
-    float *out;            // Store, EluGrad: out[n * ld + m]; Slab: out[z M N + m N + n]
+    float *out;            // Store, EluGrad: out[n * ld + m]; Slab: out[z M N + n M + m]
     long long ld;
     const float *bias;     // BiasElu: pre = D + bias[m] -> pre[n ld + m]
     float *pre;
-    float *h32;            // BiasElu: ELU(pre) (rounded to bf16 when round_bf16)
+    float *h32;            // BiasElu: ELU(pre) (may be null)
     __nv_bfloat16 *h16;    // BiasElu: its bf16 copy (may be null)
-    int round_bf16;
     const float *apre;     // EluGrad: out = D * ELU'(apre[n ld + m])
-    float *colsum;         // EluGrad on the tensor cores (may be null): per-CTA sums of out
-                           // over its columns, colsum[(blockIdx.x * 2 + half) * M + m]
+    float *colsum;         // (may be null) partial sums for a bias gradient: see the
+                           // products that take it
     __nv_bfloat16 *dhi, *dlo;   // EluGrad (may be null): out as hi = bf16(v), lo = bf16(v - hi)
+    unsigned short *dact;  // BF16 path (replaces pre / apre): ELU'(pre) as the 16-bit code
+                           // rint(ELU' 2^15) at [n ld + m]; BiasElu then writes only dact
+                           // and h16 (ELU on the special-function unit)
 };
 // FP32 product on the CUDA cores; K split over `kslices` slices (only with
 // the Slab epilogue, which writes one M x N slab per slice).
 cudaError_t gemm_simt(int M, int N, int K, const MatView &A, const MatView &B,
                       const GemmEpilogue &e, int kslices, cudaStream_t s);
 // BF16 product on the tcgen05 tensor cores with FP32 accumulation in tensor
-// memory.  Both operands bf16, each either with contiguous k (s_k = 1) or
-// with contiguous rows (s_row = 1), strides multiples of 8 elements; split =
-// 1 (2) adds the product of operand A's (B's) lo parts (view.lo), so that an
-// operand kept as hi + lo pairs counts with ~16 significant bits.
+// memory, operands brought in by TMA (the Slab epilogue; with e.colsum also
+// the sums of A over each K-slice, colsum[z * M + m]).  Both operands bf16, each either with
+// contiguous k (s_k = 1) or with contiguous rows (s_row = 1), 16-byte
+// aligned, strides multiples of 8 elements; split = 1 (2) adds the product of
+// operand A's (B's) lo parts (view.lo), so that an operand kept as hi + lo
+// pairs counts with ~16 significant bits.
 cudaError_t gemm_tc(int M, int N, int K, const MatView &A, const MatView &B, int split,
                     const GemmEpilogue &e, int kslices, int *status, cudaStream_t s);
 // Thin shapes.  thin_outer: out(a, c) = sum_k U(a, k) V(c, k) for A <= 32,
@@ -223,9 +227,29 @@ cudaError_t thin_outer(int A, int C, int K, const MatView &U, const MatView &V, 
                        int slices, float *out, bool transposed, cudaStream_t s);
 cudaError_t thin_m(int M, int N, int K, const MatView &A, const MatView &B, float *out,
                    long long ld, cudaStream_t s);
-// out[i] = sum over z < slices of slab[z * count + i] (fixed order).
-cudaError_t reduce_slabs(const float *slab, int slices, long long count, float *out,
-                         cudaStream_t s);
+// The hidden layers' products on the tensor cores, the points as the M
+// dimension: Y(p, c) = sum_k X(p, k) Wt(c, k) for p < n, c < W (<= 256, a
+// multiple of 16), k < K (<= 256); X bf16 [p][k] (with lo parts: the split
+// cotangent of the backward product), Wt bf16 [c][k].  Epilogue BiasElu (X
+// without lo; dact and h16) or EluGrad (X with lo; dact, dhi, dlo, optional
+// out and colsum), all at [p ld + c].  EluGrad's colsum gets layer_tc_parts(n, W)
+// partial sums per channel: colsum[part * W + c].
+cudaError_t layer_tc(int n, int W, int K, const MatView &X, const MatView &Wt,
+                     const GemmEpilogue &e, int *status, cudaStream_t s);
+int layer_tc_parts(int n, int W);
+// Thin K (<= 20): the input layer's forward product and the output layer's
+// backward product on the BF16 path (epilogue BiasElu or EluGrad with dact;
+// M % 4 == 0, ld % 4 == 0).  EluGrad's colsum gets thin_k_parts(N) partial
+// sums per row: colsum[part * M + m].
+cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
+                   const GemmEpilogue &e, cudaStream_t s);
+int thin_k_parts(int N);
+// out[i] = sum over z < slices of slab[z * count + i] (fixed order); the slab
+// may be overwritten.
+cudaError_t reduce_slabs(float *slab, int slices, long long count, float *out, cudaStream_t s);
+// The same sums transposed: slab[z][a][c] (count A C) -> out[c * A + a].
+cudaError_t reduce_slabs_t(const float *slab, int slices, int A, int C, float *out,
+                           cudaStream_t s);
 
 // --------------------------------------------------------------- training ---
 // Workspace of one loss/gradient evaluation (train.cu).

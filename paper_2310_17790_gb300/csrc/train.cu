@@ -204,8 +204,7 @@ __global__ void k_repack(const float *__restrict__ flat, long long total, int r,
     }
 }
 
-// K slices of a weight-gradient product over n points whose output has
-// `tiles` tiles: enough CTAs to cover the SMs, at least 256 points a slice.
+// Most K slices of a weight-gradient product (the slab holds this many).
 constexpr int kMaxSlices = 48;
 // K slices of a thin product (one 256-thread CTA per slice): 256 points a
 // slice, at most kMaxThinSlices.
@@ -214,8 +213,11 @@ int thin_slices(int n) {
     const int k = n / 256;
     return k < 1 ? 1 : (k > kMaxThinSlices ? kMaxThinSlices : k);
 }
-int weight_slices(int n, int tiles) {
-    int k = (2 * tc::sm_count() + tiles - 1) / tiles;
+// K slices of a weight-gradient product over n points whose output has
+// `tiles` tiles: about one work unit per SM for the persistent tensor-core
+// kernel, two CTAs per SM for the CUDA-core one; at least 256 points a slice.
+int weight_slices(int n, int tiles, bool tc_kernel) {
+    int k = tc_kernel ? tc::sm_count() / tiles : (2 * tc::sm_count() + tiles - 1) / tiles;
     k = k > kMaxSlices ? kMaxSlices : k;
     const int by_n = (n + 255) / 256;
     k = k > by_n ? by_n : k;
@@ -228,6 +230,7 @@ MatView view(const void *p, long long s_row, long long s_k, int bf16) {
     v.s_row = s_row;
     v.s_k = s_k;
     v.bf16 = bf16;
+    v.lo = nullptr;
     return v;
 }
 
@@ -275,10 +278,11 @@ TrainLayout train_layout(int r, int W, int D, int od, int n) {
     // slice), thin products (at most max(3 + r, od) x W per slice), the loss
     // kernel's per-CTA output-bias sums
     const size_t thin_a = (size_t)(3 + r > od ? 3 + r : od);
-    size_t slab = (size_t)kMaxSlices * W * W;
+    size_t slab = (size_t)kMaxSlices * W * (W + 1);     // weight and bias gradient slabs
     slab = slab > (size_t)kMaxThinSlices * thin_a * W ? slab : (size_t)kMaxThinSlices * thin_a * W;
     const size_t loss_parts = (nn + kT - 1) / kT * (size_t)od;
-    const size_t col_parts = 2 * ((nn + 127) / 128) * (size_t)W;    // bias column sums
+    // bias column sums: at most 4 per 128 points (layer_tc) or 1 per 64 (thin_k)
+    const size_t col_parts = (4 * ((nn + 127) / 128) + (nn + 63) / 64) * (size_t)W;
     slab = slab > loss_parts ? slab : loss_parts;
     slab = slab > col_parts ? slab : col_parts;
     L.slab = take(slab * 4);
@@ -308,34 +312,44 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
                    : gemm_simt(M, N, K, A, B, e, slices, s);
     };
     // sum over all n points (K) of an M x N product into dst, by K slices
+    // (on the tensor cores, with bias_dst: also bias_dst[m] = sum over the n
+    // points of A(m, .), from a product of A with ones)
     auto summed = [&](int M, int N, const MatView &A, const MatView &B, bool tc, int split,
-                      float *dst) -> cudaError_t {
+                      float *dst, float *bias_dst = nullptr) -> cudaError_t {
         const int tiles = tc ? ((M + 127) / 128) * ((N + 127) / 128)
                              : ((M + 63) / 64) * ((N + 63) / 64);
-        const int k = weight_slices(n, tiles);
-        const GemmEpilogue e = epi(kEpiSlab, slab);
+        const int k = weight_slices(n, tiles, tc);
+        GemmEpilogue e = epi(kEpiSlab, slab);
+        float *bslab = slab + (size_t)kMaxSlices * M * N;
+        if (bias_dst) e.colsum = bslab;
         cudaError_t err = tc ? gemm_tc(M, N, n, A, B, split, e, k, status, s)
                              : gemm_simt(M, N, n, A, B, e, k, s);
         if (err != cudaSuccess) return err;
-        return reduce_slabs(slab, k, (long long)M * N, dst, s);
+        if (bias_dst && (err = reduce_slabs(bslab, k, M, bias_dst, s)) != cudaSuccess) return err;
+        return reduce_slabs_t(slab, k, N, M, dst, s);   // slab [z][n][m] -> dst[m N + n]
     };
     auto bias_elu = [&](int l) {
         GemmEpilogue e = epi(kEpiBiasElu);
         e.ld = W;
         e.bias = F.b[l];
-        e.pre = P(L.A[l]);
-        e.h32 = b16 ? nullptr : P(L.H[l]);         // BF16 fields read the bf16 copy
-        e.h16 = b16 ? P16(L.H16[l]) : nullptr;
-        e.round_bf16 = b16;
+        if (b16) {       // ELU' codes and the bf16 activations the products read
+            e.dact = reinterpret_cast<unsigned short *>(ws + L.A[l]);
+            e.h16 = P16(L.H16[l]);
+        } else {
+            e.pre = P(L.A[l]);
+            e.h32 = P(L.H[l]);
+        }
         return e;
     };
     auto elu_grad = [&](float *out, int l, int pair, float *colsum = nullptr) {
         GemmEpilogue e = epi(kEpiEluGrad, out, W);
-        e.apre = P(L.A[l]);
         e.colsum = colsum;
         if (b16) {
+            e.dact = reinterpret_cast<unsigned short *>(ws + L.A[l]);
             e.dhi = P16(L.dh[pair]);
             e.dlo = P16(L.dl[pair]);
+        } else {
+            e.apre = P(L.A[l]);
         }
         return e;
     };
@@ -344,7 +358,12 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     const MatView Hlast_cols = b16 ? view(P16(L.H16[D - 1]), 1, W, 1) : view(P(L.H[D - 1]), 1, W, 0);
     // ---- forward
     k_inputs<<<blocks(n), kT, 0, s>>>(X, code, z_table, n, r, P(L.inp), status);
-    NSF_GT(gemm_simt(W, n, K0, view(F.W0, K0, 1, 0), view(P(L.inp), K0, 1, 0), bias_elu(0), 1, s));
+    // the input layer (K0 = 3 + r inputs)
+    if (b16)
+        NSF_GT(thin_k(W, n, K0, view(F.W0, K0, 1, 0), view(P(L.inp), K0, 1, 0), bias_elu(0), s));
+    else
+        NSF_GT(gemm_simt(W, n, K0, view(F.W0, K0, 1, 0), view(P(L.inp), K0, 1, 0), bias_elu(0),
+                         1, s));
     if (b16)
         for (int l = 1; l < D; ++l)
             k_weights_bf16<<<blocks((long long)W * W), kT, 0, s>>>(F.Wt[l], W, P16(L.Wb[l]),
@@ -352,8 +371,8 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     for (int l = 1; l < D; ++l) {
         // A_l(o, p) = sum_c W_l[o][c] H_{l-1}(c, p), W_l[o][c] = Wt[l][c W + o]
         if (b16)
-            NSF_GT(gemm_tc(W, n, W, view(P16(L.Wb[l]), W, 1, 1), view(P16(L.H16[l - 1]), W, 1, 1),
-                           0, bias_elu(l), 1, status, s));
+            NSF_GT(layer_tc(n, W, W, view(P16(L.H16[l - 1]), W, 1, 1), view(P16(L.Wb[l]), W, 1, 1),
+                            bias_elu(l), status, s));
         else
             NSF_GT(gemm_simt(W, n, W, view(F.Wt[l], 1, W, 0), view(P(L.H[l - 1]), W, 1, 0),
                              bias_elu(l), 1, s));
@@ -384,10 +403,20 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     auto boff = [&](int l) { return goff[l] + (size_t)(l == 0 ? K0 : W) * W; };
     // delta_{D-1}(c, p) = sum_a Wout[a][c] dout(a, p) * ELU'(A_{D-1}(c, p)), db_{D-1}
     int pair = 0;                       // the hi / lo buffers of dcur
-    NSF_GT(gemm_simt(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
-                     elu_grad(dcur, D - 1, pair), 1, s));
-    NSF_GT(thin_outer(1, W, n, ones, view(dcur, 1, W, 0), slab, ks_thin, grad_w + boff(D - 1),
-                      false, s));
+    if (b16) {
+        // the FP32 cotangent is read only at the input layer (D - 1 = 0); the
+        // bias gradient comes with the weight gradient of layer D - 1, or (D = 1)
+        // from this kernel's column sums
+        NSF_GT(thin_k(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
+                      elu_grad(D - 1 == 0 ? dcur : nullptr, D - 1, pair,
+                               D - 1 == 0 ? slab : nullptr), s));
+        if (D - 1 == 0) NSF_GT(reduce_slabs(slab, thin_k_parts(n), W, grad_w + boff(0), s));
+    } else {
+        NSF_GT(gemm_simt(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
+                         elu_grad(dcur, D - 1, pair), 1, s));
+        NSF_GT(thin_outer(1, W, n, ones, view(dcur, 1, W, 0), slab, ks_thin,
+                          grad_w + boff(D - 1), false, s));
+    }
     for (int l = D - 1; l >= 1; --l) {
         // dW_l[o][c] = sum_p delta_l(o, p) H_{l-1}(c, p); BF16 fields: the cotangent
         // as its hi / lo pairs, both operands with contiguous rows
@@ -395,7 +424,7 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
             MatView dpair = view(P16(L.dh[pair]), 1, W, 1);
             dpair.lo = P16(L.dl[pair]);
             NSF_GT(summed(W, W, dpair, view(P16(L.H16[l - 1]), 1, W, 1), true, 1,
-                          grad_w + goff[l]));
+                          grad_w + goff[l], grad_w + boff(l)));
         } else {
             NSF_GT(summed(W, W, view(dcur, 1, W, 0), view(P(L.H[l - 1]), 1, W, 0), false, 0,
                           grad_w + goff[l]));
@@ -406,11 +435,15 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
         if (b16) {
             MatView dpair = view(P16(L.dh[pair]), W, 1, 1);
             dpair.lo = P16(L.dl[pair]);
-            // the FP32 cotangent is read only at the input layer (l - 1 = 0)
-            NSF_GT(gemm_tc(W, n, W, view(P16(L.WTb[l]), W, 1, 1), dpair, 2,
-                           elu_grad(l - 1 == 0 ? dnext : nullptr, l - 1, pair ^ 1, slab), 1,
-                           status, s));
-            NSF_GT(reduce_slabs(slab, 2 * ((n + 127) / 128), W, grad_w + boff(l - 1), s));
+            // the FP32 cotangent, and the column sums for the bias gradient, only
+            // at the input layer (l - 1 = 0): the other biases come with the
+            // weight gradients
+            const bool first = l - 1 == 0;
+            NSF_GT(layer_tc(n, W, W, dpair, view(P16(L.WTb[l]), W, 1, 1),
+                            elu_grad(first ? dnext : nullptr, l - 1, pair ^ 1,
+                                     first ? slab : nullptr),
+                            status, s));
+            if (first) NSF_GT(reduce_slabs(slab, layer_tc_parts(n, W), W, grad_w + boff(0), s));
         } else {
             NSF_GT(gemm_simt(W, n, W, view(F.Wt[l], W, 1, 0), view(dcur, W, 1, 0),
                              elu_grad(dnext, l - 1, pair ^ 1), 1, s));
