@@ -424,7 +424,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
 // always has the same tn and keeps those 128 rows of Wt in shared memory for
 // the whole launch (ceil(K / 64) K-atoms of 16 KB); only X streams through
 // the stage ring (the CTAs of one point tile fetch it at the same time: one
-// HBM read).  TMEM: two 128 x 128 FP32 accumulators.  Roles as in k_gemm_tc,
+// HBM read).  TMEM: four 128 x 128 FP32 accumulators, so the products run up
+// to three units ahead of the epilogue.  Roles as in k_gemm_tc,
 // with 16 epilogue warps: warp w holds points 32 (w % 4) .. + 31 (TMEM lanes)
 // and channels 32 ((w - 2) / 4) .. + 31 of the unit, one point per lane.
 // Rows of an [p][c] array are 2 W bytes apart, so a lane's own row is a poor
@@ -434,6 +435,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtens
 // instruction.
 constexpr int kLP = 128, kLN = 128;
 constexpr int kLStagesMax = 8, kLEpiWarps = 16, kLThreads = 32 * (2 + kLEpiWarps);
+constexpr int kLAcc = 4;            // TMEM accumulators (all 512 columns)
 constexpr int kLRow = 80, kLStaging = 32 * kLRow;   // staging block of one warp
 struct LayerShape {
     int n, W, K, tiles_n, units, stages;
@@ -445,7 +447,7 @@ __host__ __device__ inline int layer_stage_bytes(bool split) { return (split ? 2
 // 1024 alignment slack
 __host__ __device__ inline int layer_smem_bytes(int K, bool split, int stages) {
     return layer_katoms(K) * kLN * 128 + stages * layer_stage_bytes(split) +
-           kLEpiWarps * kLStaging + kLN * 4 + (2 * kLStagesMax + 6) * 8 + 16 + 1024;
+           kLEpiWarps * kLStaging + kLN * 4 + (2 * kLStagesMax + 2 * kLAcc + 2) * 8 + 16 + 1024;
 }
 
 // Sum over the warp's lanes of each of 32 values, lane l ending with the sum
@@ -538,8 +540,8 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
     uint8_t *staging = base + katoms * kLN * 128 + S * SB;
     float *sbias = reinterpret_cast<float *>(staging + kLEpiWarps * kLStaging);
     uint64_t *full = reinterpret_cast<uint64_t *>(sbias + kLN);
-    uint64_t *empty = full + kLStagesMax, *tfull = empty + kLStagesMax, *tempty = tfull + 2;
-    uint64_t *wbar = tempty + 2, *done = wbar + 1;
+    uint64_t *empty = full + kLStagesMax, *tfull = empty + kLStagesMax, *tempty = tfull + kLAcc;
+    uint64_t *wbar = tempty + kLAcc, *done = wbar + 1;
     uint32_t *holder = reinterpret_cast<uint32_t *>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -547,7 +549,7 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kLAcc; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], kLEpiWarps);
         }
@@ -558,7 +560,7 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
     if (EPI == kEpiBiasElu)
         for (int c = threadIdx.x; c < kLN; c += kLThreads)
             sbias[c] = tn * kLN + c < g.W ? e.bias[tn * kLN + c] : 0.f;
-    if (warp == 1) tmem_alloc(holder, 2 * kLN);
+    if (warp == 1) tmem_alloc(holder, kLAcc * kLN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -599,8 +601,8 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
             uint32_t ph = 0;
             bool ok = mbar_wait(wbar, 0);
             for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
-                const int acc = it & 1;
-                if (!mbar_wait(&tempty[acc], ((it >> 1) & 1) ^ 1)) { ok = false; break; }
+                const int acc = it % kLAcc;
+                if (!mbar_wait(&tempty[acc], ((it / kLAcc) & 1) ^ 1)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * kLN);
                 for (int c = 0; c < katoms; ++c) {
@@ -646,8 +648,8 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
                                 : make_uint4(0u, 0u, 0u, 0u);
                 }
             }
-            const int acc = it & 1;
-            if (!mbar_wait(&tfull[acc], (it >> 1) & 1)) {
+            const int acc = it % kLAcc;
+            if (!mbar_wait(&tfull[acc], (it / kLAcc) & 1)) {
                 set_status(status, NSF_ERR_ITER_CAP);
                 break;
             }
@@ -657,7 +659,7 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
             tmem_wait_ld();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);   // free for the unit after next
+            if (lane == 0) mbar_arrive(&tempty[acc]);   // free for a later unit
             ++it;
             if (EPI == kEpiBiasElu) {
                 uint32_t code[16], hb[16];
@@ -722,7 +724,7 @@ k_layer_tc(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUten
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * kLN);
+        tmem_dealloc(tmem, kLAcc * kLN);
     }
 }
 
@@ -772,10 +774,12 @@ int slice_len(int K, int slices, int multiple) {
 // EluGrad epilogues of the BF16 path.  M % 4 == 0: thread (m4, point)
 // computes rows 4 m4 .. 4 m4 + 3 of one column, so every store is a vector
 // (8 bytes of codes or bf16, 16 bytes of float).  A sits in shared memory as
-// [k][m]; B's K values of a point are read by all the point's threads (one
-// broadcast).  EluGrad's colsum: each CTA's sums of out over its columns,
-// colsum[blockIdx.x * M + m], in a fixed order.
-constexpr int kThinKMax = 20, kTkThreads = 256, kTkPoints = 64;
+// [k][m] and the CTA's columns of B as [n][k] (one coalesced pass).
+// EluGrad's partial sums, each CTA's in a fixed order over its columns:
+// colsum[blockIdx.x M + m] = sum_n out(m, n) (a bias gradient) and, with
+// e.hin (bf16 H at [n ld + m]), outer[(blockIdx.x K + k) M + m] =
+// sum_n B(n, k) H(n, m) (the output layer's weight gradient).
+constexpr int kThinKMax = 20, kTkThreads = 256, kTkPoints = 128;
 
 __device__ __forceinline__ uint2 pack_codes4(const float *g) {
     return make_uint2((unsigned)dact_code(g[0]) | ((unsigned)dact_code(g[1]) << 16),
@@ -784,47 +788,77 @@ __device__ __forceinline__ uint2 pack_codes4(const float *g) {
 __device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
     return make_uint2(pack_bf16x2(a, b), pack_bf16x2(c, d));
 }
+__host__ __device__ inline int thin_k_nk(int K) { return (K + 3) / 4 * 4; }
+__host__ __device__ inline size_t thin_k_smem(int M, int K) {
+    const int ppass = kTkThreads / (M / 4);
+    return sizeof(float) * ((size_t)kTkPoints * thin_k_nk(K) + (size_t)ppass * M);
+}
 
-template <int EPI>
+template <int EPI, int NK>
 __global__ void __launch_bounds__(kTkThreads)
 k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilogue e) {
     extern __shared__ float tk_smem[];
-    float *As = tk_smem;                          // [K][M]
+    float *Bs = tk_smem;                          // [kTkPoints][NK], zero past K
+    float *part = Bs + kTkPoints * NK;            // [ppass][M]
     const int q = M / 4, ppass = kTkThreads / q;  // threads per column, columns per pass
-    for (int t = threadIdx.x; t < K * M; t += kTkThreads) As[t] = view_at(A, t % M, t / M);
-    __syncthreads();
+    const int p_beg = blockIdx.x * kTkPoints, np = min(kTkPoints, N - p_beg);
+    for (int t = threadIdx.x; t < np * NK; t += kTkThreads)
+        Bs[t] = t % NK < K ? view_at(B, p_beg + t / NK, t % NK) : 0.f;
     const int pofs = threadIdx.x / q, m = 4 * (threadIdx.x % q);
     const bool active = pofs < ppass;
+    // this thread's rows of A, kept in registers for all its columns
+    float a[NK][4];
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[k][u] = (active && k < K) ? view_at(A, m + u, k) : 0.f;
     float bias[4] = {0.f, 0.f, 0.f, 0.f};
     if (EPI == kEpiBiasElu && active)
 #pragma unroll
         for (int u = 0; u < 4; ++u) bias[u] = e.bias[m + u];
+    __syncthreads();
     float cs[4] = {0.f, 0.f, 0.f, 0.f};
-    const int p_end = min(N, (blockIdx.x + 1) * kTkPoints);
+    constexpr int NO = EPI == kEpiEluGrad ? NK : 1;    // outer-product rows (K <= NK)
+    float ot[NO][4];
+#pragma unroll
+    for (int k = 0; k < NO; ++k)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ot[k][u] = 0.f;
+    const bool outer = EPI == kEpiEluGrad && e.hin != nullptr;
+    // EluGrad: the next column's codes (and H) are loaded one column ahead
+    uint2 cn = make_uint2(0u, 0u), hn = make_uint2(0u, 0u);
+    auto fetch = [&](int pl) {
+        const size_t i = (size_t)(p_beg + pl) * e.ld + m;
+        cn = *reinterpret_cast<const uint2 *>(e.dact + i);
+        if (outer) hn = *reinterpret_cast<const uint2 *>(e.hin + i);
+    };
+    if (EPI == kEpiEluGrad && active && pofs < np) fetch(pofs);
     if (active)
-        for (int p = blockIdx.x * kTkPoints + pofs; p < p_end; p += ppass) {
+        for (int pl = pofs; pl < np; pl += ppass) {
+            const uint2 c = cn, hv = hn;
+            if (EPI == kEpiEluGrad && pl + ppass < np) fetch(pl + ppass);
+            float b[NK];
+#pragma unroll
+            for (int k4 = 0; k4 < NK; k4 += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(Bs + pl * NK + k4);
+                b[k4] = v.x; b[k4 + 1] = v.y; b[k4 + 2] = v.z; b[k4 + 3] = v.w;
+            }
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < kThinKMax; ++k) {
-                if (k >= K) break;
-                const float b = view_at(B, p, k);
-                const float4 a = *reinterpret_cast<const float4 *>(As + k * M + m);
-                acc[0] = fmaf(a.x, b, acc[0]);
-                acc[1] = fmaf(a.y, b, acc[1]);
-                acc[2] = fmaf(a.z, b, acc[2]);
-                acc[3] = fmaf(a.w, b, acc[3]);
-            }
-            const size_t i = (size_t)p * e.ld + m;
-            if (EPI == kEpiBiasElu) {
-                float h[4], g[4];
+            for (int k = 0; k < NK; ++k)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) h[u] = elu_bf16_path(acc[u] + bias[u], g[u]);
-                *reinterpret_cast<uint2 *>(e.dact + i) = pack_codes4(g);
-                *reinterpret_cast<uint2 *>(e.h16 + i) = pack_bf16x4(h[0], h[1], h[2], h[3]);
+                for (int u = 0; u < 4; ++u) acc[u] = fmaf(a[k][u], b[k], acc[u]);
+            const size_t i = (size_t)(p_beg + pl) * e.ld + m;
+            if (EPI == kEpiBiasElu) {
+                uint32_t c0, c1, h0, h1;
+                elu2_codes(make_float2(acc[0], acc[1]), make_float2(bias[0], bias[1]), c0, h0);
+                elu2_codes(make_float2(acc[2], acc[3]), make_float2(bias[2], bias[3]), c1, h1);
+                *reinterpret_cast<uint2 *>(e.dact + i) = make_uint2(c0, c1);
+                *reinterpret_cast<uint2 *>(e.h16 + i) = make_uint2(h0, h1);
             } else {
-                const uint2 c = *reinterpret_cast<const uint2 *>(e.dact + i);
-                const float o[4] = {acc[0] * dact_value(c.x & 0xFFFFu), acc[1] * dact_value(c.x >> 16),
-                                    acc[2] * dact_value(c.y & 0xFFFFu), acc[3] * dact_value(c.y >> 16)};
+                const float2 o01 = mul_codes2(make_float2(acc[0], acc[1]), c.x);
+                const float2 o23 = mul_codes2(make_float2(acc[2], acc[3]), c.y);
+                const float o[4] = {o01.x, o01.y, o23.x, o23.y};
                 if (e.out) *reinterpret_cast<float4 *>(e.out + i) = make_float4(o[0], o[1], o[2], o[3]);
                 float hi[4], lo[4];
 #pragma unroll
@@ -835,19 +869,168 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
                 }
                 *reinterpret_cast<uint2 *>(e.dhi + i) = pack_bf16x4(hi[0], hi[1], hi[2], hi[3]);
                 *reinterpret_cast<uint2 *>(e.dlo + i) = pack_bf16x4(lo[0], lo[1], lo[2], lo[3]);
+                if (outer) {
+                    const float h[4] = {__uint_as_float(hv.x << 16), __uint_as_float(hv.x & 0xFFFF0000u),
+                                        __uint_as_float(hv.y << 16), __uint_as_float(hv.y & 0xFFFF0000u)};
+#pragma unroll
+                    for (int k = 0; k < NO; ++k)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) ot[k][u] = fmaf(b[k], h[u], ot[k][u]);
+                }
             }
         }
-    if (EPI == kEpiEluGrad && e.colsum) {
-        float *part = As + K * M;                 // [ppass][M]
+    if (EPI != kEpiEluGrad) return;
+    // the CTA's partial sums over its columns, in pofs order
+    auto flush = [&](const float (&v)[4], float *dst) {
+        __syncthreads();
         if (active)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) part[pofs * M + m + u] = cs[u];
+            for (int u = 0; u < 4; ++u) part[pofs * M + m + u] = v[u];
         __syncthreads();
         for (int mm = threadIdx.x; mm < M; mm += kTkThreads) {
             float t = 0.f;
             for (int u = 0; u < ppass; ++u) t += part[u * M + mm];
-            e.colsum[(size_t)blockIdx.x * M + mm] = t;
+            dst[mm] = t;
         }
+    };
+    if (e.colsum) flush(cs, e.colsum + (size_t)blockIdx.x * M);
+    if (outer)
+#pragma unroll
+        for (int k = 0; k < NO; ++k)
+            if (k < K) flush(ot[k], e.outer + ((size_t)blockIdx.x * K + k) * M);
+}
+
+// ------------------------------------------------ input-layer backward ----
+// With delta_0(p, o) (o < W) the cotangent of the input layer's
+// pre-activation and inp(p, j) (j < K0) its inputs:
+//   dinp(p, j) = sum_o W0[o][j] delta_0(p, o)      (toward the latent codes)
+//   dW0[o][j]  = sum_p delta_0(p, o) inp(p, j),  db0[o] = sum_p delta_0(p, o).
+// One pass over delta_0 (the bf16 hi + lo pairs or an FP32 array): a CTA
+// stages 32 points x W of it and their inputs in shared memory; thread
+// (point t / 8, channel group t % 8) sums its group's channels for dinp (then
+// a fixed xor-shuffle sum over the 8 groups), and thread t = o accumulates
+// dW0 / db0 of channel o over the points of all the CTA's tiles, in order,
+// written once as the CTA's slab in the gradient layout [W0 (W x K0) | b0].
+constexpr int kIbPoints = 32, kIbThreads = 256, kIbRow = 8 * 33 + 1, kIbMaxGrid = 320;
+__host__ __device__ inline int ib_k0p(int K0) { return (K0 + 3) / 4 * 4; }
+__host__ __device__ inline size_t ib_smem(int K0) {
+    const int k0p = ib_k0p(K0);
+    return sizeof(float) * ((size_t)kIbPoints * kIbRow + kIbPoints * k0p + 8 * (32 * k0p + 4));
+}
+
+template <int K0P>
+__global__ void __launch_bounds__(kIbThreads)
+k_input_bwd(int n, int W, int K0, const __nv_bfloat16 *__restrict__ dhi,
+            const __nv_bfloat16 *__restrict__ dlo, const float *__restrict__ d32, long long ld,
+            const float *__restrict__ inp, const float *__restrict__ W0, float *dinp, float *slab) {
+    extern __shared__ float ib[];
+    constexpr int k0p = K0P;
+    float *sd = ib, *sx = sd + kIbPoints * kIbRow, *sw = sx + kIbPoints * k0p;
+    const int tid = threadIdx.x;
+    // W0 [o][j] as [group o / 32][(o % 32) k0p + j] + 4 per group (the groups'
+    // rows in different banks)
+    for (int i = tid; i < W * k0p; i += kIbThreads) {
+        const int o = i / k0p, j = i % k0p;
+        sw[(o >> 5) * (32 * k0p + 4) + (o & 31) * k0p + j] = j < K0 ? W0[(size_t)o * K0 + j] : 0.f;
+    }
+    float acc[K0P], accb = 0.f;
+#pragma unroll
+    for (int j = 0; j < K0P; ++j) acc[j] = 0.f;
+    const int o = tid, pp = tid >> 3, og = tid & 7;
+    const int ntiles = (n + kIbPoints - 1) / kIbPoints, w8 = W / 8;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int p0 = tile * kIbPoints;
+        __syncthreads();                 // the previous tile is no longer read
+        for (int q = tid; q < kIbPoints * w8; q += kIbThreads) {
+            const int pt = q / w8, c8 = (q % w8) * 8, p = p0 + pt;
+            float v[8];
+            if (p < n) {
+                if (d32) {
+                    const float4 x = *reinterpret_cast<const float4 *>(d32 + (size_t)p * ld + c8);
+                    const float4 y = *reinterpret_cast<const float4 *>(d32 + (size_t)p * ld + c8 + 4);
+                    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+                    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+                } else {
+                    const uint4 h = __ldg(reinterpret_cast<const uint4 *>(dhi + (size_t)p * ld + c8));
+                    const uint4 l = __ldg(reinterpret_cast<const uint4 *>(dlo + (size_t)p * ld + c8));
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        v[2 * t] = __uint_as_float(hw[t] << 16) + __uint_as_float(lw[t] << 16);
+                        v[2 * t + 1] = __uint_as_float(hw[t] & 0xFFFF0000u) +
+                                       __uint_as_float(lw[t] & 0xFFFF0000u);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) v[t] = 0.f;
+            }
+            float *dst = sd + pt * kIbRow + (c8 >> 5) * 33 + (c8 & 31);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) dst[t] = v[t];
+        }
+        for (int q = tid; q < kIbPoints * K0; q += kIbThreads) {
+            const int pt = q / K0, j = q % K0, p = p0 + pt;
+            sx[pt * k0p + j] = p < n ? inp[(size_t)p * K0 + j] : 0.f;
+        }
+        for (int q = tid; q < kIbPoints * (k0p - K0); q += kIbThreads)
+            sx[(q / (k0p - K0)) * k0p + K0 + q % (k0p - K0)] = 0.f;
+        __syncthreads();
+        {
+            // this group's channels (W % 32 == 0: a group is whole or absent), then a
+            // fixed-order sum over the 8 groups that every lane takes part in
+            float sj[K0P];
+#pragma unroll
+            for (int j = 0; j < K0P; ++j) sj[j] = 0.f;
+            if (og * 32 < W) {
+                const float *dp = sd + pp * kIbRow + og * 33;
+                const float *wp = sw + og * (32 * k0p + 4);
+#pragma unroll 8
+                for (int oi = 0; oi < 32; ++oi) {
+                    const float d = dp[oi];
+#pragma unroll
+                    for (int j4 = 0; j4 < K0P; j4 += 4) {
+                        const float4 w = *reinterpret_cast<const float4 *>(wp + oi * k0p + j4);
+                        sj[j4] = fmaf(w.x, d, sj[j4]);
+                        sj[j4 + 1] = fmaf(w.y, d, sj[j4 + 1]);
+                        sj[j4 + 2] = fmaf(w.z, d, sj[j4 + 2]);
+                        sj[j4 + 3] = fmaf(w.w, d, sj[j4 + 3]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1)
+#pragma unroll
+                for (int j = 0; j < K0P; ++j) sj[j] += __shfl_xor_sync(0xffffffffu, sj[j], off);
+            const int p = p0 + pp;
+            if (p < n)
+#pragma unroll
+                for (int j = 0; j < K0P; ++j)
+                    if (j < K0 && (j & 7) == og) dinp[(size_t)p * K0 + j] = sj[j];
+        }
+        if (o < W) {
+            const float *dcol = sd + (o >> 5) * 33 + (o & 31);
+#pragma unroll 8
+            for (int pt = 0; pt < kIbPoints; ++pt) {
+                const float d = dcol[pt * kIbRow];
+                accb += d;
+#pragma unroll
+                for (int j4 = 0; j4 < K0P; j4 += 4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(sx + pt * k0p + j4);
+                    acc[j4] = fmaf(d, x.x, acc[j4]);
+                    acc[j4 + 1] = fmaf(d, x.y, acc[j4 + 1]);
+                    acc[j4 + 2] = fmaf(d, x.z, acc[j4 + 2]);
+                    acc[j4 + 3] = fmaf(d, x.w, acc[j4 + 3]);
+                }
+            }
+        }
+    }
+    if (o < W) {
+        float *mine = slab + (size_t)blockIdx.x * ((size_t)W * K0 + W);
+#pragma unroll
+        for (int j = 0; j < K0P; ++j)
+            if (j < K0) mine[(size_t)o * K0 + j] = acc[j];
+        mine[(size_t)W * K0 + o] = accb;
     }
 }
 
@@ -1163,6 +1346,40 @@ cudaError_t thin_m(int M, int N, int K, const MatView &A, const MatView &B, floa
 
 int thin_k_parts(int N) { return (N + kTkPoints - 1) / kTkPoints; }
 
+int input_bwd_parts(int n) {
+    const int tiles = (n + kIbPoints - 1) / kIbPoints;
+    int grid = 2 * sm_count();
+    if (grid > kIbMaxGrid) grid = kIbMaxGrid;
+    return tiles < grid ? tiles : grid;
+}
+
+cudaError_t input_bwd(int n, int W, int K0, const __nv_bfloat16 *dhi, const __nv_bfloat16 *dlo,
+                      const float *d32, long long ld, const float *inp, const float *W0,
+                      float *dinp, float *slab, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (W % 32 || W > NSF_MAX_WIDTH || K0 < 1 || K0 > kThinKMax || ld % 8) return cudaErrorInvalidValue;
+    if (!d32 && (!dhi || !dlo)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_input_bwd<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ib_smem(4));
+        cudaFuncSetAttribute(k_input_bwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ib_smem(8));
+        cudaFuncSetAttribute(k_input_bwd<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ib_smem(12));
+        cudaFuncSetAttribute(k_input_bwd<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ib_smem(16));
+        cudaFuncSetAttribute(k_input_bwd<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ib_smem(20));
+        attr = true;
+    }
+    const int grid = input_bwd_parts(n), k0p = ib_k0p(K0);
+    const size_t smem = ib_smem(K0);
+#define NSF_IB(P_) k_input_bwd<P_><<<grid, kIbThreads, smem, s>>>(n, W, K0, dhi, dlo, d32, ld, inp, W0, dinp, slab)
+    if (k0p == 4) NSF_IB(4);
+    else if (k0p == 8) NSF_IB(8);
+    else if (k0p == 12) NSF_IB(12);
+    else if (k0p == 16) NSF_IB(16);
+    else NSF_IB(20);
+#undef NSF_IB
+    return cudaGetLastError();
+}
+
 cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
                    const GemmEpilogue &e, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
@@ -1174,15 +1391,27 @@ cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
     if (e.mode == kEpiEluGrad &&
         (!e.dhi || !e.dlo || !al(e.dhi, 8) || !al(e.dlo, 8) || (e.out && !al(e.out, 16))))
         return cudaErrorInvalidValue;
-    const int ppass = kTkThreads / (M / 4);
-    const size_t smem = (size_t)(K + ppass) * M * sizeof(float);
-    const int grid = thin_k_parts(N);
-    if (e.mode == kEpiBiasElu)
-        k_thin_k<kEpiBiasElu><<<grid, kTkThreads, smem, s>>>(M, N, K, A, B, e);
-    else if (e.mode == kEpiEluGrad)
-        k_thin_k<kEpiEluGrad><<<grid, kTkThreads, smem, s>>>(M, N, K, A, B, e);
-    else
+    if (e.mode == kEpiEluGrad && e.hin && (K > kMaxOut || !e.outer || !al(e.hin, 8)))
         return cudaErrorInvalidValue;
+    const size_t smem = thin_k_smem(M, K);
+    const int grid = thin_k_parts(N), nk = thin_k_nk(K);
+#define NSF_TK(EPI_, NK_) k_thin_k<EPI_, NK_><<<grid, kTkThreads, smem, s>>>(M, N, K, A, B, e)
+    if (e.mode == kEpiBiasElu) {
+        if (nk == 4) NSF_TK(kEpiBiasElu, 4);
+        else if (nk == 8) NSF_TK(kEpiBiasElu, 8);
+        else if (nk == 12) NSF_TK(kEpiBiasElu, 12);
+        else if (nk == 16) NSF_TK(kEpiBiasElu, 16);
+        else NSF_TK(kEpiBiasElu, 20);
+    } else if (e.mode == kEpiEluGrad) {
+        if (nk == 4) NSF_TK(kEpiEluGrad, 4);
+        else if (nk == 8) NSF_TK(kEpiEluGrad, 8);
+        else if (nk == 12) NSF_TK(kEpiEluGrad, 12);
+        else if (nk == 16) NSF_TK(kEpiEluGrad, 16);
+        else NSF_TK(kEpiEluGrad, 20);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef NSF_TK
     return cudaGetLastError();
 }
 

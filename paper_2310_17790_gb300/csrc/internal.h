@@ -202,6 +202,8 @@ struct GemmEpilogue {
     float *colsum;         // (may be null) partial sums for a bias gradient: see the
                            // products that take it
     __nv_bfloat16 *dhi, *dlo;   // EluGrad (may be null): out as hi = bf16(v), lo = bf16(v - hi)
+    const __nv_bfloat16 *hin;   // thin_k EluGrad (may be null): H for the outer-product sums
+    float *outer;          //   written per CTA (see thin_k)
     unsigned short *dact;  // BF16 path (replaces pre / apre): ELU'(pre) as the 16-bit code
                            // rint(ELU' 2^15) at [n ld + m]; BiasElu then writes only dact
                            // and h16 (ELU on the special-function unit)
@@ -241,9 +243,20 @@ int layer_tc_parts(int n, int W);
 // backward product on the BF16 path (epilogue BiasElu or EluGrad with dact;
 // M % 4 == 0, ld % 4 == 0).  EluGrad's colsum gets thin_k_parts(N) partial
 // sums per row: colsum[part * M + m].
+// With e.hin (EluGrad, K <= 16) also outer[(part K + k) M + m] = sum over the
+// part's columns of B(n, k) hin[n ld + m].
 cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
                    const GemmEpilogue &e, cudaStream_t s);
 int thin_k_parts(int N);
+// The input layer's backward pass on the BF16 path, one read of delta_0 (bf16
+// hi + lo pairs, or d32 in FP32) at [p ld + o]: dinp[p K0 + j] = sum_o
+// W0[o K0 + j] delta_0(p, o), and input_bwd_parts(n) slabs of W K0 + W
+// partial sums in the gradient layout of layer 0 (dW0[o K0 + j] = sum_p
+// delta_0(p, o) inp[p K0 + j], then db0[o] = sum_p delta_0(p, o)).
+cudaError_t input_bwd(int n, int W, int K0, const __nv_bfloat16 *dhi, const __nv_bfloat16 *dlo,
+                      const float *d32, long long ld, const float *inp, const float *W0,
+                      float *dinp, float *slab, cudaStream_t s);
+int input_bwd_parts(int n);
 // out[i] = sum over z < slices of slab[z * count + i] (fixed order); the slab
 // may be overwritten.
 cudaError_t reduce_slabs(float *slab, int slices, long long count, float *out, cudaStream_t s);

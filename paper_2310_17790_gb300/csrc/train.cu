@@ -134,14 +134,19 @@ __global__ void k_scatter_dz(const float *__restrict__ dinp, const int *__restri
 // bf16 copies of a hidden layer's weights from its transposed FP32 copy
 // Wt [in][out]: Wb [out][in] and WTb [in][out] (the values are bf16 already
 // for a BF16 field).
-__global__ void k_weights_bf16(const float *__restrict__ Wt, int W, __nv_bfloat16 *Wb,
-                               __nv_bfloat16 *WTb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// The bf16 copies of the hidden layers' weights, both orientations, for
+// layers 1 .. D - 1 in one launch (blockIdx.y = l - 1).
+struct WeightCopies {
+    const float *Wt[kMaxDepth];
+    __nv_bfloat16 *Wb[kMaxDepth], *WTb[kMaxDepth];
+};
+__global__ void k_weights_bf16(WeightCopies wc, int W) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, l = blockIdx.y + 1;
     if (i >= W * W) return;
     const int c = i / W, o = i % W;
-    const __nv_bfloat16 v = __float2bfloat16_rn(Wt[i]);
-    WTb[i] = v;
-    Wb[(size_t)o * W + c] = v;
+    const __nv_bfloat16 v = __float2bfloat16_rn(wc.Wt[l][i]);
+    wc.WTb[l][i] = v;
+    wc.Wb[l][(size_t)o * W + c] = v;
 }
 
 // Adam (Kingma and Ba 2014), bias-corrected, in place.
@@ -281,8 +286,9 @@ TrainLayout train_layout(int r, int W, int D, int od, int n) {
     size_t slab = (size_t)kMaxSlices * W * (W + 1);     // weight and bias gradient slabs
     slab = slab > (size_t)kMaxThinSlices * thin_a * W ? slab : (size_t)kMaxThinSlices * thin_a * W;
     const size_t loss_parts = (nn + kT - 1) / kT * (size_t)od;
-    // bias column sums: at most 4 per 128 points (layer_tc) or 1 per 64 (thin_k)
-    const size_t col_parts = (4 * ((nn + 127) / 128) + (nn + 63) / 64) * (size_t)W;
+    // per-CTA partial sums: bias columns and the output layer's outer products
+    // (thin_k, one part per 128 points), the input layer's slabs (at most 320)
+    const size_t col_parts = ((nn + 127) / 128) * (size_t)(od + 1) * W + 320 * (size_t)W * (4 + r);
     slab = slab > loss_parts ? slab : loss_parts;
     slab = slab > col_parts ? slab : col_parts;
     L.slab = take(slab * 4);
@@ -364,10 +370,15 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     else
         NSF_GT(gemm_simt(W, n, K0, view(F.W0, K0, 1, 0), view(P(L.inp), K0, 1, 0), bias_elu(0),
                          1, s));
-    if (b16)
-        for (int l = 1; l < D; ++l)
-            k_weights_bf16<<<blocks((long long)W * W), kT, 0, s>>>(F.Wt[l], W, P16(L.Wb[l]),
-                                                                  P16(L.WTb[l]));
+    if (b16 && D > 1) {
+        WeightCopies wc{};
+        for (int l = 1; l < D; ++l) {
+            wc.Wt[l] = F.Wt[l];
+            wc.Wb[l] = P16(L.Wb[l]);
+            wc.WTb[l] = P16(L.WTb[l]);
+        }
+        k_weights_bf16<<<dim3(blocks((long long)W * W), D - 1), kT, 0, s>>>(wc, W);
+    }
     for (int l = 1; l < D; ++l) {
         // A_l(o, p) = sum_c W_l[o][c] H_{l-1}(c, p), W_l[o][c] = Wt[l][c W + o]
         if (b16)
@@ -396,21 +407,23 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     // output layer: dbout[a] = sum_p dout(a, p) from k_loss's per-CTA sums,
     // dWout[a][c] = sum_p dout(a, p) H_{D-1}(c, p)
     NSF_GT(reduce_slabs(slab, blocks(n), od, grad_w + goff[D] + (size_t)od * W, s));
-    NSF_GT(thin_outer(od, W, n, view(P(L.dout), 1, od, 0), Hlast_cols, slab, ks_thin,
-                      grad_w + goff[D], false, s));
+    if (!b16)
+        NSF_GT(thin_outer(od, W, n, view(P(L.dout), 1, od, 0), Hlast_cols, slab, ks_thin,
+                          grad_w + goff[D], false, s));
     float *dcur = P(L.d1), *dnext = P(L.d2);
     // flat offset of layer l's bias gradient
     auto boff = [&](int l) { return goff[l] + (size_t)(l == 0 ? K0 : W) * W; };
     // delta_{D-1}(c, p) = sum_a Wout[a][c] dout(a, p) * ELU'(A_{D-1}(c, p)), db_{D-1}
     int pair = 0;                       // the hi / lo buffers of dcur
     if (b16) {
-        // the FP32 cotangent is read only at the input layer (D - 1 = 0); the
-        // bias gradient comes with the weight gradient of layer D - 1, or (D = 1)
-        // from this kernel's column sums
-        NSF_GT(thin_k(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
-                      elu_grad(D - 1 == 0 ? dcur : nullptr, D - 1, pair,
-                               D - 1 == 0 ? slab : nullptr), s));
-        if (D - 1 == 0) NSF_GT(reduce_slabs(slab, thin_k_parts(n), W, grad_w + boff(0), s));
+        // with the output layer's weight gradient dWout[a][c] = sum_p dout(a, p)
+        // H_{D-1}(p, c) from the same pass; the bias gradient of layer D - 1
+        // comes with its weight gradient (or, D = 1, with the input layer's)
+        GemmEpilogue e = elu_grad(nullptr, D - 1, pair);
+        e.hin = P16(L.H16[D - 1]);
+        e.outer = slab;
+        NSF_GT(thin_k(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0), e, s));
+        NSF_GT(reduce_slabs(slab, thin_k_parts(n), (long long)od * W, grad_w + goff[D], s));
     } else {
         NSF_GT(gemm_simt(W, n, od, view(F.Wout, 1, W, 0), view(P(L.dout), od, 1, 0),
                          elu_grad(dcur, D - 1, pair), 1, s));
@@ -435,15 +448,10 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
         if (b16) {
             MatView dpair = view(P16(L.dh[pair]), W, 1, 1);
             dpair.lo = P16(L.dl[pair]);
-            // the FP32 cotangent, and the column sums for the bias gradient, only
-            // at the input layer (l - 1 = 0): the other biases come with the
-            // weight gradients
-            const bool first = l - 1 == 0;
+            // (the bias gradients come with the weight gradients, layer 0's from
+            // the input layer's pass)
             NSF_GT(layer_tc(n, W, W, dpair, view(P16(L.WTb[l]), W, 1, 1),
-                            elu_grad(first ? dnext : nullptr, l - 1, pair ^ 1,
-                                     first ? slab : nullptr),
-                            status, s));
-            if (first) NSF_GT(reduce_slabs(slab, layer_tc_parts(n, W), W, grad_w + boff(0), s));
+                            elu_grad(nullptr, l - 1, pair ^ 1), status, s));
         } else {
             NSF_GT(gemm_simt(W, n, W, view(F.Wt[l], W, 1, 0), view(dcur, W, 1, 0),
                              elu_grad(dnext, l - 1, pair ^ 1), 1, s));
@@ -455,15 +463,20 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
         dnext = t;
         pair ^= 1;
     }
-    // input layer: dW_0[o][j] = sum_p delta_0(o, p) inp(j, p) (computed as [j][o],
-    // stored transposed)
-    const MatView d0 = view(dcur, 1, W, 0);
-    NSF_GT(thin_outer(K0, W, n, view(P(L.inp), 1, K0, 0), d0, slab, ks_thin, grad_w + goff[0],
-                      true, s));
+    // input layer: dW_0[o][j] = sum_p delta_0(o, p) inp(j, p), db_0 and
+    // dinp(j, p) = sum_o W0[o][j] delta_0(o, p)
+    if (b16) {
+        NSF_GT(input_bwd(n, W, K0, P16(L.dh[pair]), P16(L.dl[pair]), nullptr, W, P(L.inp), F.W0,
+                         P(L.dinp), slab, s));
+        NSF_GT(reduce_slabs(slab, input_bwd_parts(n), (long long)W * K0 + W, grad_w + goff[0], s));
+    } else {
+        NSF_GT(thin_outer(K0, W, n, view(P(L.inp), 1, K0, 0), view(dcur, 1, W, 0), slab, ks_thin,
+                          grad_w + goff[0], true, s));
+    }
     if (grad_z) {
         NSF_GT(cudaMemsetAsync(grad_z, 0, (size_t)n_codes * r * sizeof(float), s));
-        // dinp(j, p) = sum_o W0[o][j] delta_0(o, p)
-        NSF_GT(thin_m(K0, n, W, view(F.W0, 1, K0, 0), view(dcur, W, 1, 0), P(L.dinp), K0, s));
+        if (!b16)
+            NSF_GT(thin_m(K0, n, W, view(F.W0, 1, K0, 0), view(dcur, W, 1, 0), P(L.dinp), K0, s));
         k_scatter_dz<<<blocks(n) < 304 ? blocks(n) : 304, kT, 0, s>>>(P(L.dinp), code, n, r,
                                                                    n_codes, grad_z);
     }
