@@ -825,18 +825,34 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
 #pragma unroll
         for (int u = 0; u < 4; ++u) ot[k][u] = 0.f;
     const bool outer = EPI == kEpiEluGrad && e.hin != nullptr;
-    // EluGrad: the next column's codes (and H) are loaded one column ahead
-    uint2 cn = make_uint2(0u, 0u), hn = make_uint2(0u, 0u);
-    auto fetch = [&](int pl) {
+    // EluGrad: the codes (and H) of a column are loaded kAhead columns ahead,
+    // into a ring of registers
+    constexpr int kAhead = EPI == kEpiEluGrad ? 4 : 1;
+    uint2 cr[kAhead], hr[kAhead];
+#pragma unroll
+    for (int t = 0; t < kAhead; ++t) cr[t] = hr[t] = make_uint2(0u, 0u);
+    auto fetch = [&](int pl, int slot) {
+        if (pl >= np) return;
         const size_t i = (size_t)(p_beg + pl) * e.ld + m;
-        cn = *reinterpret_cast<const uint2 *>(e.dact + i);
-        if (outer) hn = *reinterpret_cast<const uint2 *>(e.hin + i);
+#pragma unroll
+        for (int t = 0; t < kAhead; ++t)
+            if (t == slot) {
+                cr[t] = *reinterpret_cast<const uint2 *>(e.dact + i);
+                if (outer) hr[t] = *reinterpret_cast<const uint2 *>(e.hin + i);
+            }
     };
-    if (EPI == kEpiEluGrad && active && pofs < np) fetch(pofs);
+    if (EPI == kEpiEluGrad && active)
+#pragma unroll
+        for (int t = 0; t < kAhead; ++t) fetch(pofs + t * ppass, t);
     if (active)
-        for (int pl = pofs; pl < np; pl += ppass) {
-            const uint2 c = cn, hv = hn;
-            if (EPI == kEpiEluGrad && pl + ppass < np) fetch(pl + ppass);
+#pragma unroll 4
+        for (int pl = pofs, it = 0; pl < np; pl += ppass, ++it) {
+            const int slot = it % kAhead;
+            uint2 c = make_uint2(0u, 0u), hv = make_uint2(0u, 0u);
+#pragma unroll
+            for (int t = 0; t < kAhead; ++t)
+                if (t == slot) { c = cr[t]; hv = hr[t]; }
+            if (EPI == kEpiEluGrad) fetch(pl + kAhead * ppass, slot);
             float b[NK];
 #pragma unroll
             for (int k4 = 0; k4 < NK; k4 += 4) {
@@ -1412,6 +1428,54 @@ cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
         return cudaErrorInvalidValue;
     }
 #undef NSF_TK
+    return cudaGetLastError();
+}
+
+// Weight and bias gradients of a hidden layer from the K-slices of the
+// weight-gradient product: slab[z][n][m] (z < slices, n < N, m < M) ->
+// out_w[m N + n] and bslab[z][m] -> out_b[m], each a fixed-order sum over z.
+// A CTA takes 32 consecutive slab entries (coalesced reads), 8 groups of
+// slices each, then a shared sum in group order; the CTAs past the M N / 32
+// of the weights do the same for the bias slab.
+__global__ void k_reduce_dw(const float *__restrict__ slab, const float *__restrict__ bslab,
+                            int slices, int M, int N, float *out_w, float *out_b) {
+    __shared__ float part[8][33];
+    const int ix = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const long long count = (long long)M * N, wblocks = (count + 31) / 32;
+    const bool bias = blockIdx.x >= wblocks;
+    const long long i = (bias ? blockIdx.x - wblocks : blockIdx.x) * 32 + ix;
+    const long long cnt = bias ? M : count;
+    const float *src = bias ? bslab : slab;
+    float s = 0.f;
+    if (i < cnt) {
+        int z = g;
+        for (; z + 24 < slices; z += 32) {
+            const float a = src[(size_t)z * cnt + i], b = src[(size_t)(z + 8) * cnt + i];
+            const float c = src[(size_t)(z + 16) * cnt + i], d = src[(size_t)(z + 24) * cnt + i];
+            s += a;
+            s += b;
+            s += c;
+            s += d;
+        }
+        for (; z < slices; z += 8) s += src[(size_t)z * cnt + i];
+    }
+    part[g][ix] = s;
+    __syncthreads();
+    if (g == 0 && i < cnt) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += part[q][ix];
+        if (bias) out_b[i] = t;
+        else out_w[(size_t)(i % M) * N + i / M] = t;
+    }
+}
+
+cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, int N,
+                      float *out_w, float *out_b, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const long long wblocks = ((long long)M * N + 31) / 32;
+    const int blocks = (int)wblocks + (out_b ? (M + 31) / 32 : 0);
+    k_reduce_dw<<<blocks, 256, 0, s>>>(slab, bslab, slices, M, N, out_w, out_b);
     return cudaGetLastError();
 }
 

@@ -260,6 +260,10 @@ int input_bwd_parts(int n);
 // out[i] = sum over z < slices of slab[z * count + i] (fixed order); the slab
 // may be overwritten.
 cudaError_t reduce_slabs(float *slab, int slices, long long count, float *out, cudaStream_t s);
+// A hidden layer's weight and bias gradients from the slabs of gemm_tc
+// (slab[z][n][m] -> out_w[m N + n], bslab[z][m] -> out_b[m], out_b may be null).
+cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, int N,
+                      float *out_w, float *out_b, cudaStream_t s);
 // The same sums transposed: slab[z][a][c] (count A C) -> out[c * A + a].
 cudaError_t reduce_slabs_t(const float *slab, int slices, int A, int C, float *out,
                            cudaStream_t s);

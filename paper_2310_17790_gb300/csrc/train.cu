@@ -331,8 +331,7 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
         cudaError_t err = tc ? gemm_tc(M, N, n, A, B, split, e, k, status, s)
                              : gemm_simt(M, N, n, A, B, e, k, s);
         if (err != cudaSuccess) return err;
-        if (bias_dst && (err = reduce_slabs(bslab, k, M, bias_dst, s)) != cudaSuccess) return err;
-        return reduce_slabs_t(slab, k, N, M, dst, s);   // slab [z][n][m] -> dst[m N + n]
+        return reduce_dw(slab, bslab, k, M, N, dst, bias_dst, s);   // [z][n][m] -> dst[m N + n]
     };
     auto bias_elu = [&](int l) {
         GemmEpilogue e = epi(kEpiBiasElu);
