@@ -354,9 +354,9 @@ def load_traffic(kernel):
         return None
     for line in open(path):
         f = [x.strip() for x in line.strip().strip("|").split("|")]
-        if len(f) >= 2 and f[0] == kernel:
-            try:
-                return float(f[1].replace(",", ""))
+        if len(f) >= 3 and f[0] == kernel:
+            try:       # read + write bytes
+                return float(f[1].replace(",", "")) + float(f[2].replace(",", ""))
             except ValueError:
                 return None
     return None
