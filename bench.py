@@ -590,7 +590,8 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
                 "frac": mpm_bytes / (st_ms[1] / 1e3) / 1e9 / peaks["hbm_gbs"],
                 "work": mpm_bytes, "touched_nodes": int(touched),
                 "note": "96 B per integration particle + 64 B per touched node + 36 B per "
-                        "sample particle; P2G adds into the grid with float4 atomics"},
+                        "sample particle; P2G sums each 4^3 block in a shared-memory tile "
+                        "(exact integers), one integer atomic per touched node and value"},
         "gauss_newton": {"kernel": "k_jac_batch", "bound": "tensor", "unit": "TFLOP/s",
                          "achieved": tf(fl_gn, st_ms[2]), "peak": pk,
                          "frac": tf(fl_gn, st_ms[2]) / pk, "work": fl_gn},
