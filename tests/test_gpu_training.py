@@ -6,10 +6,11 @@ update, and a short training run against the oracle's trajectory.
 
 Tolerances: FP32 fields 1e-5 on the loss and 1e-4 (norm-wise) on the
 gradients (FP32 accumulation of sums over up to 1,000 points); BF16 fields
-(bf16 operands in the forward products, the oracle's BF16 reading; TF32
-backward products) 2e-3 on the gradients: an activation whose FP32 and FP64
-pre-activations round to different bf16 values moves by one bf16 ulp, and a
-TF32 operand keeps 11 significant bits.
+(bf16 operands in the forward products, the oracle's BF16 reading; backward
+products with the cotangent split into bf16 hi + lo, ~16 significant bits;
+ELU' kept as a 16-bit fixed-point code, absolute error <= 2^-16) 2e-3 on the
+gradients: an activation whose FP32 and FP64 pre-activations round to
+different bf16 values moves by one bf16 ulp.
 """
 
 import numpy as np
