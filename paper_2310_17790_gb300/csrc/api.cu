@@ -919,6 +919,7 @@ WidthPlan plan_width(int W, int n, const nsf_latent_batch_item *items, bool with
 // shares for the smallest estimated makespan.
 struct GnPlan {
     std::vector<int> cw;
+    int batch_cw = 0;
     std::vector<GnBatchEntry> entries;
     std::vector<int> cta_entry;
     int nctas = 0;
@@ -950,10 +951,17 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
     std::vector<double> cost(n);
     std::vector<int> tiles(n);
     double total = 0.0;
+    // one column width for the whole launch: the narrowest any scene needs
+    G.batch_cw = 0;
+    for (int s = 0; s < n; ++s) {
+        const nsf_fields_desc &d = items[s].fields->desc;
+        const int cw = jac_batch_cw(d.r, d.width[NSF_FIELD_G], d.depth[NSF_FIELD_G]);
+        if (G.batch_cw == 0 || cw < G.batch_cw) G.batch_cw = cw;
+    }
     for (int s = 0; s < n; ++s) {
         const nsf_fields_desc &d = items[s].fields->desc;
         const int W = d.width[NSF_FIELD_G], D = d.depth[NSF_FIELD_G];
-        const int cw = jac_batch_cw(d.r, W, D);
+        const int cw = G.batch_cw;
         G.cw.push_back(cw);
         const int P = jac_batch_points(d.r, cw);
         tiles[s] = (items[s].scene.n_S + P - 1) / P;
@@ -962,7 +970,7 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
         if (tiles[s] > slots) tiles[s] = slots;
         cost[s] = (double)items[s].scene.n_S * (D + 1) * jac_point_layer_cost(jac_slots_host(d.r), W);
         total += cost[s];
-        const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw, 4);
+        const size_t sm = jac_tc_smem_bytes_cw(d.r, W, D, cw, jac_batch_wg());
         G.smem = sm > G.smem ? sm : G.smem;
     }
     const int cap = sms < kGnMaxCtas ? sms : kGnMaxCtas;
@@ -1064,6 +1072,7 @@ struct nsf_latent_batch {
     int *cta_entry;
     int gn_ctas;
     size_t gn_smem;
+    int gn_cw;
 };
 
 extern "C" {
@@ -1235,6 +1244,7 @@ nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
     B->cta_entry = reinterpret_cast<int *>(dm + o_ce);
     B->gn_ctas = G.nctas;
     B->gn_smem = G.smem;
+    B->gn_cw = G.batch_cw;
     *out = B;
     return NSF_OK;
 }
@@ -1284,7 +1294,7 @@ nsf_status nsf_latent_step_batched(const nsf_latent_batch *b, double t0, int nst
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_MPM));
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_GN));
         NSF_CUDA_TRY(launch_jac_batch(b->probs, b->entries, b->cta_entry, b->gn_ctas, b->gn_smem,
-                                      d_status, s));
+                                      b->gn_cw, d_status, s));
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_GN));
     }
     // keep every scene's g(X, z_prev) of the returned z_prev in u[1]

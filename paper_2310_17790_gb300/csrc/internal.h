@@ -342,10 +342,11 @@ struct GnBatchEntry {
 };
 int jac_points_per_cta_tile(int r);
 int jac_batch_cw(int r, int width, int depth);
+int jac_batch_wg();
 int jac_batch_points(int r, int cw);
 size_t jac_tc_smem_bytes_cw(int r, int width, int depth, int CW, int NWG);
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
-                             const int *cta_entry, int nctas, size_t smem, int *status,
+                             const int *cta_entry, int nctas, size_t smem, int cw, int *status,
                              cudaStream_t s);
 
 // MPM step: one cooperative launch each (P2G, block activation, grid update

@@ -467,10 +467,14 @@ __device__ __forceinline__ void jac_batch_problem(const GnBatchProblem &pb, cons
 // shared by a group of CTAs (group size > 1) is the first entry of each of
 // them, so every member reaches the group's barriers inside that problem and
 // no barrier waits on a CTA that is still busy with another problem.  The CTAs
-// have four warpgroups of 32 or 64 columns: tiles of up to 256 point slots,
-// whose products take as many tcgen05.mma instructions as the single-problem
-// kernel's 64-slot tiles (a layer's instructions cost about the same per
-// issue up to this size), at 128 registers per thread.
+// have four warpgroups of CW = 64 (or, when a scene's operands need it, 32)
+// columns: tiles of 256 (128) point slots, whose products take as many
+// tcgen05.mma instructions as the single-problem kernel's 64-slot tiles (a
+// layer's instructions cost about the same per issue up to this size).  One
+// CW for the whole launch keeps a single body per kernel.  (Eight warpgroups
+// of half the columns measured slower: 5.85 against 4.71 ms on the 256-scene
+// batch.)
+template <int CW>
 __global__ void __launch_bounds__(kBatchWG * kWgThreads, 1)
 k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__restrict__ entries,
             const int *__restrict__ cta_entry, int *status) {
@@ -478,9 +482,7 @@ k_jac_batch(const GnBatchProblem *__restrict__ probs, const GnBatchEntry *__rest
     const int e0 = cta_entry[blockIdx.x], e1 = cta_entry[blockIdx.x + 1];
     for (int e = e0; e < e1; ++e) {
         const GnBatchEntry en = entries[e];
-        const GnBatchProblem &pb = probs[en.problem];
-        if (pb.cw == 32) jac_batch_problem<32>(pb, en, smem_dyn, status);
-        else jac_batch_problem<64>(pb, en, smem_dyn, status);
+        jac_batch_problem<CW>(probs[en.problem], en, smem_dyn, status);
         __syncthreads();
     }
 }
@@ -560,20 +562,25 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
 int jac_points_per_cta_tile(int r) { return jac_points(r); }
 
 // Columns per warpgroup of a batched problem (four warpgroups per CTA): 64 if
-// the operands fit (a 256-slot tile), else 32; 0 if neither fits.
+// the operands fit (a 256-slot tile), else 32; at least the problem's slot
+// count; 0 if neither fits.
 int jac_batch_cw(int r, int width, int depth) {
     for (int cw = 64; cw >= 32; cw >>= 1)
-        if (jac_tc_smem_bytes_cw(r, width, depth, cw, kBatchWG)) return cw;
+        if (cw >= jac_slots(r) && jac_tc_smem_bytes_cw(r, width, depth, cw, kBatchWG)) return cw;
     return 0;
 }
 int jac_batch_points(int r, int cw) { return kBatchWG * cw / jac_slots(r); }
 
+int jac_batch_wg() { return kBatchWG; }
+
 cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *entries,
-                             const int *cta_entry, int nctas, size_t smem, int *status,
+                             const int *cta_entry, int nctas, size_t smem, int cw, int *status,
                              cudaStream_t s) {
     if (nctas <= 0) return cudaSuccess;
-    static bool done = false;
-    set_max_dynamic_smem(k_jac_batch, done);
+    if (cw != 32 && cw != 64) return cudaErrorInvalidValue;
+    static bool done32 = false, done64 = false;
+    if (cw == 32) set_max_dynamic_smem(k_jac_batch<32>, done32);
+    else set_max_dynamic_smem(k_jac_batch<64>, done64);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nctas);
     cfg.blockDim = dim3(kBatchWG * kWgThreads);
@@ -584,7 +591,8 @@ cudaError_t launch_jac_batch(const GnBatchProblem *probs, const GnBatchEntry *en
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_jac_batch, probs, entries, cta_entry, status);
+    if (cw == 32) return cudaLaunchKernelEx(&cfg, k_jac_batch<32>, probs, entries, cta_entry, status);
+    return cudaLaunchKernelEx(&cfg, k_jac_batch<64>, probs, entries, cta_entry, status);
 }
 
 }  // namespace nsf
