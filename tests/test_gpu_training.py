@@ -78,14 +78,20 @@ def _gpu_loss_grad(nsf, F, k, X, z, code, target):
     return float(loss.item()), gw.cpu().numpy().astype(np.float64), gz.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("precision,k,width,depth", [
-    ("fp32", "g", 64, 3), ("fp32", "h", 64, 4), ("fp32", "l", 128, 2),
-    ("bf16", "g", 128, 5), ("bf16", "h", 64, 3)])
-def test_loss_and_gradients_match_oracle(nsf, precision, k, width, depth):
-    spec = _spec(7, precision, width=width, depth=depth)
+# BF16 shapes beyond the benchmark's: a width of 192 (a partial second
+# 128-channel tile of the hidden-layer products), 256 at depth 1 (no hidden
+# product), r = 16 (19 inputs, the widest thin-K and input-layer kernels),
+# field l's 9 outputs, and point counts off every tile size
+@pytest.mark.parametrize("precision,k,width,depth,r,n", [
+    ("fp32", "g", 64, 3, 6, 1000), ("fp32", "h", 64, 4, 6, 1000), ("fp32", "l", 128, 2, 6, 1000),
+    ("bf16", "g", 128, 5, 6, 1000), ("bf16", "h", 64, 3, 6, 1000),
+    ("bf16", "l", 192, 3, 6, 1000), ("bf16", "g", 256, 1, 16, 777),
+    ("bf16", "h", 64, 4, 16, 129), ("bf16", "g", 256, 3, 3, 2049)])
+def test_loss_and_gradients_match_oracle(nsf, precision, k, width, depth, r, n):
+    spec = _spec(7, precision, r=r, width=width, depth=depth)
     F = nsf.Fields.from_spec(spec)
     od = ofields.OUT_DIM[k]
-    X, z, code, target = _data(8, 1000, spec.r, 5, od, k)
+    X, z, code, target = _data(8, n, spec.r, 5, od, k)
     L, gw, gz = _gpu_loss_grad(nsf, F, k, X, z, code, target)
     of = _oracle_field(spec, k)
     L_o, grads, gz_o = otraining.loss_and_grads(of, X, z.astype(np.float64), code,
@@ -97,6 +103,18 @@ def test_loss_and_gradients_match_oracle(nsf, precision, k, width, depth):
     assert abs(L - L_o) <= (1e-5 if precision == "fp32" else 1e-3) * L_o
     assert rel(gw, gw_o) < tol
     assert rel(gz, gz_o) < tol
+
+
+def test_bf16_weight_gradients_are_reproducible_bit_for_bit(nsf):
+    """Every sum behind the weight gradient (slabs, bias column sums, the
+    input layer's per-CTA partials) runs in a fixed order, so two calls on the
+    same data agree in every bit.  (The loss value and the latent codes'
+    gradient are summed with float atomics and are not compared.)"""
+    spec = _spec(21, "bf16", width=256, depth=3)
+    F = nsf.Fields.from_spec(spec)
+    X, z, code, target = _data(22, 4099, spec.r, 7, ofields.OUT_DIM["g"], "g")
+    runs = [_gpu_loss_grad(nsf, F, "g", X, z, code, target) for _ in range(2)]
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
