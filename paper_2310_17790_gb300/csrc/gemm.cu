@@ -922,16 +922,21 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
 //   dinp(p, j) = sum_o W0[o][j] delta_0(p, o)      (toward the latent codes)
 //   dW0[o][j]  = sum_p delta_0(p, o) inp(p, j),  db0[o] = sum_p delta_0(p, o).
 // One pass over delta_0 (the bf16 hi + lo pairs or an FP32 array): a CTA
-// stages 32 points x W of it and their inputs in shared memory; thread
-// (point t / 8, channel group t % 8) sums its group's channels for dinp (then
-// a fixed xor-shuffle sum over the 8 groups), and thread t = o accumulates
-// dW0 / db0 of channel o over the points of all the CTA's tiles, in order,
-// written once as the CTA's slab in the gradient layout [W0 (W x K0) | b0].
-constexpr int kIbPoints = 32, kIbThreads = 256, kIbRow = 8 * 33 + 1, kIbMaxGrid = 320;
+// stages 64 points x W of it and their inputs in shared memory, then
+//   dinp: thread (point pair t / 8, channel group t % 8 of 32) sums its
+//         group's channels for two points (each weight load serves both),
+//         then a fixed xor-shuffle sum over the 8 groups;
+//   dW0 / db0: thread (point quarter t / 64, channels 4 (t % 64) .. + 3)
+//         accumulates its 16 points of every tile, in order;
+// and at the end the four quarters' sums are added in order and written once
+// as the CTA's slab in the gradient layout [W0 (W x K0) | b0].
+constexpr int kIbPoints = 64, kIbThreads = 256, kIbRow = 8 * 33 + 1, kIbMaxGrid = 320;
 __host__ __device__ inline int ib_k0p(int K0) { return (K0 + 3) / 4 * 4; }
 __host__ __device__ inline size_t ib_smem(int K0) {
     const int k0p = ib_k0p(K0);
-    return sizeof(float) * ((size_t)kIbPoints * kIbRow + kIbPoints * k0p + 8 * (32 * k0p + 4));
+    const size_t tiles = (size_t)kIbPoints * kIbRow + kIbPoints * k0p + 8 * (32 * k0p + 4);
+    const size_t comb = 4 * (size_t)NSF_MAX_WIDTH * (k0p + 1);   // the final combine
+    return sizeof(float) * (tiles > comb ? tiles : comb);
 }
 
 template <int K0P>
@@ -949,10 +954,13 @@ k_input_bwd(int n, int W, int K0, const __nv_bfloat16 *__restrict__ dhi,
         const int o = i / k0p, j = i % k0p;
         sw[(o >> 5) * (32 * k0p + 4) + (o & 31) * k0p + j] = j < K0 ? W0[(size_t)o * K0 + j] : 0.f;
     }
-    float acc[K0P], accb = 0.f;
+    const int pq = tid >> 3, og = tid & 7;           // dinp: points 2 pq, 2 pq + 1; group og
+    const int qt = tid >> 6, c4 = 4 * (tid & 63);    // dW0: points 16 qt .. + 15; channels c4 .. + 3
+    float acc[4][K0P + 1];
 #pragma unroll
-    for (int j = 0; j < K0P; ++j) acc[j] = 0.f;
-    const int o = tid, pp = tid >> 3, og = tid & 7;
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j <= K0P; ++j) acc[u][j] = 0.f;
     const int ntiles = (n + kIbPoints - 1) / kIbPoints, w8 = W / 8;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int p0 = tile * kIbPoints;
@@ -985,68 +993,91 @@ k_input_bwd(int n, int W, int K0, const __nv_bfloat16 *__restrict__ dhi,
 #pragma unroll
             for (int t = 0; t < 8; ++t) dst[t] = v[t];
         }
-        for (int q = tid; q < kIbPoints * K0; q += kIbThreads) {
-            const int pt = q / K0, j = q % K0, p = p0 + pt;
-            sx[pt * k0p + j] = p < n ? inp[(size_t)p * K0 + j] : 0.f;
+        for (int q = tid; q < kIbPoints * k0p; q += kIbThreads) {
+            const int pt = q / k0p, j = q % k0p, p = p0 + pt;
+            sx[q] = (p < n && j < K0) ? inp[(size_t)p * K0 + j] : 0.f;
         }
-        for (int q = tid; q < kIbPoints * (k0p - K0); q += kIbThreads)
-            sx[(q / (k0p - K0)) * k0p + K0 + q % (k0p - K0)] = 0.f;
         __syncthreads();
         {
-            // this group's channels (W % 32 == 0: a group is whole or absent), then a
-            // fixed-order sum over the 8 groups that every lane takes part in
-            float sj[K0P];
+            // this group's channels (W % 32 == 0: a group is whole or absent),
+            // then a fixed-order sum over the 8 groups that every lane takes part in
+            float s0[K0P], s1[K0P];
 #pragma unroll
-            for (int j = 0; j < K0P; ++j) sj[j] = 0.f;
+            for (int j = 0; j < K0P; ++j) s0[j] = s1[j] = 0.f;
             if (og * 32 < W) {
-                const float *dp = sd + pp * kIbRow + og * 33;
+                const float *dp0 = sd + (2 * pq) * kIbRow + og * 33, *dp1 = dp0 + kIbRow;
                 const float *wp = sw + og * (32 * k0p + 4);
-#pragma unroll 8
+#pragma unroll 4
                 for (int oi = 0; oi < 32; ++oi) {
-                    const float d = dp[oi];
+                    const float d0 = dp0[oi], d1 = dp1[oi];
 #pragma unroll
                     for (int j4 = 0; j4 < K0P; j4 += 4) {
                         const float4 w = *reinterpret_cast<const float4 *>(wp + oi * k0p + j4);
-                        sj[j4] = fmaf(w.x, d, sj[j4]);
-                        sj[j4 + 1] = fmaf(w.y, d, sj[j4 + 1]);
-                        sj[j4 + 2] = fmaf(w.z, d, sj[j4 + 2]);
-                        sj[j4 + 3] = fmaf(w.w, d, sj[j4 + 3]);
+                        s0[j4] = fmaf(w.x, d0, s0[j4]);
+                        s0[j4 + 1] = fmaf(w.y, d0, s0[j4 + 1]);
+                        s0[j4 + 2] = fmaf(w.z, d0, s0[j4 + 2]);
+                        s0[j4 + 3] = fmaf(w.w, d0, s0[j4 + 3]);
+                        s1[j4] = fmaf(w.x, d1, s1[j4]);
+                        s1[j4 + 1] = fmaf(w.y, d1, s1[j4 + 1]);
+                        s1[j4 + 2] = fmaf(w.z, d1, s1[j4 + 2]);
+                        s1[j4 + 3] = fmaf(w.w, d1, s1[j4 + 3]);
                     }
                 }
             }
 #pragma unroll
             for (int off = 1; off < 8; off <<= 1)
 #pragma unroll
-                for (int j = 0; j < K0P; ++j) sj[j] += __shfl_xor_sync(0xffffffffu, sj[j], off);
-            const int p = p0 + pp;
-            if (p < n)
+                for (int j = 0; j < K0P; ++j) {
+                    s0[j] += __shfl_xor_sync(0xffffffffu, s0[j], off);
+                    s1[j] += __shfl_xor_sync(0xffffffffu, s1[j], off);
+                }
+            const int p = p0 + 2 * pq;
 #pragma unroll
-                for (int j = 0; j < K0P; ++j)
-                    if (j < K0 && (j & 7) == og) dinp[(size_t)p * K0 + j] = sj[j];
+            for (int j = 0; j < K0P; ++j)
+                if (j < K0 && (j & 7) == og) {
+                    if (p < n) dinp[(size_t)p * K0 + j] = s0[j];
+                    if (p + 1 < n) dinp[(size_t)(p + 1) * K0 + j] = s1[j];
+                }
         }
-        if (o < W) {
-            const float *dcol = sd + (o >> 5) * 33 + (o & 31);
-#pragma unroll 8
-            for (int pt = 0; pt < kIbPoints; ++pt) {
-                const float d = dcol[pt * kIbRow];
-                accb += d;
+        if (c4 < W) {
+            const float *dcol = sd + (c4 >> 5) * 33 + (c4 & 31);
+#pragma unroll 4
+            for (int pt = 16 * qt; pt < 16 * qt + 16; ++pt) {
+                const float d[4] = {dcol[pt * kIbRow], dcol[pt * kIbRow + 1], dcol[pt * kIbRow + 2],
+                                    dcol[pt * kIbRow + 3]};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u][K0P] += d[u];
 #pragma unroll
                 for (int j4 = 0; j4 < K0P; j4 += 4) {
                     const float4 x = *reinterpret_cast<const float4 *>(sx + pt * k0p + j4);
-                    acc[j4] = fmaf(d, x.x, acc[j4]);
-                    acc[j4 + 1] = fmaf(d, x.y, acc[j4 + 1]);
-                    acc[j4 + 2] = fmaf(d, x.z, acc[j4 + 2]);
-                    acc[j4 + 3] = fmaf(d, x.w, acc[j4 + 3]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        acc[u][j4] = fmaf(d[u], x.x, acc[u][j4]);
+                        acc[u][j4 + 1] = fmaf(d[u], x.y, acc[u][j4 + 1]);
+                        acc[u][j4 + 2] = fmaf(d[u], x.z, acc[u][j4 + 2]);
+                        acc[u][j4 + 3] = fmaf(d[u], x.w, acc[u][j4 + 3]);
+                    }
                 }
             }
         }
     }
-    if (o < W) {
-        float *mine = slab + (size_t)blockIdx.x * ((size_t)W * K0 + W);
+    // the four point quarters' sums, added in quarter order
+    __syncthreads();
+    float *comb = ib;                    // [quarter][channel][k0p + 1]
+    if (c4 < W)
 #pragma unroll
-        for (int j = 0; j < K0P; ++j)
-            if (j < K0) mine[(size_t)o * K0 + j] = acc[j];
-        mine[(size_t)W * K0 + o] = accb;
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j <= K0P; ++j) comb[((size_t)qt * W + c4 + u) * (k0p + 1) + j] = acc[u][j];
+    __syncthreads();
+    float *mine = slab + (size_t)blockIdx.x * ((size_t)W * K0 + W);
+    for (int e = tid; e < W * (K0 + 1); e += kIbThreads) {
+        const int o = e / (K0 + 1), j = e % (K0 + 1), jj = j < K0 ? j : K0P;
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t += comb[((size_t)q * W + o) * (k0p + 1) + jj];
+        if (j < K0) mine[(size_t)o * K0 + j] = t;
+        else mine[(size_t)W * K0 + o] = t;
     }
 }
 
@@ -1147,6 +1178,59 @@ k_thin_m(int M, int N, int K, const MatView A, const MatView B, float *out, long
 #pragma unroll
     for (int m = 0; m < NM; ++m)
         if (m < M) out[(size_t)n * ld + m] = acc[m];
+}
+
+// The same for a bf16 B with contiguous k (the output layer's forward
+// product on the BF16 path): one warp per column n, lane l multiplying k =
+// 8 l .. 8 l + 7 (one 16-byte load of B's row; A's matching values held in
+// registers for all the warp's columns), then a fixed xor-shuffle sum over the
+// lanes.  A row of B is read as one 512-byte stretch by the warp.
+template <int NM>
+__global__ void __launch_bounds__(256)
+k_thin_m_warp(int M, int N, int K, const MatView A, const __nv_bfloat16 *__restrict__ B,
+              long long ldb, float *out, long long ld) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const bool act = 8 * lane < K;
+    float a[NM][8];
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[m][j] = (act && m < M) ? view_at(A, m, 8 * lane + j) : 0.f;
+    constexpr int kU = 4;                       // columns whose loads are in flight together
+    for (int n0 = warp; n0 < N; n0 += kU * nwarps) {
+        uint4 q[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int n = n0 + u * nwarps;
+            q[u] = (act && n < N) ? __ldg(reinterpret_cast<const uint4 *>(B + (size_t)n * ldb) + lane)
+                                  : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int n = n0 + u * nwarps;
+            const uint32_t w[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+            float acc[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                acc[m] = 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    acc[m] = fmaf(a[m][2 * t], __uint_as_float(w[t] << 16), acc[m]);
+                    acc[m] = fmaf(a[m][2 * t + 1], __uint_as_float(w[t] & 0xFFFF0000u), acc[m]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], off);
+            if (n < N)
+#pragma unroll
+                for (int m = 0; m < NM; ++m)
+                    if (m < M && lane == m) out[(size_t)n * ld + m] = acc[m];
+        }
+    }
 }
 
 __global__ void k_reduce_slabs_t(const float *__restrict__ slab, int slices, int A, int C,
@@ -1353,6 +1437,16 @@ cudaError_t thin_m(int M, int N, int K, const MatView &A, const MatView &B, floa
                    long long ld, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (M > kThinA || K > kThinMaxK) return cudaErrorInvalidValue;
+    if (B.bf16 && B.s_k == 1 && K % 8 == 0 && B.s_row % 8 == 0 && (((size_t)B.ptr) & 15) == 0 &&
+        M <= 16) {
+        const int grid = 2 * sm_count();   // two CTAs of 8 warps a SM share the columns
+        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(B.ptr);
+        if (M <= 4) k_thin_m_warp<4><<<grid, 256, 0, s>>>(M, N, K, A, b, B.s_row, out, ld);
+        else if (M <= 8) k_thin_m_warp<8><<<grid, 256, 0, s>>>(M, N, K, A, b, B.s_row, out, ld);
+        else if (M <= 12) k_thin_m_warp<12><<<grid, 256, 0, s>>>(M, N, K, A, b, B.s_row, out, ld);
+        else k_thin_m_warp<16><<<grid, 256, 0, s>>>(M, N, K, A, b, B.s_row, out, ld);
+        return cudaGetLastError();
+    }
     const int g = (N + kThinThreads - 1) / kThinThreads;
     if (M <= 4) k_thin_m<4><<<g, kThinThreads, 0, s>>>(M, N, K, A, B, out, ld);
     else if (M <= 16) k_thin_m<16><<<g, kThinThreads, 0, s>>>(M, N, K, A, B, out, ld);
