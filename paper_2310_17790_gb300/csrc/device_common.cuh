@@ -15,6 +15,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may be scheduled while the kernel before it
+// in the stream is still finishing; griddepcontrol.wait then blocks until that
+// kernel has completed and its memory is visible (a no-op for a normal
+// launch).  The kernels that are launched this way call it before touching
+// global memory at all, so only their launch and CTA set-up overlap the
+// previous kernel.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // First error wins: the status word only moves away from NSF_OK once.
 __device__ __forceinline__ void set_status(int *status, int code) {
     if (status) atomicCAS(status, NSF_OK, code);

@@ -400,6 +400,7 @@ template <int W>
 __global__ void __launch_bounds__(kMaxGroups * kGroupThreads, 1)
 k_fields_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
             const __grid_constant__ TcJobs jobs, int ng, int maxD, int *status) {
+    pdl_wait();
     extern __shared__ uint8_t smem_dyn[];
     const SingleSrc src{&fd, X, n, ld, &jobs};
     fields_body<W>(src, 1, ng, maxD, smem_dyn, status);
@@ -466,8 +467,19 @@ cudaError_t launch_fields_tc_w(const FieldsDev &fd, const float *X, int n, int l
         const int d = fd.f[tj.job[i].field].depth;
         maxD = d > maxD ? d : maxD;
     }
-    k_fields_tc<W><<<grid, ng * kGroupThreads, sm, s>>>(fd, X, n, ld, tj, ng, maxD, status);
-    return cudaGetLastError();
+    // programmatic stream serialisation: the kernel waits for its predecessor
+    // (pdl_wait) before any global access
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(ng * kGroupThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fields_tc<W>, fd, X, n, ld, tj, ng, maxD, status);
 }
 
 }  // namespace

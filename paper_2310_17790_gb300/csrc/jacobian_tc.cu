@@ -447,6 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_jac_tc(const __grid_constant__ FieldsDev fd, const float *__restrict__ X, int n, int ld,
          const double *zj, float *u, float *dudz, const __grid_constant__ GnArgs gn, int gn_on,
          int *status) {
+    pdl_wait();
     extern __shared__ uint8_t smem_dyn[];
     jac_body<CW>(fd, X, n, ld, zj, u, dudz, gn, gn_on, (int)blockIdx.x, (int)gridDim.x, true,
                  smem_dyn, status);
@@ -539,11 +540,20 @@ cudaError_t launch_jacobian_tc(const FieldsDev &fd, const float *X, int n, int l
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    // cooperative for Gauss-Newton (grid barriers); programmatic stream
+    // serialisation either way (the kernel calls pdl_wait first)
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (gn_on) {
+        attr[na].id = cudaLaunchAttributeCooperative;
+        attr[na].val.cooperative = 1;
+        ++na;
+    }
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
     cfg.attrs = attr;
-    cfg.numAttrs = gn_on ? 1 : 0;
+    cfg.numAttrs = na;
     if (jac_cw(fd.r) == 8) {
         static bool done = false;
         set_max_dynamic_smem(k_jac_tc<8>, done);

@@ -750,6 +750,7 @@ constexpr int kTileThreadsFull = 128;
 __global__ void __launch_bounds__(kThreads)
 k_mpm_latent(GridWs g, GridParams gp, P2gLatentArgs a, int n_S, double t, float *d_next,
              float *tap_mp, float *tap_v, int *status) {
+    pdl_wait();
     const int epoch = begin_step(g);
     if (!bin_p2g_grid<kTileThreadsLatent>(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
     if (!grid_barrier(&g.ctl->bar, status)) return;
@@ -988,17 +989,21 @@ int coop_grid(K kernel, int cap = 4) {
     return sms * per;
 }
 
+// A cooperative launch; pdl: also programmatic stream serialisation (the
+// kernel calls pdl_wait() first).
 template <class K, class... A>
-cudaError_t launch_coop(K kernel, int grid, cudaStream_t s, A... args) {
+cudaError_t launch_coop(K kernel, int grid, cudaStream_t s, bool pdl, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -1033,21 +1038,21 @@ cudaError_t launch_mpm_latent(const GridWs &g, const GridParams &gp, const P2gLa
                               int n_S, double t, float *d_next, float *tap_mp, float *tap_v,
                               int *status, cudaStream_t s) {
     static const int grid = coop_grid(k_mpm_latent, NSF_LATENT_MPM_CTAS_PER_SM);
-    return launch_coop(k_mpm_latent, grid, s, g, gp, a, n_S, t, d_next, tap_mp,
+    return launch_coop(k_mpm_latent, grid, s, true, g, gp, a, n_S, t, d_next, tap_mp,
                        tap_v, status);
 }
 
 cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int *status, cudaStream_t s) {
     if (b.nscenes < 1 || b.nscenes > kMaxBatchScenes) return cudaErrorInvalidValue;
     static const int grid = coop_grid(k_mpm_batch);
-    return launch_coop(k_mpm_batch, grid, s, b, status);
+    return launch_coop(k_mpm_batch, grid, s, false, b, status);
 }
 
 cudaError_t launch_mpm_full(const GridWs &g, const GridParams &gp, const P2gFullArgs &pa,
                             const G2pFullArgs &ga, double t, float *tap_mp, float *tap_v,
                             int *status, cudaStream_t s) {
     static const int grid = coop_grid(k_mpm_full);
-    cudaError_t e = launch_coop(k_mpm_full, grid, s, g, gp, pa, t, tap_mp, tap_v,
+    cudaError_t e = launch_coop(k_mpm_full, grid, s, false, g, gp, pa, t, tap_mp, tap_v,
                                 status);
     if (e != cudaSuccess) return e;
     k_g2p_full<<<(ga.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(g, gp, ga, status);
