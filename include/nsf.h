@@ -410,6 +410,34 @@ nsf_status nsf_latent_batch_workspace_size(int n_items, const nsf_latent_batch_i
 nsf_status nsf_latent_batch_create(int n_items, const nsf_latent_batch_item *items,
                                    const nsf_gn_opts *opts, void *d_workspace,
                                    size_t workspace_bytes, nsf_latent_batch **out);
+
+/*
+ * Tile choices of a batch plan, for a tuner that times candidates (the
+ * library's Python layer has one: paper_2310_17790_gb300.autotune).  Every
+ * choice changes only the schedule and the tile shapes, not the arithmetic of
+ * a scene's step beyond the order of some float sums.  0 keeps the default.
+ *   gn_columns  columns per warpgroup of the Gauss-Newton tiles, 32 or 64
+ *               (tiles of 128 or 256 point slots); default: 64 where every
+ *               scene's operands fit in shared memory, else 32.
+ *   gn_split    the cost above which a scene's Gauss-Newton run is split over
+ *               a group of CTAs, as a multiple (> 0) of the per-SM share of the
+ *               batch's estimated cost; default: the multiple with the smallest
+ *               estimated makespan.
+ *   p2g_group   threads per 4^3-block P2G tile of the MPM step, 64 or 128.
+ */
+typedef struct nsf_batch_tuning {
+    int gn_columns;
+    double gn_split;
+    int p2g_group;
+} nsf_batch_tuning;
+
+/* nsf_latent_batch_create with explicit tile choices (tuning may be NULL: the
+ * defaults); NSF_ERR_INVALID_ARG for a value outside the lists above or a
+ * column count some scene's operands do not fit. */
+nsf_status nsf_latent_batch_create_tuned(int n_items, const nsf_latent_batch_item *items,
+                                         const nsf_gn_opts *opts,
+                                         const nsf_batch_tuning *tuning, void *d_workspace,
+                                         size_t workspace_bytes, nsf_latent_batch **out);
 void nsf_latent_batch_destroy(nsf_latent_batch *batch);
 
 /* Optional stage events of nsf_latent_step_batched (cudaEvent_t handles or

@@ -346,10 +346,24 @@ def nsf_latent_batch_workspace_size(items):
     return b.value
 
 
-def nsf_latent_batch_create(items, opts, workspace):
+def batch_tuning(gn_columns=0, gn_split=0.0, p2g_group=0):
+    """nsf_batch_tuning (0 keeps a default)."""
+    return N.nsf_batch_tuning(int(gn_columns), float(gn_split), int(p2g_group))
+
+
+def nsf_latent_batch_create(items, opts, workspace, tuning=None):
     h = C.c_void_p()
-    check(N.lib.nsf_latent_batch_create(len(items), items, C.byref(opts), _ptr(workspace),
-                                        workspace.numel(), C.byref(h)), "nsf_latent_batch_create")
+    if tuning is None:
+        check(N.lib.nsf_latent_batch_create(len(items), items, C.byref(opts), _ptr(workspace),
+                                            workspace.numel(), C.byref(h)),
+              "nsf_latent_batch_create")
+    else:
+        if isinstance(tuning, dict):
+            tuning = batch_tuning(**tuning)
+        check(N.lib.nsf_latent_batch_create_tuned(len(items), items, C.byref(opts),
+                                                  C.byref(tuning), _ptr(workspace),
+                                                  workspace.numel(), C.byref(h)),
+              "nsf_latent_batch_create_tuned")
     return h
 
 
@@ -428,14 +442,15 @@ class LatentBatch:
     together (nsf_latent_step_batched).  entries as in batch_items; the
     tensors must stay alive with the batch."""
 
-    def __init__(self, entries, iters=5, damping=1e-6):
+    def __init__(self, entries, iters=5, damping=1e-6, tuning=None):
         torch = _torch()
         self.entries = list(entries)
         self.items = batch_items(self.entries)
         dev = self.entries[0][1].device
         self.ws = _zeros_u8(nsf_latent_batch_workspace_size(self.items), dev)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
-        self.handle = nsf_latent_batch_create(self.items, gn_opts(iters, damping), self.ws)
+        self.handle = nsf_latent_batch_create(self.items, gn_opts(iters, damping), self.ws,
+                                              tuning)
 
     def step(self, t0=0.0, nsteps=1, events=None, stream=None, reuse_prev=False):
         nsf_latent_step_batched(self.handle, t0, nsteps, self.status, events, stream,

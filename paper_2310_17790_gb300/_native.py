@@ -69,6 +69,10 @@ class nsf_latent_batch_item(C.Structure):
                 ("d_z", C.c_void_p), ("d_z_prev", C.c_void_p)]
 
 
+class nsf_batch_tuning(C.Structure):
+    _fields_ = [("gn_columns", C.c_int), ("gn_split", C.c_double), ("p2g_group", C.c_int)]
+
+
 class nsf_batch_events(C.Structure):
     _fields_ = [("ev_begin", C.c_void_p * NSF_LATENT_STAGES),
                 ("ev_end", C.c_void_p * NSF_LATENT_STAGES)]
@@ -118,6 +122,9 @@ SIGNATURES = [
     ("nsf_latent_batch_workspace_size", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(_S)]),
     ("nsf_latent_batch_create", _ST, [_I, C.POINTER(nsf_latent_batch_item), C.POINTER(nsf_gn_opts),
                                       _P, _S, C.POINTER(_P)]),
+    ("nsf_latent_batch_create_tuned", _ST, [_I, C.POINTER(nsf_latent_batch_item),
+                                            C.POINTER(nsf_gn_opts), C.POINTER(nsf_batch_tuning),
+                                            _P, _S, C.POINTER(_P)]),
     ("nsf_latent_batch_destroy", None, [_P]),
     ("nsf_latent_step_batched", _ST, [_P, _D, _I, C.c_uint, _P, C.POINTER(nsf_batch_events), _P]),
     ("nsf_full_workspace_size", _ST, [C.POINTER(nsf_grid_desc), _I, C.POINTER(_S)]),

@@ -946,17 +946,26 @@ double jac_point_layer_cost(int L, int W) {
 // (its group barriers and the combine of its sums).
 constexpr double kGnSplitOverhead = 1.03;
 
-GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
+GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms, int want_cw, double split) {
     GnPlan G;
     std::vector<double> cost(n);
     std::vector<int> tiles(n);
     double total = 0.0;
-    // one column width for the whole launch: the narrowest any scene needs
+    // one column width for the whole launch: the narrowest any scene needs,
+    // or the requested one where every scene's operands fit
     G.batch_cw = 0;
     for (int s = 0; s < n; ++s) {
         const nsf_fields_desc &d = items[s].fields->desc;
         const int cw = jac_batch_cw(d.r, d.width[NSF_FIELD_G], d.depth[NSF_FIELD_G]);
         if (G.batch_cw == 0 || cw < G.batch_cw) G.batch_cw = cw;
+        if (want_cw && (want_cw < jac_slots_host(d.r) ||
+                        !jac_tc_smem_bytes_cw(d.r, d.width[NSF_FIELD_G], d.depth[NSF_FIELD_G],
+                                              want_cw, jac_batch_wg())))
+            G.batch_cw = -1;
+    }
+    if (want_cw) {
+        if (G.batch_cw < 0) return G;        // not every scene fits: an empty plan
+        G.batch_cw = want_cw;
     }
     for (int s = 0; s < n; ++s) {
         const nsf_fields_desc &d = items[s].fields->desc;
@@ -1023,8 +1032,8 @@ GnPlan plan_gn(int n, const nsf_latent_batch_item *items, int sms) {
     };
 
     std::vector<std::vector<GnBatchEntry>> per, trial;
-    double best = plan_for(share, per);
-    for (int k = 0; k <= 150; ++k) {
+    double best = plan_for(split > 0.0 ? share * split : share, per);
+    for (int k = 0; k <= 150 && split <= 0.0; ++k) {
         const double span = plan_for(share * (0.5 + 0.01 * k), trial);
         if (span < best) {
             best = span;
@@ -1073,6 +1082,7 @@ struct nsf_latent_batch {
     int gn_ctas;
     size_t gn_smem;
     int gn_cw;
+    int p2g_group;
 };
 
 extern "C" {
@@ -1091,7 +1101,19 @@ nsf_status nsf_latent_batch_workspace_size(int n, const nsf_latent_batch_item *i
 nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
                                    const nsf_gn_opts *opts, void *d_ws, size_t ws_bytes,
                                    nsf_latent_batch **out) {
+    return nsf_latent_batch_create_tuned(n, items, opts, nullptr, d_ws, ws_bytes, out);
+}
+
+nsf_status nsf_latent_batch_create_tuned(int n, const nsf_latent_batch_item *items,
+                                         const nsf_gn_opts *opts, const nsf_batch_tuning *tuning,
+                                         void *d_ws, size_t ws_bytes, nsf_latent_batch **out) {
     if (!out || n < 1 || n > NSF_MAX_BATCH || n > kMaxBatchScenes || !items || !valid_gn(opts))
+        return NSF_ERR_INVALID_ARG;
+    nsf_batch_tuning tu{0, 0.0, 0};
+    if (tuning) tu = *tuning;
+    if ((tu.gn_columns != 0 && tu.gn_columns != 32 && tu.gn_columns != 64) ||
+        !(tu.gn_split >= 0.0) || !std::isfinite(tu.gn_split) ||
+        (tu.p2g_group != 0 && tu.p2g_group != 64 && tu.p2g_group != 128))
         return NSF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         if (!valid_batch_item(items[i])) return NSF_ERR_INVALID_ARG;
@@ -1124,7 +1146,8 @@ nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
             WidthPlan P = plan_width(w, n, items, set == 1, sms);
             if (P.nctas > 0) wp[set].push_back(P);
         }
-    const GnPlan G = plan_gn(n, items, sms);
+    const GnPlan G = plan_gn(n, items, sms, tu.gn_columns, tu.gn_split);
+    if (G.batch_cw <= 0) return NSF_ERR_INVALID_ARG;     // a requested width that does not fit
 
     // table layout
     TableCarver tc_;
@@ -1245,6 +1268,7 @@ nsf_status nsf_latent_batch_create(int n, const nsf_latent_batch_item *items,
     B->gn_ctas = G.nctas;
     B->gn_smem = G.smem;
     B->gn_cw = G.batch_cw;
+    B->p2g_group = tu.p2g_group ? tu.p2g_group : 64;
     *out = B;
     return NSF_OK;
 }
@@ -1290,7 +1314,7 @@ nsf_status nsf_latent_step_batched(const nsf_latent_batch *b, double t0, int nst
         ma.step = step;
         ma.bar = b->mpm_bar;
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_MPM));
-        NSF_CUDA_TRY(launch_mpm_batch(ma, d_status, s));
+        NSF_CUDA_TRY(launch_mpm_batch(ma, b->p2g_group, d_status, s));
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_end : nullptr, NSF_STAGE_MPM));
         NSF_CUDA_TRY(ev(tev, tev ? events->ev_begin : nullptr, NSF_STAGE_GN));
         NSF_CUDA_TRY(launch_jac_batch(b->probs, b->entries, b->cta_entry, b->gn_ctas, b->gn_smem,

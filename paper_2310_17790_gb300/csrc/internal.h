@@ -326,7 +326,8 @@ struct MpmBatchArgs {
     int step;                  // step index within the call (t = t0 + step dt per scene)
     unsigned *bar;             // grid-barrier word, zero before the first launch
 };
-cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int *status, cudaStream_t s);
+// p2g_group: threads per 4^3-block P2G tile, 64 or 128.
+cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int p2g_group, int *status, cudaStream_t s);
 
 // Batched Gauss-Newton (jacobian_tc.cu): one problem per scene, each run by a
 // group of CTAs of one cooperative launch.

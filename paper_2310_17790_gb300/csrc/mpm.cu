@@ -859,12 +859,13 @@ __device__ __forceinline__ P2gLatentArgs latent_args(const BatchSceneDev &sc, in
 // active grid blocks and sample particles), with one grid barrier between
 // phases for the whole batch.  Each scene keeps its own counters, epoch,
 // buckets and fixed-point scales.
+template <int TT>
 __global__ void __launch_bounds__(kThreads, 4)
 k_mpm_batch(MpmBatchArgs b, int *status) {
     __shared__ int off[kMaxBatchScenes + 1];
     __shared__ int s_epoch[kMaxBatchScenes];
-    __shared__ TileSmem<kTileThreadsLatent> sm;
-    constexpr int TT = kTileThreadsLatent, kGroups = kThreads / TT;
+    __shared__ TileSmem<TT> sm;
+    constexpr int kGroups = kThreads / TT;
     const int ns = b.nscenes;
     const int stride = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -1042,10 +1043,15 @@ cudaError_t launch_mpm_latent(const GridWs &g, const GridParams &gp, const P2gLa
                        tap_v, status);
 }
 
-cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int *status, cudaStream_t s) {
+cudaError_t launch_mpm_batch(const MpmBatchArgs &b, int p2g_group, int *status, cudaStream_t s) {
     if (b.nscenes < 1 || b.nscenes > kMaxBatchScenes) return cudaErrorInvalidValue;
-    static const int grid = coop_grid(k_mpm_batch);
-    return launch_coop(k_mpm_batch, grid, s, false, b, status);
+    if (p2g_group == 128) {
+        static const int grid = coop_grid(k_mpm_batch<128>);
+        return launch_coop(k_mpm_batch<128>, grid, s, false, b, status);
+    }
+    if (p2g_group != 64) return cudaErrorInvalidValue;
+    static const int grid = coop_grid(k_mpm_batch<64>);
+    return launch_coop(k_mpm_batch<64>, grid, s, false, b, status);
 }
 
 cudaError_t launch_mpm_full(const GridWs &g, const GridParams &gp, const P2gFullArgs &pa,

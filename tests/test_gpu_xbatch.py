@@ -107,7 +107,7 @@ def _pos_dx(f, za, zb, sc):
     return np.abs(f.fitted(za) - f.fitted(zb)).max() / sc.grid.dx
 
 
-def _batched(nsf, scenes, calls, order=None, nsteps=1):
+def _batched(nsf, scenes, calls, order=None, nsteps=1, tuning=None):
     import torch
     order = list(range(len(scenes))) if order is None else order
     keep, entries, zs = [], [], []
@@ -120,7 +120,8 @@ def _batched(nsf, scenes, calls, order=None, nsteps=1):
         keep += [F, X]
         zs.append((i, z, zp))
         entries.append((F, X, sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid), sc.dt, z, zp))
-    b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping)
+    b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping,
+                        tuning=tuning)
     res = []
     for k in range(calls):
         b.step(t0=0.0, nsteps=nsteps, reuse_prev=k > 0)
@@ -178,6 +179,58 @@ def test_batch_is_reproducible_bit_for_bit(nsf):
         for i in range(len(scenes)):
             np.testing.assert_array_equal(a[call][i][0], b[call][i][0])
             np.testing.assert_array_equal(a[call][i][1], b[call][i][1])
+
+
+def test_tile_choices_step_like_the_default_plan(nsf):
+    """The tuner's choices (nsf_batch_tuning) change tile shapes and the
+    schedule only: 128-thread P2G tiles sum the same exact integers, so the
+    step is identical bit for bit; 128-slot Gauss-Newton tiles and a fixed
+    split threshold group the float-float sums differently, so z stays within
+    the batch tolerance of the default plan's."""
+    scenes = _scenes()
+    base = _batched(nsf, scenes, 2)
+    p2g = _batched(nsf, scenes, 2, tuning={"p2g_group": 128})
+    gn = _batched(nsf, scenes, 2, tuning={"gn_columns": 32, "gn_split": 1.0, "p2g_group": 64})
+    for call in range(2):
+        for i in range(len(scenes)):
+            np.testing.assert_array_equal(p2g[call][i][0], base[call][i][0])
+            np.testing.assert_array_equal(p2g[call][i][1], base[call][i][1])
+            print(f"call {call} scene {i}: |dz| 128-slot tiles vs default "
+                  f"{np.abs(gn[call][i][0] - base[call][i][0]).max():.3e}")
+            assert _close(gn[call][i][0], base[call][i][0]), (call, i)
+
+
+def test_tile_choices_outside_the_lists_are_rejected(nsf):
+    scenes = _scenes()[:2]
+    for bad in ({"gn_columns": 16}, {"p2g_group": 32}, {"gn_split": -1.0}):
+        with pytest.raises(nsf._native.NsfError) as e:
+            _batched(nsf, scenes, 1, tuning=bad)
+        assert e.value.status == nsf._native.NSF_ERR_INVALID_ARG
+
+
+def test_tuner_times_candidates_and_caches_the_winner(nsf, tmp_path):
+    import torch
+    from paper_2310_17790_gb300 import autotune
+    scenes = _scenes()[:3]
+    entries, keep = [], []
+    for sc in scenes:
+        F = nsf.Fields.from_spec(sc.fields)
+        X = soa(sc.X)
+        z = torch.tensor(sc.z0, dtype=torch.float64, device="cuda")
+        zp = torch.tensor(sc.z_prev, dtype=torch.float64, device="cuda")
+        keep += [F, X]
+        entries.append((F, X, sc.n_S, sc.mass, sc.vol0, grid_desc(nsf, sc.grid), sc.dt, z, zp))
+    z_before = [e[7].cpu().numpy().copy() for e in entries]
+    cands = [{"gn_columns": 64, "gn_split": 0.0, "p2g_group": 64},
+             {"gn_columns": 32, "gn_split": 1.0, "p2g_group": 128}]
+    best, ms, results = autotune.tune_batch(entries, candidates=cands, steps=2)
+    assert best in cands and ms > 0 and all(r[1] is not None for r in results)
+    # the caller's latent codes are untouched (the tuner steps copies)
+    for e, zb in zip(entries, z_before):
+        np.testing.assert_array_equal(e[7].cpu().numpy(), zb)
+    cache = autotune.TuningCache(str(tmp_path / "t.json"))
+    cache.put(entries, best, ms)
+    assert autotune.TuningCache(str(tmp_path / "t.json")).get(entries) == best
 
 
 def test_batch_two_steps_in_one_call_match_two_calls(nsf):
