@@ -532,47 +532,77 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
         gd = nsf.grid_desc(sc.grid.n, sc.grid.dx, sc.grid.gravity, sc.grid.wall_cells)
         keep.append((F, X, z, zp))
         entries.append((F, X, sc.n_S, sc.mass, sc.vol0, gd, sc.dt, z, zp))
-    b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping)
-    stream = torch.cuda.Stream(device=dev)
+    codes = [(e[7], e[8], e[7].clone(), e[8].clone()) for e in entries]
     nst = N.NSF_LATENT_STAGES
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
-    with torch.cuda.stream(stream):
-        for e in ev_b + ev_e:
-            e.record(stream)
-    torch.cuda.synchronize()
-    evs = N.nsf_batch_events()
-    for i in range(nst):
-        evs.ev_begin[i] = ev_b[i].cuda_event
-        evs.ev_end[i] = ev_e[i].cuda_event
-    with torch.cuda.stream(stream):
-        b.step(t0=0.0, nsteps=1, stream=stream)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        b.step(t0=0.0, nsteps=1, events=evs, stream=stream, reuse_prev=True)
-    torch.cuda.synchronize()
-    for _ in range(max(3, args.warmup)):
-        graph.replay()
-    torch.cuda.synchronize()
-    assert b.read_status() == 0, nsf.status_string(b.read_status())
     K = max(1, min(args.steps, 100))
-    s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    st_acc = np.zeros(nst)
-    with torch.cuda.stream(stream):
-        for k in range(K):
-            flush.fill_(float(k))
-            s_ev[k].record(stream)
+
+    def measure(tuning):
+        """ms per batched step (mean of K graph replays, L2 flushed before each)
+        and the stage times, for the plan with `tuning` (None: the defaults)."""
+        b = nsf.LatentBatch(entries, iters=scenes[0].gn_iters, damping=scenes[0].damping,
+                            tuning=tuning)
+        for z, zp, z0, zp0 in codes:               # every plan starts from the same codes
+            z.copy_(z0)
+            zp.copy_(zp0)
+        stream = torch.cuda.Stream(device=dev)
+        ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+        ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(nst)]
+        with torch.cuda.stream(stream):
+            for e in ev_b + ev_e:
+                e.record(stream)
+        torch.cuda.synchronize()
+        evs = N.nsf_batch_events()
+        for i in range(nst):
+            evs.ev_begin[i] = ev_b[i].cuda_event
+            evs.ev_end[i] = ev_e[i].cuda_event
+        with torch.cuda.stream(stream):
+            b.step(t0=0.0, nsteps=1, stream=stream)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            b.step(t0=0.0, nsteps=1, events=evs, stream=stream, reuse_prev=True)
+        torch.cuda.synchronize()
+        for _ in range(max(3, args.warmup)):
             graph.replay()
-            e_ev[k].record(stream)
-            if k < 20:
-                torch.cuda.synchronize()
-                st_acc += [ev_b[i].elapsed_time(ev_e[i]) for i in range(nst)]
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(c) for a, c in zip(s_ev, e_ev)) / K
-    st_ms = st_acc / min(K, 20)
-    status = b.read_status()
+        torch.cuda.synchronize()
+        assert b.read_status() == 0, nsf.status_string(b.read_status())
+        s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        st_acc = np.zeros(nst)
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                flush.fill_(float(k))
+                s_ev[k].record(stream)
+                graph.replay()
+                e_ev[k].record(stream)
+                if k < 20:
+                    torch.cuda.synchronize()
+                    st_acc += [ev_b[i].elapsed_time(ev_e[i]) for i in range(nst)]
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(c) for a, c in zip(s_ev, e_ev)) / K
+        st_ms = st_acc / min(K, 20)
+        status = b.read_status()
+        b.close()
+        return ms, st_ms, status
+
+    from paper_2310_17790_gb300 import autotune
+    cache = autotune.TuningCache(args.tuning_cache) if args.tuning_cache else None
+    tuned = cache.get(entries) if cache else None
+    tuner = None
+    if args.tune:
+        best, best_ms, results = autotune.tune_batch(entries, steps=3, iters=scenes[0].gn_iters,
+                                                     damping=scenes[0].damping)
+        for z, zp, z0, zp0 in codes:
+            z.copy_(z0)
+            zp.copy_(zp0)
+        tuned = best
+        if cache is not None and best is not None:
+            cache.put(entries, best, best_ms)
+        tuner = {"signature": autotune.batch_signature(entries),
+                 "timed": [{"tuning": t, "ms_per_step": m} for t, m in results]}
+    ms_default, st_default, status_default = measure(None)
+    ms, st_ms, status = measure(tuned) if tuned else (ms_default, st_default, status_default)
+    status = status or status_default
 
     n_N = np.array([sc.X.shape[0] for sc in scenes], np.float64)
     n_S = np.array([sc.n_S for sc in scenes], np.float64)
@@ -604,7 +634,6 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
                          "achieved": tf(fl_gn, st_ms[2]), "peak": pk,
                          "frac": tf(fl_gn, st_ms[2]) / pk, "work": fl_gn},
     }
-    b.close()
     return {"workload": f"batch-{len(scenes)}scenes-{int(n_N.sum())}N-{int(n_S.sum())}S-bf16",
             "scenes": len(scenes), "n_integration_total": int(n_N.sum()),
             "n_sample_total": int(n_S.sum()), "steps": K, "ms_per_step": ms,
@@ -612,7 +641,13 @@ def run_batched(args, nsf, dev, flush, peaks, peak_src):
             "stages_ms": stages, "roofline": roof, "status": status,
             "launches_per_step": 2 + len({sc.fields.width[0] for sc in scenes}),
             "peak_source": f"measured ({peak_src})",
-            "note": "one CUDA-graph replay of one batched step; L2 flushed between steps"}
+            "tuning": tuned, "default_plan_ms_per_step": ms_default,
+            "default_plan_stages_ms": {names[i]: float(st_default[i]) for i in range(nst)},
+            "tuner": tuner,
+            "note": "one CUDA-graph replay of one batched step; L2 flushed between steps; "
+                    "the plan with the tile choices of the tuning table (paper_2310_17790_gb300/"
+                    "tuning_gb300.json) when it holds this batch's signature, else the "
+                    "default plan"}
 
 
 def run_training(args, nsf, dev, peaks, peak_src):
@@ -620,8 +655,8 @@ def run_training(args, nsf, dev, peaks, peak_src):
     (App. D): 64 snapshots of the 200,000-particle slab from the library's
     full-order step (5 steps apart), minibatches of 65,536 (particle,
     snapshot) pairs, field g of 5 hidden layers x 256 (BF16 forward, backward
-    products with the cotangent split into bf16 hi + lo, FP32 master weights), per-snapshot latent codes r = 6 learned
-    jointly, Adam lr 1e-4.  A step = loss and gradients + Adam on weights and
+    products with the cotangent split into bf16 hi + lo, FP32 master weights),
+    per-snapshot latent codes r = 6 learned jointly, Adam lr 1e-4.  A step = loss and gradients + Adam on weights and
     codes + re-pack of the weights, all through the C ABI."""
     import torch
     from scenes.synthetic import full_config2, make_fields
@@ -903,6 +938,11 @@ def main():
                     help="latent / batched / mlp / training / full / matched: run that part "
                          "alone (profiling runs) and print its JSON")
     ap.add_argument("--batch-scenes", type=int, default=256)
+    ap.add_argument("--tuning-cache", default=os.path.join(ROOT, "paper_2310_17790_gb300",
+                                                           "tuning_gb300.json"),
+                    help="JSON table of batch tile choices by batch signature ('' for none)")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the tuner's candidates on the batch and record the winner")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
