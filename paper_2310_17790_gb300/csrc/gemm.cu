@@ -1573,14 +1573,6 @@ cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, 
     return cudaGetLastError();
 }
 
-cudaError_t reduce_slabs_t(const float *slab, int slices, int A, int C, float *out,
-                           cudaStream_t s) {
-    const long long count = (long long)A * C;
-    if (count <= 0) return cudaSuccess;
-    k_reduce_slabs_t<<<(int)((count + 31) / 32), 256, 0, s>>>(slab, slices, A, C, out);
-    return cudaGetLastError();
-}
-
 // Few outputs over many slabs (the bias column sums): first sums of groups of
 // rows in place, one CTA per group, then the sum of the groups' results.
 // The slab is overwritten.

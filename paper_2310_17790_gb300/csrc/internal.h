@@ -264,9 +264,7 @@ cudaError_t reduce_slabs(float *slab, int slices, long long count, float *out, c
 // (slab[z][n][m] -> out_w[m N + n], bslab[z][m] -> out_b[m], out_b may be null).
 cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, int N,
                       float *out_w, float *out_b, cudaStream_t s);
-// The same sums transposed: slab[z][a][c] (count A C) -> out[c * A + a].
-cudaError_t reduce_slabs_t(const float *slab, int slices, int A, int C, float *out,
-                           cudaStream_t s);
+
 
 // --------------------------------------------------------------- training ---
 // Workspace of one loss/gradient evaluation (train.cu).
