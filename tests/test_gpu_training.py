@@ -86,7 +86,8 @@ def _gpu_loss_grad(nsf, F, k, X, z, code, target):
     ("fp32", "g", 64, 3, 6, 1000), ("fp32", "h", 64, 4, 6, 1000), ("fp32", "l", 128, 2, 6, 1000),
     ("bf16", "g", 128, 5, 6, 1000), ("bf16", "h", 64, 3, 6, 1000),
     ("bf16", "l", 192, 3, 6, 1000), ("bf16", "g", 256, 1, 16, 777),
-    ("bf16", "h", 64, 4, 16, 129), ("bf16", "g", 256, 3, 3, 2049)])
+    ("bf16", "h", 64, 4, 16, 129), ("bf16", "g", 256, 3, 3, 2049),
+    ("bf16", "g", 128, 3, 6, 1), ("bf16", "l", 256, 2, 6, 3)])
 def test_loss_and_gradients_match_oracle(nsf, precision, k, width, depth, r, n):
     spec = _spec(7, precision, r=r, width=width, depth=depth)
     F = nsf.Fields.from_spec(spec)
@@ -103,6 +104,26 @@ def test_loss_and_gradients_match_oracle(nsf, precision, k, width, depth, r, n):
     assert abs(L - L_o) <= (1e-5 if precision == "fp32" else 1e-3) * L_o
     assert rel(gw, gw_o) < tol
     assert rel(gz, gz_o) < tol
+
+
+def test_loss_grad_rejects_an_empty_batch(nsf):
+    """n = 0 points through the C ABI itself: an argument error, nothing enqueued."""
+    import torch
+    spec = _spec(23, "bf16", width=128, depth=3)
+    F = nsf.Fields.from_spec(spec)
+    X, z, code, target = _data(24, 4, spec.r, 2, ofields.OUT_DIM["g"], "g")
+    field = nsf.FIELD_INDEX["g"]
+    nw = nsf.nsf_field_weight_count(F, field)
+    Xd, td = soa(X), soa(target)
+    cd, zd = torch.from_numpy(code).cuda(), torch.from_numpy(z).cuda()
+    loss, gw = torch.zeros(1, device="cuda"), torch.empty(nw, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.zeros(nsf.nsf_train_workspace_size(F, field, 4), dtype=torch.uint8, device="cuda")
+    rc = nsf._native.lib.nsf_field_loss_grad(F.handle, field, Xd.data_ptr(), cd.data_ptr(),
+                                             td.data_ptr(), 0, zd.data_ptr(), zd.shape[0],
+                                             loss.data_ptr(), gw.data_ptr(), None, ws.data_ptr(),
+                                             ws.numel(), st.data_ptr(), None)
+    assert rc == nsf._native.NSF_ERR_INVALID_ARG
 
 
 def test_bf16_weight_gradients_are_reproducible_bit_for_bit(nsf):
