@@ -859,11 +859,15 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
                 const float4 v = *reinterpret_cast<const float4 *>(Bs + pl * NK + k4);
                 b[k4] = v.x; b[k4 + 1] = v.y; b[k4 + 2] = v.z; b[k4 + 3] = v.w;
             }
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            // packed f32x2 FMAs (each lane rounds as fmaf does)
+            float2 acc01 = make_float2(0.f, 0.f), acc23 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < NK; ++k)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[u] = fmaf(a[k][u], b[k], acc[u]);
+            for (int k = 0; k < NK; ++k) {
+                const float2 bb = make_float2(b[k], b[k]);
+                acc01 = __ffma2_rn(make_float2(a[k][0], a[k][1]), bb, acc01);
+                acc23 = __ffma2_rn(make_float2(a[k][2], a[k][3]), bb, acc23);
+            }
+            const float acc[4] = {acc01.x, acc01.y, acc23.x, acc23.y};
             const size_t i = (size_t)(p_beg + pl) * e.ld + m;
             if (EPI == kEpiBiasElu) {
                 uint32_t c0, c1, h0, h1;
@@ -888,10 +892,14 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
                 if (outer) {
                     const float h[4] = {__uint_as_float(hv.x << 16), __uint_as_float(hv.x & 0xFFFF0000u),
                                         __uint_as_float(hv.y << 16), __uint_as_float(hv.y & 0xFFFF0000u)};
+                    const float2 h01 = make_float2(h[0], h[1]), h23 = make_float2(h[2], h[3]);
 #pragma unroll
-                    for (int k = 0; k < NO; ++k)
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) ot[k][u] = fmaf(b[k], h[u], ot[k][u]);
+                    for (int k = 0; k < NO; ++k) {
+                        const float2 bb = make_float2(b[k], b[k]);
+                        const float2 o01 = __ffma2_rn(bb, h01, make_float2(ot[k][0], ot[k][1]));
+                        const float2 o23 = __ffma2_rn(bb, h23, make_float2(ot[k][2], ot[k][3]));
+                        ot[k][0] = o01.x; ot[k][1] = o01.y; ot[k][2] = o23.x; ot[k][3] = o23.y;
+                    }
                 }
             }
         }
@@ -931,6 +939,7 @@ k_thin_k(int M, int N, int K, const MatView A, const MatView B, const GemmEpilog
 // and at the end the four quarters' sums are added in order and written once
 // as the CTA's slab in the gradient layout [W0 (W x K0) | b0].
 constexpr int kIbPoints = 64, kIbThreads = 256, kIbRow = 8 * 33 + 1, kIbMaxGrid = 320;
+constexpr int kIbLoads = 4;   // 16-byte pieces of delta_0 per thread and load round
 __host__ __device__ inline int ib_k0p(int K0) { return (K0 + 3) / 4 * 4; }
 __host__ __device__ inline size_t ib_smem(int K0) {
     const int k0p = ib_k0p(K0);
@@ -965,19 +974,41 @@ k_input_bwd(int n, int W, int K0, const __nv_bfloat16 *__restrict__ dhi,
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int p0 = tile * kIbPoints;
         __syncthreads();                 // the previous tile is no longer read
-        for (int q = tid; q < kIbPoints * w8; q += kIbThreads) {
-            const int pt = q / w8, c8 = (q % w8) * 8, p = p0 + pt;
-            float v[8];
-            if (p < n) {
+        // the tile's 8-channel pieces (kIbPoints * w8 = 8 W of them, a multiple
+        // of the block size) in rounds of four per thread: a round's loads
+        // are all issued before any of them is converted and stored
+        for (int q0 = 0; q0 < kIbPoints * w8; q0 += kIbLoads * kIbThreads) {
+            uint4 ra[kIbLoads], rb[kIbLoads];
+#pragma unroll
+            for (int i = 0; i < kIbLoads; ++i) {
+                const int q = q0 + i * kIbThreads + tid;
+                const int pt = q / w8, c8 = (q % w8) * 8, p = p0 + pt;
+                ra[i] = rb[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (q < kIbPoints * w8 && p < n) {
+                    if (d32) {
+                        ra[i] = *reinterpret_cast<const uint4 *>(d32 + (size_t)p * ld + c8);
+                        rb[i] = *reinterpret_cast<const uint4 *>(d32 + (size_t)p * ld + c8 + 4);
+                    } else {
+                        ra[i] = __ldg(reinterpret_cast<const uint4 *>(dhi + (size_t)p * ld + c8));
+                        rb[i] = __ldg(reinterpret_cast<const uint4 *>(dlo + (size_t)p * ld + c8));
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kIbLoads; ++i) {
+                const int q = q0 + i * kIbThreads + tid;
+                if (q >= kIbPoints * w8) break;
+                const int pt = q / w8, c8 = (q % w8) * 8;
+                float v[8];
                 if (d32) {
-                    const float4 x = *reinterpret_cast<const float4 *>(d32 + (size_t)p * ld + c8);
-                    const float4 y = *reinterpret_cast<const float4 *>(d32 + (size_t)p * ld + c8 + 4);
-                    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-                    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+                    v[0] = __uint_as_float(ra[i].x); v[1] = __uint_as_float(ra[i].y);
+                    v[2] = __uint_as_float(ra[i].z); v[3] = __uint_as_float(ra[i].w);
+                    v[4] = __uint_as_float(rb[i].x); v[5] = __uint_as_float(rb[i].y);
+                    v[6] = __uint_as_float(rb[i].z); v[7] = __uint_as_float(rb[i].w);
                 } else {
-                    const uint4 h = __ldg(reinterpret_cast<const uint4 *>(dhi + (size_t)p * ld + c8));
-                    const uint4 l = __ldg(reinterpret_cast<const uint4 *>(dlo + (size_t)p * ld + c8));
-                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+                    // bf16 hi + lo pairs (zero pairs past n give zero)
+                    const uint32_t hw[4] = {ra[i].x, ra[i].y, ra[i].z, ra[i].w},
+                                   lw[4] = {rb[i].x, rb[i].y, rb[i].z, rb[i].w};
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         v[2 * t] = __uint_as_float(hw[t] << 16) + __uint_as_float(lw[t] << 16);
@@ -985,13 +1016,10 @@ k_input_bwd(int n, int W, int K0, const __nv_bfloat16 *__restrict__ dhi,
                                        __uint_as_float(lw[t] & 0xFFFF0000u);
                     }
                 }
-            } else {
+                float *dst = sd + pt * kIbRow + (c8 >> 5) * 33 + (c8 & 31);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) v[t] = 0.f;
+                for (int t = 0; t < 8; ++t) dst[t] = v[t];
             }
-            float *dst = sd + pt * kIbRow + (c8 >> 5) * 33 + (c8 & 31);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) dst[t] = v[t];
         }
         for (int q = tid; q < kIbPoints * k0p; q += kIbThreads) {
             const int pt = q / k0p, j = q % k0p, p = p0 + pt;
