@@ -29,6 +29,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "tc_common.cuh"
 
 namespace nsf {
@@ -1553,51 +1555,74 @@ cudaError_t thin_k(int M, int N, int K, const MatView &A, const MatView &B,
     return cudaGetLastError();
 }
 
+// Element-wise accumulation of float or float4 values (same order per element).
+template <class T> __device__ __forceinline__ T vzero();
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vadd(float &a, float b) { a += b; }
+__device__ __forceinline__ void vadd(float4 &a, const float4 &b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+
 // Weight and bias gradients of a hidden layer from the K-slices of the
 // weight-gradient product: slab[z][n][m] (z < slices, n < N, m < M) ->
 // out_w[m N + n] and bslab[z][m] -> out_b[m], each a fixed-order sum over z.
-// A CTA takes 32 consecutive slab entries (coalesced reads), 8 groups of
-// slices each, then a shared sum in group order; the CTAs past the M N / 32
-// of the weights do the same for the bias slab.
+// A CTA takes 32 V consecutive slab entries (a lane V of them, coalesced
+// reads), 8 groups of slices each, then a shared sum in group order; the
+// CTAs past the M N / (32 V) of the weights do the same for the bias slab.
+// V = 4 needs M % 4 == 0 and 16-byte aligned slabs.
+template <int V>
 __global__ void k_reduce_dw(const float *__restrict__ slab, const float *__restrict__ bslab,
                             int slices, int M, int N, float *out_w, float *out_b) {
-    __shared__ float part[8][33];
+    using Vec = typename std::conditional<V == 4, float4, float>::type;
+    __shared__ Vec part[8][33];
     const int ix = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const long long count = (long long)M * N, wblocks = (count + 31) / 32;
+    const long long count = (long long)M * N, wblocks = (count + 32 * V - 1) / (32 * V);
     const bool bias = blockIdx.x >= wblocks;
-    const long long i = (bias ? blockIdx.x - wblocks : blockIdx.x) * 32 + ix;
+    const long long i = ((bias ? blockIdx.x - wblocks : blockIdx.x) * 32 + ix) * V;
     const long long cnt = bias ? M : count;
     const float *src = bias ? bslab : slab;
-    float s = 0.f;
+    auto ld = [&](int z) { return *reinterpret_cast<const Vec *>(src + (size_t)z * cnt + i); };
+    Vec s = vzero<Vec>();
     if (i < cnt) {
         int z = g;
         for (; z + 24 < slices; z += 32) {
-            const float a = src[(size_t)z * cnt + i], b = src[(size_t)(z + 8) * cnt + i];
-            const float c = src[(size_t)(z + 16) * cnt + i], d = src[(size_t)(z + 24) * cnt + i];
-            s += a;
-            s += b;
-            s += c;
-            s += d;
+            const Vec a = ld(z), b = ld(z + 8), c = ld(z + 16), d = ld(z + 24);
+            vadd(s, a);
+            vadd(s, b);
+            vadd(s, c);
+            vadd(s, d);
         }
-        for (; z < slices; z += 8) s += src[(size_t)z * cnt + i];
+        for (; z < slices; z += 8) vadd(s, ld(z));
     }
     part[g][ix] = s;
     __syncthreads();
     if (g == 0 && i < cnt) {
-        float t = 0.f;
+        Vec t = vzero<Vec>();
 #pragma unroll
-        for (int q = 0; q < 8; ++q) t += part[q][ix];
-        if (bias) out_b[i] = t;
-        else out_w[(size_t)(i % M) * N + i / M] = t;
+        for (int q = 0; q < 8; ++q) vadd(t, part[q][ix]);
+        const float *tv = reinterpret_cast<const float *>(&t);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            if (bias) out_b[i + u] = tv[u];
+            else out_w[(size_t)((i + u) % M) * N + (i + u) / M] = tv[u];
+        }
     }
 }
 
 cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, int N,
                       float *out_w, float *out_b, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    const long long wblocks = ((long long)M * N + 31) / 32;
-    const int blocks = (int)wblocks + (out_b ? (M + 31) / 32 : 0);
-    k_reduce_dw<<<blocks, 256, 0, s>>>(slab, bslab, slices, M, N, out_w, out_b);
+    const bool vec = M % 4 == 0 && ((uintptr_t)slab % 16) == 0 &&
+                     (out_b == nullptr || ((uintptr_t)bslab % 16) == 0);
+    const int V = vec ? 4 : 1;
+    const long long wblocks = ((long long)M * N + 32 * V - 1) / (32 * V);
+    const int blocks = (int)wblocks + (out_b ? (M + 32 * V - 1) / (32 * V) : 0);
+    if (vec) k_reduce_dw<4><<<blocks, 256, 0, s>>>(slab, bslab, slices, M, N, out_w, out_b);
+    else k_reduce_dw<1><<<blocks, 256, 0, s>>>(slab, bslab, slices, M, N, out_w, out_b);
     return cudaGetLastError();
 }
 
