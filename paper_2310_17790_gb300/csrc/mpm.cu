@@ -157,16 +157,27 @@ struct Stencil {
     Axis ax, ay, az;
 };
 
-__device__ __forceinline__ float4 node_contribution(const P2gParticle &q, const Stencil &s,
-                                                    float mass, float dx, int a, int b, int c) {
+// The same with the weight w of node (a, b, c) given.
+__device__ __forceinline__ float4 node_contribution_w(const P2gParticle &q, const Stencil &s,
+                                                      float mass, float dx, int a, int b, int c,
+                                                      float w) {
     const float dxa = ((float)a - s.ax.fx) * dx;
     const float dyb = ((float)b - s.ay.fx) * dx;
     const float dzc = ((float)c - s.az.fx) * dx;
-    const float w = s.ax.w[a] * s.ay.w[b] * s.az.w[c];
     const float px = q.mv[0] + q.Q[0] * dxa + q.Q[1] * dyb + q.Q[2] * dzc;
     const float py = q.mv[1] + q.Q[3] * dxa + q.Q[4] * dyb + q.Q[5] * dzc;
     const float pz = q.mv[2] + q.Q[6] * dxa + q.Q[7] * dyb + q.Q[8] * dzc;
     return make_float4(w * mass, w * px, w * py, w * pz);
+}
+
+__device__ __forceinline__ float4 node_contribution(const P2gParticle &q, const Stencil &s,
+                                                    float mass, float dx, int a, int b, int c) {
+    return node_contribution_w(q, s, mass, dx, a, b, c, s.ax.w[a] * s.ay.w[b] * s.az.w[c]);
+}
+
+// w[i] by selects (i need not be a compile-time constant).
+__device__ __forceinline__ float pick3(const float (&w)[3], int i) {
+    return i == 0 ? w[0] : (i == 1 ? w[1] : w[2]);
 }
 
 // ------------------------------------------------------- fixed point ----
@@ -377,6 +388,33 @@ __device__ __forceinline__ void tile_add_particle(const GridWs &g, const GridPar
             }
 }
 
+// Node nidx = 9 a + 3 b + c of particle p's stencil added to the tile: the
+// work of tile_add_particle spread over 27 lanes, for blocks with few
+// particles (the same contributions, so the same integer sums).
+__device__ __forceinline__ void tile_add_node(const GridWs &g, const GridParams &gp, float mass,
+                                              const FixScales &fs, int p, int nidx, int ox,
+                                              int oy, int oz, uint32_t tile, int *status) {
+    P2gParticle q;
+    unpack_record(g.rec, p, q);
+    const Stencil s{bspline_axis(q.x[0], gp.inv_dx), bspline_axis(q.x[1], gp.inv_dx),
+                    bspline_axis(q.x[2], gp.inv_dx)};
+    const int lx = s.ax.base - ox, ly = s.ay.base - oy, lz = s.az.base - oz;   // 0 .. 3
+    if ((unsigned)lx > 3u || (unsigned)ly > 3u || (unsigned)lz > 3u) {
+        set_status(status, NSF_ERR_OUT_OF_GRID);
+        return;
+    }
+    const int ia = nidx / 9, ib = (nidx / 3) % 3, ic = nidx % 3;
+    const float4 c = node_contribution_w(q, s, mass, gp.dx, ia, ib, ic,
+                                         pick3(s.ax.w, ia) * pick3(s.ay.w, ib) * pick3(s.az.w, ic));
+    const int l = ((lx + ia) * 6 + (ly + ib)) * 6 + (lz + ic);
+    constexpr uint32_t W = 4u * kTileNodes;          // bytes per word array
+    const uint32_t n = tile + 4u * (uint32_t)l;
+    red_shared_split(n, n + W, c.x, fs.m);
+    red_shared_split(n + 2u * W, n + 3u * W, c.y, fs.p);
+    red_shared_split(n + 4u * W, n + 5u * W, c.z, fs.p);
+    red_shared_split(n + 6u * W, n + 7u * W, c.w, fs.p);
+}
+
 // Particle p's 27 contributions straight into the grid's fixed-point sums
 // (particles past their block's bucket capacity).
 __device__ __forceinline__ void grid_add_particle(const GridWs &g, const GridParams &gp,
@@ -412,8 +450,13 @@ __device__ __forceinline__ void group_sync(int bar_id) {
 // P2G of particle block `key`: its particles' contributions summed in the
 // tile (shared memory, exact integer sums), then every node of the tile with
 // a nonzero sum added once to the grid (integer atomics, so the order in
-// which tiles meet on their shared halo nodes does not matter).
-template <int TT>
+// which tiles meet on their shared halo nodes does not matter).  kSparse
+// (the batched step, whose scenes leave most blocks with a few particles):
+// blocks of at most 4 TT / 27 particles take one lane per (particle, node)
+// instead of one lane per particle (batched MPM 2.04 -> 1.74 ms; the
+// single-scene latent step measured 1.4 us slower with it and keeps the
+// per-particle lanes).
+template <int TT, bool kSparse>
 __device__ __forceinline__ void tile_block(const GridWs &g, const GridParams &gp, float mass,
                                            const FixScales &fs, int key, int epoch,
                                            unsigned long long *tile, int gt, int bar_id,
@@ -425,8 +468,15 @@ __device__ __forceinline__ void tile_block(const GridWs &g, const GridParams &gp
     const int np = min(__ldcg(&g.bcount[key]), g.cap);
     const int *bk = g.bucket + (size_t)key * g.cap;
     const uint32_t ts = (uint32_t)__cvta_generic_to_shared(tile);
-    for (int k = gt; k < np; k += TT)
-        tile_add_particle(g, gp, mass, fs, __ldcg(&bk[k]), ox, oy, oz, ts, status);
+    if (kSparse && np * 27 <= 4 * TT) {
+        for (int w = gt; w < np * 27; w += TT) {
+            const int k = w / 27;
+            tile_add_node(g, gp, mass, fs, __ldcg(&bk[k]), w - 27 * k, ox, oy, oz, ts, status);
+        }
+    } else {
+        for (int k = gt; k < np; k += TT)
+            tile_add_particle(g, gp, mass, fs, __ldcg(&bk[k]), ox, oy, oz, ts, status);
+    }
     group_sync<TT>(bar_id);
     if (gt < 8) activate_grid_block(g, kx, ky, kz, gt, epoch);
     const unsigned *tw = reinterpret_cast<const unsigned *>(tile);
@@ -466,7 +516,7 @@ struct __align__(16) TileSmem {
 
 // P2G phase of a single scene: every listed particle block's tile, then the
 // overflow particles.
-template <int TT>
+template <int TT, bool kSparse>
 __device__ void phase_p2g(const GridWs &g, const GridParams &gp, float mass, int epoch,
                           TileSmem<TT> &sm, int *status) {
     const StepCtl &st = g.ctl->st[epoch & 1];
@@ -477,7 +527,7 @@ __device__ void phase_p2g(const GridWs &g, const GridParams &gp, float mass, int
     // group w of CTA c takes blocks w * gridDim.x + c, + all groups: a short
     // list still spreads over every SM
     for (int q = grp * gridDim.x + blockIdx.x; q < n_p; q += kGroups * gridDim.x)
-        tile_block<TT>(g, gp, mass, fs, __ldcg(&g.plist[q]), epoch, sm.tile[grp], gt, 1 + grp,
+        tile_block<TT, kSparse>(g, gp, mass, fs, __ldcg(&g.plist[q]), epoch, sm.tile[grp], gt, 1 + grp,
                        status);
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_over; u += gridDim.x * blockDim.x)
         grid_add_particle(g, gp, mass, fs, __ldcg(&g.over[u]));
@@ -598,7 +648,7 @@ __device__ __forceinline__ int begin_step(const GridWs &g) {
 // barrier timed out.  After the first barrier (every CTA has read the old
 // epoch) CTA 0 publishes the step's epoch, which later launches of the step
 // read.
-template <int TT, class Args>
+template <int TT, bool kSparse, class Args>
 __device__ bool bin_p2g_grid(const GridWs &g, const GridParams &gp, const Args &a, double t,
                              int epoch, float *tap_mp, float *tap_v, int *status) {
     __shared__ TileSmem<TT> sm;
@@ -607,7 +657,7 @@ __device__ bool bin_p2g_grid(const GridWs &g, const GridParams &gp, const Args &
     if (!grid_barrier(&g.ctl->bar, status)) return false;
     if (cta0_thread0()) g.ctl->epoch = epoch;
     const StepCtl &st = g.ctl->st[epoch & 1];
-    phase_p2g<TT>(g, gp, a.mass, epoch, sm, status);
+    phase_p2g<TT, kSparse>(g, gp, a.mass, epoch, sm, status);
     if (!grid_barrier(&g.ctl->bar, status)) return false;
     phase_grid(g, gp, a.mass, a.dt, t, st, tap_mp, tap_v);
     return true;
@@ -752,7 +802,7 @@ k_mpm_latent(GridWs g, GridParams gp, P2gLatentArgs a, int n_S, double t, float 
              float *tap_mp, float *tap_v, int *status) {
     pdl_wait();
     const int epoch = begin_step(g);
-    if (!bin_p2g_grid<kTileThreadsLatent>(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
+    if (!bin_p2g_grid<kTileThreadsLatent, false>(g, gp, a, t, epoch, tap_mp, tap_v, status)) return;
     if (!grid_barrier(&g.ctl->bar, status)) return;
     phase_g2p_latent(g, gp, a.X, a.u, a.n, n_S, a.dt, d_next, status);
     clear_bins(g, g.ctl->st[epoch & 1]);
@@ -762,7 +812,7 @@ __global__ void __launch_bounds__(kThreads)
 k_mpm_full(GridWs g, GridParams gp, P2gFullArgs a, double t, float *tap_mp, float *tap_v,
            int *status) {
     const int epoch = begin_step(g);
-    bin_p2g_grid<kTileThreadsFull>(g, gp, a, t, epoch, tap_mp, tap_v, status);
+    bin_p2g_grid<kTileThreadsFull, false>(g, gp, a, t, epoch, tap_mp, tap_v, status);
 }
 
 // Full-order G2P, one thread per particle; it also clears the step's bucket
@@ -901,7 +951,7 @@ k_mpm_batch(MpmBatchArgs b, int *status) {
             const BatchSceneDev &sc = b.scenes[sidx];
             const StepCtl &st = sc.g.ctl->st[s_epoch[sidx] & 1];
             const FixScales fs = fix_scales(sc.mass, __ldcg(&st.bound));
-            tile_block<TT>(sc.g, sc.gp, sc.mass, fs, __ldcg(&sc.g.plist[q - off[sidx]]),
+            tile_block<TT, true>(sc.g, sc.gp, sc.mass, fs, __ldcg(&sc.g.plist[q - off[sidx]]),
                            s_epoch[sidx], sm.tile[grp], gt, 1 + grp, status);
         }
     }
