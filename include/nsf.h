@@ -315,7 +315,9 @@ nsf_status nsf_project_static(const nsf_fields *fields, const float *d_X_S,
  * backward products of the hidden layers multiply the bf16 weights and
  * activations by the cotangent split into two bf16 parts (hi + lo, ~16
  * significant bits) on the tensor cores, FP32 accumulation.  Every product is
- * one of the library's own kernels (no BLAS library).
+ * one of the library's own kernels (no BLAS library).  Every sum over points
+ * (the loss, the weight and bias gradients, dL/dz) is taken in a fixed order,
+ * so the same inputs give the same results bit for bit.
  * A negative code[p] sets NSF_ERR_INVALID_ARG in *d_status.
  *
  * nsf_adam_step: one Adam step (Kingma and Ba 2014; App. D) on count float32

@@ -271,6 +271,7 @@ cudaError_t reduce_dw(const float *slab, const float *bslab, int slices, int M, 
 struct TrainLayout {
     size_t inp, dinp, A[kMaxDepth], H[kMaxDepth], H16[kMaxDepth], raw, dout, d1, d2, ones, slab,
         dh[2], dl[2], Wb[kMaxDepth], WTb[kMaxDepth], total;
+    size_t slab_floats;   // size of the slab region in floats
 };
 TrainLayout train_layout(int r, int W, int D, int od, int n);
 cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const int *code,

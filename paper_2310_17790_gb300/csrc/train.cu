@@ -58,7 +58,7 @@ __global__ void k_inputs(const float *__restrict__ X, const int *__restrict__ co
 // partials) into dbias_part[blockIdx.x][od].
 __global__ void k_loss(const float *__restrict__ raw, const float *__restrict__ bout,
                        const float *__restrict__ X, const float *__restrict__ target, int n,
-                       int od, FieldDev F, int residual, float *delta, float *loss,
+                       int od, FieldDev F, int residual, float *delta, float *loss_part,
                        float *dbias_part) {
     __shared__ float part[kT];
     __shared__ float dsum[kT / 32][9];
@@ -98,7 +98,7 @@ __global__ void k_loss(const float *__restrict__ raw, const float *__restrict__ 
         if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(loss, part[0] / ((float)n * (float)od));
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = part[0] / ((float)n * (float)od);
 }
 
 __global__ void k_fill(float *a, float v, int count) {
@@ -106,29 +106,51 @@ __global__ void k_fill(float *a, float v, int count) {
     if (i < count) a[i] = v;
 }
 
-// dz_code(p) += dinp[3:, p]: per CTA into a shared copy of the table (when it
-// fits), then one global atomic per entry the CTA touched.
-constexpr int kDzShared = 4096;
-__global__ void k_scatter_dz(const float *__restrict__ dinp, const int *__restrict__ code, int n,
-                             int r, int n_codes, float *gz) {
+constexpr int kDzShared = 4096;   // floats of a CTA's code table
+
+// dz_code(p) summed over the points p with that code, in a fixed order, for
+// the codes [c0, c0 + nc) (nc r <= kDzShared): CTA b takes the points
+// [b per, (b + 1) per) in rounds of 256; in a round the lanes of a warp with
+// the same code add their values in lane order (shuffles) and the warps then
+// add their sums to the CTA's table in warp order.  The CTA writes its table
+// to part[b][nc r]; the tables are then added in CTA order (reduce_slabs).
+__global__ void __launch_bounds__(kT)
+k_scatter_dz(const float *__restrict__ dinp, const int *__restrict__ code, int n, int r, int c0,
+             int nc, int per, float *part) {
     __shared__ float tab[kDzShared];
-    const bool local = n_codes * r <= kDzShared;
-    if (local)
-        for (int i = threadIdx.x; i < n_codes * r; i += blockDim.x) tab[i] = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p_beg = blockIdx.x * per, p_end = min(n, p_beg + per);
+    for (int i = threadIdx.x; i < nc * r; i += kT) tab[i] = 0.f;
     __syncthreads();
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int c = code[p];
-        if (c < 0 || c >= n_codes) continue;
-        for (int k = 0; k < r; ++k) {
-            const float v = dinp[(size_t)p * (3 + r) + 3 + k];
-            if (local) atomicAdd(&tab[c * r + k], v);
-            else atomicAdd(&gz[(size_t)c * r + k], v);
+    for (int base = p_beg; base < p_end; base += kT) {
+        const int p = base + threadIdx.x;
+        int c = -1;
+        if (p < p_end) {
+            c = code[p] - c0;
+            if (c < 0 || c >= nc) c = -1;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const bool leader = c >= 0 && lane == __ffs(peers) - 1;
+        float sum[NSF_MAX_R];
+#pragma unroll
+        for (int k = 0; k < NSF_MAX_R; ++k) {
+            sum[k] = 0.f;
+            if (k < r) {
+                const float v = c >= 0 ? dinp[(size_t)p * (3 + r) + 3 + k] : 0.f;
+                for (unsigned m = peers; m; m &= m - 1u)
+                    sum[k] += __shfl_sync(peers, v, __ffs(m) - 1);
+            }
+        }
+        for (int w = 0; w < kT / 32; ++w) {
+            if (warp == w && leader)
+#pragma unroll
+                for (int k = 0; k < NSF_MAX_R; ++k)
+                    if (k < r) tab[c * r + k] += sum[k];
+            __syncthreads();
         }
     }
-    if (!local) return;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_codes * r; i += blockDim.x)
-        if (tab[i] != 0.f) atomicAdd(&gz[i], tab[i]);
+    float *dst = part + (size_t)blockIdx.x * nc * r;
+    for (int i = threadIdx.x; i < nc * r; i += kT) dst[i] = tab[i];
 }
 
 // bf16 copies of a hidden layer's weights from its transposed FP32 copy
@@ -285,13 +307,14 @@ TrainLayout train_layout(int r, int W, int D, int od, int n) {
     const size_t thin_a = (size_t)(3 + r > od ? 3 + r : od);
     size_t slab = (size_t)kMaxSlices * W * (W + 1);     // weight and bias gradient slabs
     slab = slab > (size_t)kMaxThinSlices * thin_a * W ? slab : (size_t)kMaxThinSlices * thin_a * W;
-    const size_t loss_parts = (nn + kT - 1) / kT * (size_t)od;
+    const size_t loss_parts = (nn + kT - 1) / kT * (size_t)(od + 1);   // + the loss partials
     // per-CTA partial sums: bias columns and the output layer's outer products
     // (thin_k, one part per 128 points), the input layer's slabs (at most 320)
     const size_t col_parts = ((nn + 127) / 128) * (size_t)(od + 1) * W + 320 * (size_t)W * (4 + r);
     slab = slab > loss_parts ? slab : loss_parts;
     slab = slab > col_parts ? slab : col_parts;
     L.slab = take(slab * 4);
+    L.slab_floats = slab;
     L.total = o;
     return L;
 }
@@ -311,12 +334,6 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     const MatView ones = view(P(L.ones), 0, 0, 0);
     const int ks_thin = thin_slices(n);
 #define NSF_GT(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return e_; } while (0)
-    // a hidden W x W product: tensor cores for BF16 fields, CUDA cores for FP32
-    auto hidden = [&](int M, int N, int K, const MatView &A, const MatView &B, int split,
-                      const GemmEpilogue &e, int slices) {
-        return b16 ? gemm_tc(M, N, K, A, B, split, e, slices, status, s)
-                   : gemm_simt(M, N, K, A, B, e, slices, s);
-    };
     // sum over all n points (K) of an M x N product into dst, by K slices
     // (on the tensor cores, with bias_dst: also bias_dst[m] = sum over the n
     // points of A(m, .), from a product of A with ones)
@@ -389,9 +406,12 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
     }
     NSF_GT(thin_m(od, n, W, view(F.Wout, W, 1, 0), Hlast_rows, P(L.raw), od, s));
     // ---- loss, dL/draw and the output bias gradient
-    NSF_GT(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    // the per-CTA loss partials sit after the output-bias partials and are
+    // added in CTA order before the slab is reused
+    float *loss_part = slab + (size_t)blocks(n) * od;
     k_loss<<<blocks(n), kT, 0, s>>>(P(L.raw), F.b[D], X, target, n, od, F, residual ? 1 : 0,
-                                    P(L.dout), loss, slab);
+                                    P(L.dout), loss_part, slab);
+    NSF_GT(reduce_slabs(loss_part, blocks(n), 1, loss, s));
     k_fill<<<1, 32, 0, s>>>(P(L.ones), 1.f, 4);
     // ---- backward; gradient offsets in the flat layout
     std::vector<size_t> goff(D + 1);
@@ -473,11 +493,23 @@ cudaError_t run_loss_grad(const FieldsDev &fd, int field, const float *X, const 
                           grad_w + goff[0], true, s));
     }
     if (grad_z) {
-        NSF_GT(cudaMemsetAsync(grad_z, 0, (size_t)n_codes * r * sizeof(float), s));
         if (!b16)
             NSF_GT(thin_m(K0, n, W, view(F.W0, 1, K0, 0), view(dcur, W, 1, 0), P(L.dinp), K0, s));
-        k_scatter_dz<<<blocks(n) < 304 ? blocks(n) : 304, kT, 0, s>>>(P(L.dinp), code, n, r,
-                                                                   n_codes, grad_z);
+        // the codes in windows that fit the kernel's shared table; the slab
+        // (free again) holds the CTAs' tables of a window
+        const int win = kDzShared / r;
+        for (int c0 = 0; c0 < n_codes; c0 += win) {
+            const int nc = n_codes - c0 < win ? n_codes - c0 : win;
+            long long g = (long long)(L.slab_floats / ((size_t)nc * r));
+            g = g < 304 ? g : 304;
+            g = g < blocks(n) ? g : blocks(n);
+            g = g < 1 ? 1 : g;
+            const int per = (int)((n + g - 1) / g);
+            const int grid = (n + per - 1) / per;
+            k_scatter_dz<<<grid, kT, 0, s>>>(P(L.dinp), code, n, r, c0, nc, per, slab);
+            NSF_GT(cudaGetLastError());
+            NSF_GT(reduce_slabs(slab, grid, (long long)nc * r, grad_z + (size_t)c0 * r, s));
+        }
     }
 #undef NSF_GT
     return cudaGetLastError();

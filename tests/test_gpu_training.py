@@ -126,16 +126,19 @@ def test_loss_grad_rejects_an_empty_batch(nsf):
     assert rc == nsf._native.NSF_ERR_INVALID_ARG
 
 
-def test_bf16_weight_gradients_are_reproducible_bit_for_bit(nsf):
-    """Every sum behind the weight gradient (slabs, bias column sums, the
-    input layer's per-CTA partials) runs in a fixed order, so two calls on the
-    same data agree in every bit.  (The loss value and the latent codes'
-    gradient are summed with float atomics and are not compared.)"""
-    spec = _spec(21, "bf16", width=256, depth=3)
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_loss_and_gradients_are_reproducible_bit_for_bit(nsf, precision):
+    """Every sum behind the loss and the gradients (weight slabs, bias column
+    sums, the input layer's per-CTA partials, the per-CTA loss partials, the
+    latent codes' per-CTA tables) runs in a fixed order, so two calls on the
+    same data agree in every bit."""
+    spec = _spec(21, precision, width=256 if precision == "bf16" else 64, depth=3)
     F = nsf.Fields.from_spec(spec)
     X, z, code, target = _data(22, 4099, spec.r, 7, ofields.OUT_DIM["g"], "g")
     runs = [_gpu_loss_grad(nsf, F, "g", X, z, code, target) for _ in range(2)]
+    assert runs[0][0] == runs[1][0]
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
