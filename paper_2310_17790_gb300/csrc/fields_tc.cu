@@ -6,19 +6,21 @@
 // A CTA holds one field's weights resident in shared memory (one bulk copy on
 // an mbarrier with a transaction count) and runs up to two tile groups of 256
 // threads (two warpgroups) side by side.  Each group owns a 128-point tile at
-// a time, its own activation operand in shared memory and its own FP32
-// accumulator in tensor memory; point i of the tile is tile row i and TMEM
-// lane i, which only the warps with (warp index % 4) == i / 32 can read, and
-// warpgroup h of the group owns the column half [h W / 2, (h + 1) W / 2).
+// a time, with its FP32 accumulator and its bf16 activation operand (the A
+// operand of tcgen05.mma) both in tensor memory; point i of the tile is tile
+// row i and TMEM lane i, which only the warps with (warp index % 4) == i / 32
+// can access, and warpgroup h of the group owns the column half
+// [h W / 2, (h + 1) W / 2).
 // Per tile:
 //   layer 0 (K = 3 + r)  on the CUDA cores in FP32, written as bf16 into the
-//                        group's shared-memory A operand;
+//                        group's activation operand (tcgen05.st);
 //   hidden layers        tcgen05.mma M = 128, N = width, K = width (16 per
-//                        instruction) issued by the group's first thread; the
-//                        epilogue reads the accumulator with tcgen05.ld, adds
-//                        the FP32 bias, applies ELU (packed f32x2 arithmetic,
-//                        one special-function exp per element), rounds to
-//                        bf16 and rewrites A in place;
+//                        instruction, A from tensor memory) issued by the
+//                        group's first thread; the epilogue reads the
+//                        accumulator with tcgen05.ld, adds the FP32 bias,
+//                        applies ELU (packed f32x2 arithmetic, one
+//                        special-function exp per element), rounds to bf16 and
+//                        rewrites the activation operand;
 //   output layer         the same MMA with N = 16 (out_dim padded with zero
 //                        rows), bias added when the outputs are read.
 // The groups synchronise on their own named barriers, so while one group runs
@@ -27,8 +29,8 @@
 // records NSF_ERR_ITER_CAP, waits (bounded) for its outstanding operations,
 // frees its tensor memory and returns.
 //
-// Weight operands (B here, A in the Jacobian kernel) and the activation tile
-// are K-major with the 128-byte swizzle (tc_common.cuh).
+// Weight operands (B here, A in the Jacobian kernel) are K-major with the
+// 128-byte swizzle (tc_common.cuh).
 #include "tc_common.cuh"
 
 namespace nsf {

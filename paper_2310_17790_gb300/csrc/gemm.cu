@@ -4,28 +4,29 @@
 //
 //   D(m, n) = sum_k A(m, k) B(n, k),  m < M, n < N, k < K,
 //
-// with each operand read through a strided view (element (row, k) at
-// ptr[row * s_row + k * s_k], float or bf16), so every product of the
-// training chain -- whatever the transposition of its factors in the
-// column-per-point activation layout -- is the same kernel.  Epilogues fuse
-// the elementwise work of the chain: bias + ELU (with the pre-activation and
-// the bf16 copy the next product reads), multiplication by ELU'(a), or a
-// per-K-slice slab for split-K weight gradients (summed in a fixed order by
-// reduce_slabs).
+// Epilogues fuse the elementwise work of the chain: bias + ELU (with the
+// ELU' code and the bf16 copy the next product reads), multiplication by
+// ELU'(a), or a per-K-slice slab for split-K weight gradients (summed in a
+// fixed order by reduce_slabs / reduce_dw).  BF16 fields:
 //
-// k_gemm_tc (BF16 fields, the width x width layers): 128 x 128 output tiles on
-// the tcgen05 tensor cores, FP32 accumulator in tensor memory.  Per K-chunk of
-// 64 every thread stages 8-element row pieces of both operands from their
-// views into shared memory as bf16, K-major with the 128-byte swizzle; one
-// thread issues four M = 128, N = 128, K = 16 tcgen05.mma per chunk and
-// commits them to the chunk's buffer barrier; two buffers, so the staging of
-// chunk c + 1 overlaps the products of chunk c.  A "split" operand is staged
-// as two bf16 tiles, hi = bf16(v) and lo = bf16(v - hi), and both are
-// multiplied: the backward products keep ~16 significant bits of the FP32
-// cotangents against the exact bf16 weights and activations.
+//   k_layer_tc   the hidden W x W layers with the points as the M dimension,
+//                persistent and warp-specialised (TMA producer warp, MMA warp,
+//                16 epilogue warps), the unit's weight rows resident in shared
+//                memory, four TMEM accumulators, coalesced staged stores;
+//   k_gemm_tc    the weight gradients delta H^T (and, from a tile of ones, the
+//                bias sums): persistent, warp-specialised, 128 x 128 tiles over
+//                K-slices of points, both operands MN-major through TMA;
+//   k_thin_k     the input layer forward (K = 3 + r) and the output layer
+//                backward with its weight gradient, on the CUDA cores;
+//   k_thin_m_warp  the output layer forward (few output rows);
+//   k_input_bwd  the input layer backward: dinp, dW0 and db0 in one pass.
 //
-// k_gemm_simt (FP32 fields, and the thin input and output layers of every
-// field): 64 x 64 tiles, 4 x 4 outputs per thread, FP32 FMA.
+// The backward products multiply the FP32 cotangent split into two bf16
+// parts, hi = bf16(v) and lo = bf16(v - hi), against the exact bf16 weights
+// and activations (~16 significant bits).  FP32 fields run every product in
+// FP32 on the CUDA cores (k_gemm_simt: 64 x 64 tiles, 4 x 4 outputs per
+// thread; k_thin_outer, k_thin_m), each operand read through a strided view
+// (element (row, k) at ptr[row * s_row + k * s_k], float or bf16).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -783,10 +784,6 @@ int slice_len(int K, int slices, int multiple) {
 // sum_n B(n, k) H(n, m) (the output layer's weight gradient).
 constexpr int kThinKMax = 20, kTkThreads = 256, kTkPoints = 128;
 
-__device__ __forceinline__ uint2 pack_codes4(const float *g) {
-    return make_uint2((unsigned)dact_code(g[0]) | ((unsigned)dact_code(g[1]) << 16),
-                      (unsigned)dact_code(g[2]) | ((unsigned)dact_code(g[3]) << 16));
-}
 __device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
     return make_uint2(pack_bf16x2(a, b), pack_bf16x2(c, d));
 }
