@@ -13,9 +13,11 @@
 //            block's bucket; the first arrival in a block lists it.
 //   P2G      each listed particle block is taken by one group of threads:
 //            its particles' 27 node contributions are summed in the block's
-//            6^3-node tile in shared memory, then every nonzero node of the
-//            tile is added once to the grid (one integer atomic per value),
-//            and the 8 grid blocks the tile covers are activated.
+//            6^3-node tile in shared memory (one lane per particle; in the
+//            batched step a block of few particles gives each lane one
+//            (particle, node) pair), then every nonzero node of the tile is
+//            added once to the grid (one integer atomic per value), and the 8
+//            grid blocks the tile covers are activated.
 //   grid     v = p / m + dt g, walls, blade, over the activated grid blocks;
 //            the sums are cleared on the way.
 //   G2P      latent: x^{n+1} on the sample particles, in the same launch;
