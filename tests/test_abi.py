@@ -47,7 +47,7 @@ def test_library_exports_every_declared_symbol(native):
 def test_ctypes_structs_match_c_layout(native, tmp_path):
     structs = ["nsf_fields_desc", "nsf_grid_desc", "nsf_latent_scene", "nsf_gn_opts",
                "nsf_latent_taps", "nsf_material", "nsf_particles", "nsf_full_taps",
-               "nsf_latent_batch_item", "nsf_batch_events"]
+               "nsf_latent_batch_item", "nsf_batch_events", "nsf_batch_tuning"]
     prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "nsf.h"', "int main(void){"]
     for s in structs:
         prog.append(f'printf("{s} %zu\\n", sizeof({s}));')
